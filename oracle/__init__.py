@@ -1,0 +1,114 @@
+"""FP64 CPU oracle of the QDS Maxwell + axion field step.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg are the only callers.  The product path never imports this
+package.  The arithmetic lives in ``qds_oracle.c`` (plain C loops written from
+the paper's equations); this module only marshals numpy arrays.
+
+State layout (complex128): ``fields[15, M, nx, nr]`` in the order
+``Trp Trm Ttp Ttm Ex Bx phi Tap Tam Trp1 Trm1 Ttp1 Ttm1 Ex1 Bx1`` and
+``phi_prev[M, nx]`` (phi on the outermost half row at time n-1).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AXION, AREM, MOVING_WINDOW, X_PERIODIC, R_CLOSED = 1, 2, 4, 8, 16
+FIELDS = ("Trp", "Trm", "Ttp", "Ttm", "Ex", "Bx", "phi", "Tap", "Tam",
+          "Trp1", "Trm1", "Ttp1", "Ttm1", "Ex1", "Bx1")
+N_FIELDS = len(FIELDS)
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.ora_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               dp, dp, dp, dp, dp]
+        L.ora_step.restype = ctypes.c_int
+        L.ora_diagnostics.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, dp, dp, dp]
+        L.ora_diagnostics.restype = ctypes.c_int
+        L.ora_mode_conv.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.ora_mode_conv.restype = None
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.complex128 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class State:
+    """Oracle state: contiguous complex128 buffer viewed as fields + phi_prev."""
+
+    def __init__(self, M, nx, nr, buf=None):
+        self.M, self.nx, self.nr = M, nx, nr
+        n = N_FIELDS * M * nx * nr + M * nx
+        self.buf = np.zeros(n, np.complex128) if buf is None else np.ascontiguousarray(buf, np.complex128).copy()
+        assert self.buf.size == n
+
+    @property
+    def fields(self):
+        return self.buf[: N_FIELDS * self.M * self.nx * self.nr].reshape(N_FIELDS, self.M, self.nx, self.nr)
+
+    @property
+    def phi_prev(self):
+        return self.buf[N_FIELDS * self.M * self.nx * self.nr:].reshape(self.M, self.nx)
+
+    def __getitem__(self, name):
+        return self.fields[FIELDS.index(name)]
+
+    def copy(self):
+        return State(self.M, self.nx, self.nr, self.buf)
+
+
+def step(p, st, jx=None, jr=None, jt=None, s_ext=None, nsteps=1):
+    """Advance ``st`` in place by ``nsteps`` steps with constant sources.
+
+    ``p``: dict with nx, nr, M, h, dr, m_a, g, flags.  Sources are complex128
+    arrays [M, nx, nr] at the native staggered positions (or None)."""
+    L = lib()
+    srcs = [None if a is None else np.ascontiguousarray(a, np.complex128) for a in (jx, jr, jt, s_ext)]
+    for _ in range(nsteps):
+        rc = L.ora_step(p["nx"], p["nr"], p["M"], p["h"], p["dr"], p.get("m_a", 0.0), p.get("g", 0.0),
+                        p.get("flags", 0), _ptr(st.buf), *[_ptr(a) for a in srcs])
+        if rc != 0:
+            raise RuntimeError(f"ora_step failed: {rc}")
+    return st
+
+
+def diagnostics(p, st, profile=False):
+    """Energies: dict(em0, axion, em1, cross[, profile])."""
+    L = lib()
+    out = np.zeros(4)
+    prof = np.zeros(p["nx"]) if profile else None
+    L.ora_diagnostics(p["nx"], p["nr"], p["M"], p["h"], p["dr"], p.get("m_a", 0.0), p.get("g", 0.0),
+                      p.get("flags", 0), _ptr(st.buf),
+                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      None if prof is None else prof.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    d = dict(em0=out[0], axion=out[1], em1=out[2], cross=out[3])
+    if profile:
+        d["profile"] = prof
+    return d
+
+
+def mode_conv(A, B):
+    """C_m{A, B} for m = 0..M-1 (Eq. mode_convolution); A, B complex [M]."""
+    A = np.ascontiguousarray(A, np.complex128)
+    B = np.ascontiguousarray(B, np.complex128)
+    out = np.zeros(A.size, np.complex128)
+    lib().ora_mode_conv(A.size, _ptr(A), _ptr(B), _ptr(out))
+    return out
