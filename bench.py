@@ -1,0 +1,325 @@
+"""Benchmark of the QDS field step on B300.
+
+Workload (default): the batched vacuum two-colour scan - 512 independent
+EM + axion + axion-regenerated-field solves of uneven size (nx 512..4096,
+nr 32..256, 2..4 modes, from seed 2), FP32 with the axion and regenerated
+fields carried as phi/g and E1/g^2, moving window.  One "step" advances every
+instance by one time step (one launch per mode count).  Inputs (72 GB of
+state) are far larger than L2.  The FP64 plain path is timed on the same
+workload; the FP64 CPU oracle is timed on a bounded sample on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qds|reference]
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QDS cell-mode updates/s FP32-batched vs FP64-plain; % HBM roofline"
+UNIT = "cell-mode updates/s"
+# algorithmic bytes per cell-mode per step: the 15 complex state words
+# (T_r+-, T_th+-, E_x, B_x; phi, T_a+-; and the regenerated group) read once
+# and written once (phi_prev and the tile halos excluded)
+WORDS = 15
+BYTES_PER_UNIT = {"f32": 2 * WORDS * 8, "f64": 2 * WORDS * 16}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_03550_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, prec):
+    """DRAM bytes per step from an ncu capture summarised under profiles/,
+    used only while the kernel source is the one that was profiled."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        e = d.get(f"{workload}/{prec}")
+        if e and e.get("kernel_hash") == kernel_hash():
+            return e["bytes_per_step"]
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_solver(wls, flags, device):
+    import torch
+    from paper_2609_03550_b300 import qds as Q
+    params = [Q.Params(w.nx, w.nr, w.M, w.dr, g=w.g, m_a=w.m_a, flags=flags) for w in wls]
+    s = Q.QDSSolver(params, device=device)
+    for i, w in enumerate(wls):
+        s.set_state(w.initial_state(device=device), i=i)
+    torch.cuda.synchronize()
+    return s
+
+
+def time_steps(s, K, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.step(K, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def cpu_baseline(wls, flags, budget_s):
+    """The FP64 oracle on the host cores over a bounded sample of the same
+    workload: whole instances in order, one step each, until budget_s."""
+    import numpy as np  # noqa: F401
+    import oracle
+    units, t_total, used = 0, 0.0, []
+    for w in wls:
+        st = oracle.State(w.M, w.nx, w.nr, w.initial_state())
+        p = dict(nx=w.nx, nr=w.nr, M=w.M, h=1.0, dr=w.dr, g=w.g, m_a=w.m_a, flags=flags & 31)
+        t0 = time.perf_counter()
+        oracle.step(p, st)
+        t_total += time.perf_counter() - t0
+        units += w.cell_modes()
+        used.append(w.name)
+        if t_total >= budget_s:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    return {"value": units / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one FP64 step of each of the first {len(used)} instances ({units} cell-modes, {t_total:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    from paper_2609_03550_b300 import inputs as I
+    wls = I.batched_scan()
+    flags = 1 | 2 | 4
+    import oracle
+    # each step: one oracle step over a bounded sample (instance 0)
+    w = wls[0]
+    st = oracle.State(w.M, w.nx, w.nr, w.initial_state())
+    p = dict(nx=w.nx, nr=w.nr, M=w.M, h=1.0, dr=w.dr, g=w.g, flags=flags)
+    for _ in range(args.warmup):
+        oracle.step(p, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(p, st)
+    dt = time.perf_counter() - t0
+    v = w.cell_modes() * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "batched_vacuum_two_colour_scan_512_seed2",
+                                           "sample": f"instance 0 ({w.nx}x{w.nr}x{w.M})"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"FP64 oracle steps of instance 0 ({w.cell_modes()} cell-modes per step)"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_qds(args):
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2609_03550_b300 import inputs as I
+    from paper_2609_03550_b300 import qds as Q
+    wls = I.batched_scan()[: args.instances]  # every rank runs its own scan (weak scaling)
+    units = sum(w.cell_modes() for w in wls)
+    flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
+    stream = torch.cuda.current_stream(device)
+
+    # ---------------- FP32 batched ----------------
+    s = build_solver(wls, flags | Q.FP32, device)
+    tile = s.tile()
+    groups_per_step = len({w.M for w in wls}) + 1   # step kernels (one per mode count) + counter advance
+    s.step(args.warmup, stream=stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    t32 = time_steps(s, args.steps, stream)
+    barrier()
+    clk = clocks.stop()
+    t32 = max_over_ranks(t32)
+    step32 = t32 / args.steps
+
+    # ---------------- end to end through the public API ----------------
+    # per step: advance every instance, compute every instance's energies
+    # (EM, axion, regenerated, exchange) and read them back to pinned host
+    # memory; the undriven vacuum workload has no per-step inputs.
+    diag_dev = torch.empty((len(wls), 4), dtype=torch.float64, device=device)
+    diag_host = torch.empty((len(wls), 4), dtype=torch.float64, pin_memory=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step(1, stream=stream)
+        s.diagnostics_all(diag_dev, stream=stream)
+        diag_host.copy_(diag_dev, non_blocking=True)
+        stream.synchronize()
+    te2e = max_over_ranks(time.perf_counter() - t0)
+    e2e_finite = bool(torch.isfinite(diag_host).all())
+    del s
+    torch.cuda.empty_cache()
+
+    # ---------------- FP64 plain on the same workload ----------------
+    fp64 = None
+    if not args.no_fp64:
+        s64 = build_solver(wls, flags, device)
+        s64.step(1, stream=stream)
+        barrier()
+        t64 = max_over_ranks(time_steps(s64, args.fp64_steps, stream))
+        step64 = t64 / args.fp64_steps
+        fp64 = {"value": world * units / step64, "unit": UNIT, "ms_per_step": 1e3 * step64,
+                "steps": args.fp64_steps, "dtype": "f64",
+                "hbm_gbs_algorithmic": units * BYTES_PER_UNIT["f64"] / step64 / 1e9,
+                "fp32_speedup": step64 / step32}
+        del s64
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_peak()
+    achieved = units * BYTES_PER_UNIT["f32"] / step32 / 1e9
+    traffic = recorded_traffic("batched_scan", "f32")
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wls, flags, args.cpu_seconds)
+    out = {
+        "metric": METRIC, "value": world * units / step32, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step32,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "batched_vacuum_two_colour_scan_512_seed2" if len(wls) == 512
+                   else f"batched_vacuum_two_colour_scan_first{len(wls)}_seed2", "instances": len(wls),
+                   "cell_modes_per_step": units, "modes": "2..4", "nx": "513..4085", "nr": "32..254",
+                   "precision": "FP32, phi/g and E1/g^2", "parallelism": f"instances, {world} GPU(s)",
+                   "l2": f"inputs larger than L2 ({units * BYTES_PER_UNIT['f32'] / 2e9:.1f} GB FP32 state per GPU)",
+                   "tile": tile},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "step_kernel (all mode-count launches of one step)",
+                     "bytes_per_unit": BYTES_PER_UNIT["f32"], "peak_kind": peak_kind},
+        "fp64_plain": fp64,
+        "e2e": {"value": world * units * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(diag_host.numel() * 8), "finite": e2e_finite,
+                "per_step": "step + diagnostics of all instances + device-to-host read"},
+        "gpu_launches": args.steps * groups_per_step,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="qds", choices=["qds", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--instances", type=int, default=512, help="first N instances (profiling runs only)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "qds":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_qds(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,144 @@
+/*
+ * qds.h -- C ABI of the B300 QDS field-step library (libqds.so).
+ *
+ * One step advances, for every retained azimuthal mode m (Sec. 2, Eq.
+ * fourier_decomp), the quasi-cylindrical direction-splitting (QDS) Maxwell
+ * solve of Sec. 2.1 (characteristic shift of T_r^+-, T_theta^+- by exactly
+ * one cell with c dt = dx, Eqs. Trp/Trm/Ttp/Ttm_update; leapfrog of E_x, B_x,
+ * Eq. Ex_update; axis rules of Sec. 2.3; open boundaries of Sec. 3.2), the
+ * Klein-Gordon axion transport of Sec. 2.2 (Eqs. Ta_plus_update,
+ * Ta_minus_update, phi_update, mode convolution Eq. mode_convolution) and the
+ * axion-regenerated fields (Eqs. jax_mode, jar_mode, jat_mode), driven by
+ * given current arrays.  Normalised units: c = eps0 = mu0 = hbar = 1.
+ *
+ * Memory: the caller allocates (and owns) the field-state buffer of
+ * qds_state_bytes() bytes, 256-byte aligned, and any source arrays; all of
+ * them are device pointers.  The handle owns only small descriptor tables
+ * and captured CUDA graphs, released by qds_free().
+ *
+ * Layouts: a "complex plane set" [M][nx][nr] stores mode m, x index i and
+ * radial index j at ((m*nx + i)*nr + j), each element an interleaved
+ * (re, im) pair of the working precision (float for QDS_FP32, else double).
+ * Staggering: T_r at (x_i, r_{j+1/2}), T_theta at (x_i, r_j), E_x at
+ * (x_{i+1/2}, r_j), B_x and phi at (x_{i+1/2}, r_{j+1/2}), T_a at
+ * (x_i, r_{j+1/2}); r_j = j dr.  Faces i = 0..nx-2 are real (nx-1 is held
+ * at zero unless x is periodic).
+ *
+ * Canonical state (qds_set_state / qds_get_state): complex128 planes
+ *   fields[15][M][nx][nr] in the order Trp Trm Ttp Ttm Ex Bx phi Tap Tam
+ *   Trp1 Trm1 Ttp1 Ttm1 Ex1 Bx1, then phi_prev[M][nx]
+ * (phi on the outermost half row one step back), in physical units and
+ * window order whatever the working precision and ring offset.
+ *
+ * Errors: every int-returning call returns QDS_OK (0) or a QDS_ERR_* code
+ * and sets a message readable with qds_last_error() (thread-local).  No call
+ * aborts the process or traps the device.  Kernel launches are asynchronous:
+ * a later call on the same stream (or a stream synchronise) reports faults.
+ */
+#ifndef QDS_H
+#define QDS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QDS_OK 0
+#define QDS_ERR_INVALID_ARG 1
+#define QDS_ERR_CUDA 2
+#define QDS_ERR_NONFINITE 3
+#define QDS_ERR_TIMEOUT 4
+#define QDS_ERR_UNSUPPORTED 5
+
+/* flags */
+#define QDS_AXION 1u          /* advance phi and T_a (Sec. 2.2)                        */
+#define QDS_AREM 2u           /* advance the axion-regenerated fields (needs QDS_AXION) */
+#define QDS_MOVING_WINDOW 4u  /* box moves one cell per step (ring offset, zero inflow)  */
+#define QDS_X_PERIODIC 8u     /* periodic x (test mode)                                 */
+#define QDS_R_CLOSED 16u      /* conducting wall / Neumann axion at r = nr dr (test)    */
+#define QDS_FP32 32u          /* FP32 storage and arithmetic (implies QDS_SCALE_G)      */
+#define QDS_SCALE_G 64u       /* store phi/g and (E1, B1)/g^2 internally                */
+
+/* The statement of one solve (Sec. 2): grid, retained modes, steps, axion. */
+typedef struct qds_params {
+  int32_t nx;              /* cells along x (>= 8)                                    */
+  int32_t nr;              /* radial rows (>= 4): integer rows 0..nr-1, half rows 1/2..nr-1/2 */
+  int32_t n_modes;         /* retained modes M (1..4)                                 */
+  const int32_t *modes;    /* host array {0, 1, ..., M-1} or NULL                     */
+  double dx, dr, dt;       /* c dt must equal dx; stability needs
+                              dr >= dx max(1.5, M - 3/4)(1 + dx m_a)                  */
+  double omega0;           /* laser frequency used only by callers' normalisations   */
+  double m_a;              /* axion mass (normalised wavenumber), dx m_a <= 1         */
+  double g;                /* axion-photon coupling g_{a gamma gamma} (normalised)    */
+  uint32_t flags;          /* QDS_* bits                                              */
+} qds_params;
+
+/* Per-step drive, device pointers in the working precision, complex plane
+ * sets [M][nx][nr] at native positions; any may be NULL (zero).
+ *   jx  at (x_{i+1/2}, r_j,     t^n)
+ *   jr  at (x_i,       r_{j+1/2}, t^{n+1/2})
+ *   jth at (x_i,       r_j,     t^{n+1/2})
+ *   s_ext: additive axion source at (x_{i+1/2}, r_{j+1/2}, t^n) (test hook)
+ * They must stay valid until the stream has executed the steps that use them.
+ * Sources are taken in window order (slot = window index); with a moving
+ * window the caller provides them in window coordinates each step. */
+typedef struct qds_sources {
+  const void *jx, *jr, *jth, *s_ext;
+} qds_sources;
+
+typedef struct qds_handle qds_handle;
+
+/* Bytes of caller-owned state for one solve (two ping-pong copies of the
+ * 15 planes + phi_prev in the working precision); 0 if params are invalid. */
+size_t qds_state_bytes(const qds_params *p);
+
+/* Create a solver bound to state_dev (>= qds_state_bytes, 256-byte aligned).
+ * Returns QDS_ERR_INVALID_ARG for an inconsistent or unstable statement
+ * (c dt != dx, dr below the stability bound, bad mode list, ...). */
+int qds_create(const qds_params *p, void *state_dev, size_t bytes, qds_handle **out);
+
+/* Import the canonical complex128 state (device pointer) and reset the step
+ * counter; asynchronous on stream (a cudaStream_t, NULL = default stream). */
+int qds_set_state(qds_handle *h, const void *src_dev, void *stream);
+
+/* Export the canonical complex128 state (device pointer), asynchronous. */
+int qds_get_state(qds_handle *h, void *dst_dev, void *stream);
+
+/* Advance nsteps steps with constant sources (src may be NULL); calls of
+ * >= 16 steps replay a captured CUDA graph.  Asynchronous on stream. */
+int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream);
+
+/* Energies into out_host[4] = {EM energy, axion energy, regenerated EM
+ * energy, int (E0.E1 + B0.B1) dV} (mode-weighted volume integrals, FP64,
+ * compensated sums); if profile_dev is non-NULL (device, nx doubles) also the
+ * transverse energy per unit length U(x) of Sec. 4.1.  Synchronises stream. */
+int qds_diagnostics(qds_handle *h, double *out_host, double *profile_dev, void *stream);
+
+/* Batched solves: n independent statements (uneven grids and mode counts,
+ * one precision) advanced together, one launch per mode count per step.
+ * Instance i owns a contiguous block of the state arena in order. */
+size_t qds_batch_state_bytes(int n, const qds_params *p);
+int qds_batch_create(int n, const qds_params *p, void *state_dev, size_t bytes, qds_handle **out);
+int qds_set_state_i(qds_handle *h, int i, const void *src_dev, void *stream);
+int qds_get_state_i(qds_handle *h, int i, void *dst_dev, void *stream);
+int qds_diagnostics_i(qds_handle *h, int i, double *out_host, double *profile_dev, void *stream);
+int qds_num_instances(const qds_handle *h);
+/* The four energies of every instance into out_dev[4*i .. 4*i+3] (device,
+ * n_inst*4 doubles) in two launches; asynchronous on stream. */
+int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
+
+/* Tile shape of the fused step kernel (x cells, radial rows); used by the
+ * autotuner.  qds_get_tile also reports the tile count and shared memory. */
+int qds_set_tile(qds_handle *h, int tx, int tr);
+int qds_get_tile(qds_handle *h, int *tx, int *tr, int *ntiles, int *smem_bytes);
+
+void qds_free(qds_handle *h);
+const char *qds_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDS_H */

@@ -1,0 +1,136 @@
+// qds_emu.cpp -- host emulation of the fused step kernel, for CPU tests only.
+//
+// Compiles the same stage code as the CUDA kernel (qds_stages.cuh) for the
+// host with bounds checks on every global and shared-memory access, and runs
+// each tile's stages in kernel order (all threads of a stage before the next
+// stage).  It exists so that the tile indexing can be checked on the CPU
+// before the kernel runs on a GPU; it is a separate library (libqds_emu.so)
+// that the product path never loads.
+#define QDS_EMU 1
+#include <cstring>
+#include <vector>
+
+#include "qds_stages.cuh"
+
+using namespace qds;
+
+namespace {
+
+template <class R, int M>
+void emu_steps(const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
+               uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext,
+               int nsteps, int TX, int TR, int nthreads) {
+  const size_t P = plane_elems(M, nx, nr), E = state_elems(M, nx, nr);
+  const bool sc = (flags & (F_FP32 | F_SCALE_G)) && g != 0.0;
+  const double s_ax = sc ? 1.0 / g : 1.0, s_ar = sc ? 1.0 / (g * g) : 1.0;
+  std::vector<C<R>> buf[2];
+  buf[0].resize(E);
+  buf[1].resize(E);
+  for (size_t q = 0; q < E; q++) {
+    double sc_ = 1.0;
+    if (q < (size_t)NFIELD * P) {
+      int f = (int)(q / P);
+      if (f == PHI || f == TAP || f == TAM) sc_ = s_ax;
+      else if (f >= TRP1) sc_ = s_ar;
+    } else sc_ = s_ax;
+    buf[0][q] = buf[1][q] = mk<R>((R)(canon[2 * q] * sc_), (R)(canon[2 * q + 1] * sc_));
+  }
+  std::vector<C<R>> sj[4];
+  const double *srcs[4] = {jx, jr, jt, sext};
+  for (int a = 0; a < 4; a++)
+    if (srcs[a]) {
+      sj[a].resize(P);
+      for (size_t q = 0; q < P; q++) sj[a][q] = mk<R>((R)srcs[a][2 * q], (R)srcs[a][2 * q + 1]);
+    }
+  Inst<R> I;
+  std::memset(&I, 0, sizeof I);
+  I.nx = nx; I.nr = nr; I.M = M; I.flags = flags;
+  I.h = (R)h; I.dr = (R)dr; I.inv_h = (R)(1.0 / h); I.inv_dr = (R)(1.0 / dr);
+  I.ma2 = (R)(m_a * m_a);
+  I.gs = sc ? (R)1 : (R)g;
+  I.gj = sc ? (R)1 : (R)g;
+  I.jx = jx ? sj[0].data() : nullptr;
+  I.jr = jr ? sj[1].data() : nullptr;
+  I.jt = jt ? sj[2].data() : nullptr;
+  I.sext = sext ? sj[3].data() : nullptr;
+  Geo geo;
+  geo.TX = TX;
+  geo.TR = TR;
+  Smem L = smem_layout(geo, M, flags);
+  std::vector<C<R>> sm(L.total);
+  for (int n = 0; n < nsteps; n++) {
+    const int par = n & 1;
+    for (int x0 = 0; x0 < nx; x0 += TX)
+      for (int r0 = 0; r0 < nr; r0 += TR) {
+        Tile<R, M> t;
+        t.I = &I;
+        t.nx = nx; t.nr = nr; t.J = nr - 1;
+        t.x0 = x0; t.r0 = r0;
+        t.per = (flags & F_X_PERIODIC) != 0;
+        t.closed = (flags & F_R_CLOSED) != 0;
+        t.mw = (flags & F_MOVING_WINDOW) != 0;
+        t.s = t.mw ? n % nx : 0;
+        t.P = P;
+        t.o = buf[par].data();
+        t.n = buf[par ^ 1].data();
+        t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
+        t.g = geo;
+        t.L = L;
+        // poison shared memory so that a read of a slot no stage wrote shows up
+        for (auto &z : sm) z = mk<R>((R)1e30, (R)1e30);
+        t.sm = sm.data();
+        t.state_len = E;
+        t.sm_len = L.total;
+        for (int st = 0; st < N_STAGE; st++)
+          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M>(t, st, tid, nthreads);
+      }
+  }
+  // export in window order
+  const auto &b = buf[nsteps & 1];
+  const int s = (flags & F_MOVING_WINDOW) ? nsteps % nx : 0;
+  for (size_t q = 0; q < E; q++) {
+    double sc_ = 1.0;
+    size_t from;
+    if (q < (size_t)NFIELD * P) {
+      int f = (int)(q / P);
+      if (f == PHI || f == TAP || f == TAM) sc_ = 1.0 / s_ax;
+      else if (f >= TRP1) sc_ = 1.0 / s_ar;
+      size_t rem = q % P;
+      int j = (int)(rem % nr);
+      size_t kw = rem / nr;
+      int w = (int)(kw % nx), k = (int)(kw / nx);
+      int sl = (w + s) % nx;
+      from = (size_t)f * P + ((size_t)k * nx + sl) * nr + j;
+    } else {
+      sc_ = 1.0 / s_ax;
+      size_t rem = q - (size_t)NFIELD * P;
+      int w = (int)(rem % nx), k = (int)(rem / nx);
+      from = (size_t)NFIELD * P + (size_t)k * nx + (w + s) % nx;
+    }
+    out[2 * q] = (double)b[from].re * sc_;
+    out[2 * q + 1] = (double)b[from].im * sc_;
+  }
+}
+
+template <class R>
+int dispatch(int M, const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
+             uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext, int nsteps,
+             int TX, int TR, int nth) {
+  switch (M) {
+    case 1: emu_steps<R, 1>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
+    case 2: emu_steps<R, 2>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
+    case 3: emu_steps<R, 3>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
+    case 4: emu_steps<R, 4>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
+  }
+  return 1;
+}
+
+}  // namespace
+
+extern "C" int qds_emu_steps(int M, const double *canon, double *out, int nx, int nr, double h, double dr,
+                             double m_a, double g, uint32_t flags, const double *jx, const double *jr,
+                             const double *jt, const double *sext, int nsteps, int TX, int TR, int nthreads) {
+  if (flags & F_FP32)
+    return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads);
+  return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads);
+}

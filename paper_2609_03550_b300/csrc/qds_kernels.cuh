@@ -1,0 +1,274 @@
+// qds_kernels.cuh -- CUDA kernels of the QDS library: the fused step, the
+// step-counter advance, state import/export and the diagnostics reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qds_stages.cuh"
+
+namespace qds {
+
+struct Ctrl {
+  unsigned long long step;  // steps taken since the last state import
+  unsigned int err;         // device-side error flags
+  unsigned int pad;
+};
+
+// One CTA per (instance, x-tile, r-tile); every stage of the step runs on
+// the tile in order with a barrier in between.
+template <class R, int M>
+__global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ insts,
+                                                   const int4 *__restrict__ tiles,
+                                                   const Ctrl *__restrict__ ctrl, Geo g, Smem L) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int4 td = tiles[blockIdx.x];
+  const Inst<R> &I = insts[td.x];
+  const unsigned long long n = ctrl->step;
+  Tile<R, M> t;
+  t.I = &I;
+  t.nx = I.nx;
+  t.nr = I.nr;
+  t.J = I.nr - 1;
+  t.x0 = td.y;
+  t.r0 = td.z;
+  t.per = (I.flags & F_X_PERIODIC) != 0;
+  t.closed = (I.flags & F_R_CLOSED) != 0;
+  t.mw = (I.flags & F_MOVING_WINDOW) != 0;
+  t.s = t.mw ? (int)(n % (unsigned long long)I.nx) : 0;
+  t.P = plane_elems(M, I.nx, I.nr);
+  const int par = (int)(n & 1ull);
+  t.o = I.state[par];
+  t.n = I.state[par ^ 1];
+  t.h = I.h;
+  t.dr = I.dr;
+  t.ih = I.inv_h;
+  t.idr = I.inv_dr;
+  t.g = g;
+  t.L = L;
+  t.sm = reinterpret_cast<C<R> *>(smraw);
+#pragma unroll 1
+  for (int st = 0; st < N_STAGE; st++) {
+    run_stage<R, M>(t, st, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+}
+
+__global__ void advance_kernel(Ctrl *ctrl, int nsteps) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->step += (unsigned long long)nsteps;
+}
+
+__global__ void reset_kernel(Ctrl *ctrl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) { ctrl->step = 0; ctrl->err = 0; }
+}
+
+// Canonical complex128 layout <-> working storage (precision, ring offset,
+// 1/g scaling of the axion and regenerated groups).
+template <class R>
+__global__ void import_kernel(const double2 *__restrict__ src, C<R> *b0, C<R> *b1, int M, int nx, int nr,
+                              double s_ax, double s_ar) {
+  const size_t P = plane_elems(M, nx, nr);
+  const size_t total = state_elems(M, nx, nr);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    double sc = 1.0;
+    if (q < (size_t)NFIELD * P) {
+      int f = (int)(q / P);
+      if (f == PHI || f == TAP || f == TAM) sc = s_ax;
+      else if (f >= TRP1) sc = s_ar;
+    } else {
+      sc = s_ax;  // phi_prev
+    }
+    double2 v = src[q];
+    C<R> z = mk<R>((R)(v.x * sc), (R)(v.y * sc));
+    b0[q] = z;
+    b1[q] = z;
+  }
+}
+
+template <class R>
+__global__ void export_kernel(const C<R> *__restrict__ b0, const C<R> *__restrict__ b1, const Ctrl *ctrl,
+                              double2 *dst, int M, int nx, int nr, uint32_t flags, double s_ax, double s_ar) {
+  const unsigned long long n = ctrl->step;
+  const C<R> *b = (n & 1ull) ? b1 : b0;
+  const int s = (flags & F_MOVING_WINDOW) ? (int)(n % (unsigned long long)nx) : 0;
+  const size_t P = plane_elems(M, nx, nr);
+  const size_t total = state_elems(M, nx, nr);
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    double sc = 1.0;
+    size_t from;
+    if (q < (size_t)NFIELD * P) {
+      int f = (int)(q / P);
+      if (f == PHI || f == TAP || f == TAM) sc = s_ax;
+      else if (f >= TRP1) sc = s_ar;
+      size_t rem = q % P;
+      int j = (int)(rem % nr);
+      size_t kw = rem / nr;
+      int w = (int)(kw % nx), k = (int)(kw / nx);
+      int sl = w + s; if (sl >= nx) sl -= nx;
+      from = (size_t)f * P + ((size_t)k * nx + sl) * nr + j;
+    } else {
+      sc = s_ax;
+      size_t rem = q - (size_t)NFIELD * P;
+      int w = (int)(rem % nx), k = (int)(rem / nx);
+      int sl = w + s; if (sl >= nx) sl -= nx;
+      from = (size_t)NFIELD * P + (size_t)k * nx + sl;
+    }
+    C<R> z = b[from];
+    dst[q] = make_double2((double)z.re * sc, (double)z.im * sc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: energies with the azimuthal weights of Eq. fourier_decomp
+// (w_0 = 1, w_m = 1/2) and the cell volume 2 pi r dr h (r_0 -> dr/8 on the
+// axis row), accumulated in FP64 with Neumaier compensation.
+// ---------------------------------------------------------------------------
+struct Neu {
+  double s = 0.0, c = 0.0;
+  __device__ void add(double x) {
+    double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  __device__ double val() const { return s + c; }
+};
+
+template <class R>
+__device__ __forceinline__ double nrm(C<R> a) { return (double)a.re * a.re + (double)a.im * a.im; }
+template <class R>
+__device__ __forceinline__ double dotre(C<R> a, C<R> b) { return (double)a.re * b.re + (double)a.im * b.im; }
+
+// Energy densities of one (mode, x, r) element of one instance, added to the
+// four accumulators em0, axion, em1, cross (without the common prefactor).
+template <class R>
+__device__ __forceinline__ void diag_element(const C<R> *S, size_t P, size_t q, int nx, int nr, double dr,
+                                             double ma2, Neu &a0, Neu &a1, Neu &a2, Neu &a3) {
+  const int j = (int)(q % nr);
+  const int k = (int)(q / ((size_t)nx * nr));
+  const double wm = k == 0 ? 1.0 : 0.5;
+  const double rh = (j + 0.5) * dr, rs = j == 0 ? dr / 8.0 : j * dr;
+  double e[2];
+  C<R> er[2], bt[2], et[2], br[2], ex[2], bx[2];
+  for (int gi = 0; gi < 2; gi++) {
+    const int o = gi ? TRP1 : TRP;
+    C<R> tp = S[(size_t)(o + 0) * P + q], tm = S[(size_t)(o + 1) * P + q];
+    C<R> up = S[(size_t)(o + 2) * P + q], um = S[(size_t)(o + 3) * P + q];
+    er[gi] = R(0.5) * (tp + tm); bt[gi] = R(0.5) * (tp - tm);
+    et[gi] = R(0.5) * (up + um); br[gi] = R(0.5) * (up - um);
+    ex[gi] = S[(size_t)(o + 4) * P + q]; bx[gi] = S[(size_t)(o + 5) * P + q];
+    e[gi] = rh * (nrm(er[gi]) + nrm(bt[gi])) + rs * (nrm(et[gi]) + nrm(br[gi])) + rs * nrm(ex[gi]) + rh * nrm(bx[gi]);
+  }
+  a0.add(wm * e[0]);
+  a2.add(wm * e[1]);
+  C<R> ph = S[(size_t)PHI * P + q], ap = S[(size_t)TAP * P + q], am = S[(size_t)TAM * P + q];
+  double ua = rh * 0.5 * (nrm(ap) + nrm(am)) + rh * ((double)k * k / (rh * rh) + ma2) * nrm(ph);
+  if (j > 0) {
+    C<R> d = S[(size_t)PHI * P + q] - S[(size_t)PHI * P + q - 1];
+    ua += (j * dr) * nrm(d) / (dr * dr);
+  }
+  a1.add(wm * ua);
+  double cr = rh * (dotre(er[0], er[1]) + dotre(bt[0], bt[1])) + rs * (dotre(et[0], et[1]) + dotre(br[0], br[1])) +
+              rs * dotre(ex[0], ex[1]) + rh * dotre(bx[0], bx[1]);
+  a3.add(wm * cr);
+}
+
+__device__ __forceinline__ void block_reduce4(Neu &a0, Neu &a1, Neu &a2, Neu &a3, double *dst) {
+  __shared__ double red[4][256];
+  red[0][threadIdx.x] = a0.val();
+  red[1][threadIdx.x] = a1.val();
+  red[2][threadIdx.x] = a2.val();
+  red[3][threadIdx.x] = a3.val();
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int c = 0; c < 4; c++) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 4; c++) dst[c] = red[c][0];
+}
+
+// partial[b*4 + 0..3]: em0, axion, em1, cross of one instance
+template <class R>
+__global__ void diag_partial_kernel(const C<R> *__restrict__ b0, const C<R> *__restrict__ b1, const Ctrl *ctrl,
+                                    int M, int nx, int nr, double dr, double ma2, double *partial) {
+  const C<R> *S = (ctrl->step & 1ull) ? b1 : b0;
+  const size_t P = plane_elems(M, nx, nr);
+  Neu a0, a1, a2, a3;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x)
+    diag_element(S, P, q, nx, nr, dr, ma2, a0, a1, a2, a3);
+  block_reduce4(a0, a1, a2, a3, partial + blockIdx.x * 4);
+}
+
+// All instances of a batch in one launch: grid (blocks, instances).
+template <class R>
+__global__ void diag_partial_all_kernel(const Inst<R> *__restrict__ insts, const Ctrl *ctrl, double *partial) {
+  const Inst<R> &I = insts[blockIdx.y];
+  const C<R> *S = I.state[ctrl->step & 1ull];
+  const size_t P = plane_elems(I.M, I.nx, I.nr);
+  const double dr = (double)I.dr, ma2 = (double)I.ma2;
+  Neu a0, a1, a2, a3;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x)
+    diag_element(S, P, q, I.nx, I.nr, dr, ma2, a0, a1, a2, a3);
+  block_reduce4(a0, a1, a2, a3, partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4);
+}
+
+// scal[i] = {pi dr dx, g^2 or 1, g^4 or 1, g^2 or 1} per instance
+__global__ void diag_final_all_kernel(const double *partial, int nblk, const double4 *scal, int n, double *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Neu s[4];
+  for (int b = 0; b < nblk; b++)
+    for (int c = 0; c < 4; c++) s[c].add(partial[((size_t)i * nblk + b) * 4 + c]);
+  const double4 f = scal[i];
+  out[4 * i + 0] = f.x * s[0].val();
+  out[4 * i + 1] = f.x * s[1].val() * f.y;
+  out[4 * i + 2] = f.x * s[2].val() * f.z;
+  out[4 * i + 3] = 2.0 * f.x * s[3].val() * f.w;
+}
+
+__global__ void diag_final_kernel(const double *partial, int nblk, double pref, double s_ax2, double s_ar2,
+                                  double s_cross, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Neu s[4];
+  for (int b = 0; b < nblk; b++)
+    for (int c = 0; c < 4; c++) s[c].add(partial[b * 4 + c]);
+  out[0] = pref * s[0].val();
+  out[1] = pref * s[1].val() * s_ax2;
+  out[2] = pref * s[2].val() * s_ar2;
+  out[3] = 2.0 * pref * s[3].val() * s_cross;
+}
+
+// U(x_w) = int (1/2)(|E_perp|^2 + |B_perp|^2) dA of group 0 (Sec. 4.1), one
+// block per window column.
+template <class R>
+__global__ void profile_kernel(const C<R> *__restrict__ b0, const C<R> *__restrict__ b1, const Ctrl *ctrl,
+                               int M, int nx, int nr, double dr, uint32_t flags, double *prof) {
+  const unsigned long long n = ctrl->step;
+  const C<R> *S = (n & 1ull) ? b1 : b0;
+  const int s = (flags & F_MOVING_WINDOW) ? (int)(n % (unsigned long long)nx) : 0;
+  const int w = blockIdx.x;
+  int sl = w + s; if (sl >= nx) sl -= nx;
+  const size_t P = plane_elems(M, nx, nr);
+  Neu acc;
+  for (int q = threadIdx.x; q < M * nr; q += blockDim.x) {
+    const int k = q / nr, j = q % nr;
+    const size_t e = ((size_t)k * nx + sl) * nr + j;
+    C<R> tp = S[(size_t)TRP * P + e], tm = S[(size_t)TRM * P + e];
+    C<R> up = S[(size_t)TTP * P + e], um = S[(size_t)TTM * P + e];
+    const double wm = k == 0 ? 1.0 : 0.5;
+    const double rh = (j + 0.5) * dr, rs = j == 0 ? dr / 8.0 : j * dr;
+    acc.add(wm * (rh * (nrm(R(0.5) * (tp + tm)) + nrm(R(0.5) * (tp - tm))) +
+                  rs * (nrm(R(0.5) * (up + um)) + nrm(R(0.5) * (up - um)))));
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc.val();
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) prof[w] = 3.14159265358979323846 * dr * red[0];
+}
+
+}  // namespace qds

@@ -1,0 +1,696 @@
+// qds_stages.cuh -- the stages of one fused QDS + axion + AREM step on an
+// (x, r) tile.  Every stage is a loop over the points of a tile-local region
+// with a barrier between stages; each point handles all retained modes.
+//
+// Window coordinates: cell w sits at x_w, face w at x_{w+1/2}; the storage
+// slot of window position w is (w + s) mod nx, where s advances by one per
+// step when the window moves (the x-shift of the whole box is an index
+// offset, not a copy).  Outside the box (non-periodic) every field reads as
+// zero, which is the open x boundary of Eq. em_x_open / axion_x_open.
+#pragma once
+
+#include "qds_common.cuh"
+
+#if defined(QDS_EMU)
+#include <cstdio>
+#include <cstdlib>
+#define QDS_CHECK(cond, what)                                              \
+  do {                                                                     \
+    if (!(cond)) {                                                         \
+      std::fprintf(stderr, "qds emu bounds: %s (%s:%d)\n", what, __FILE__, \
+                   __LINE__);                                              \
+      std::abort();                                                        \
+    }                                                                      \
+  } while (0)
+#else
+#define QDS_CHECK(cond, what) ((void)0)
+#endif
+
+namespace qds {
+
+template <class R>
+QDS_HD C<R> ldg(const C<R> *p) {
+#if defined(__CUDA_ARCH__)
+  if (sizeof(R) == 4) {
+    float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return mk<R>((R)v.x, (R)v.y);
+  } else {
+    double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return mk<R>((R)v.x, (R)v.y);
+  }
+#else
+  return *p;
+#endif
+}
+
+template <class R, int M>
+struct Tile {
+  const Inst<R> *I;
+  int nx, nr, J;       // J = nr - 1: last integer row / last half row
+  int x0, r0;          // tile origin in window coordinates
+  int s;               // ring offset of the window
+  bool per, closed, mw;
+  size_t P;            // elements per field (M planes)
+  const C<R> *o;       // old state
+  C<R> *n;             // new state
+  R h, dr, ih, idr;
+  Geo g;
+  Smem L;
+  C<R> *sm;
+#if defined(QDS_EMU)
+  size_t state_len;    // bounds for the emulator
+  int sm_len;
+#endif
+
+  // ---------------- index helpers ----------------
+  QDS_HD bool cell_ok(int w) const { return per || (w >= 0 && w < nx); }
+  QDS_HD bool face_ok(int w) const { return per || (w >= 0 && w <= nx - 2); }
+  QDS_HD int slot(int w) const {
+    if (per) { w %= nx; if (w < 0) w += nx; return w; }
+    int q = w + s;
+    return q >= nx ? q - nx : q;
+  }
+  QDS_HD size_t gidx(int field, int k, int w, int j) const {
+    return (size_t)field * P + ((size_t)k * nx + slot(w)) * nr + j;
+  }
+  QDS_HD C<R> cell(int field, int k, int w, int j) const {
+    if (!cell_ok(w) || j < 0 || j >= nr) return zero<R>();
+#if defined(QDS_EMU)
+    QDS_CHECK(gidx(field, k, w, j) < state_len, "cell read");
+#endif
+    return ldg(o + gidx(field, k, w, j));
+  }
+  QDS_HD C<R> face(int field, int k, int w, int j) const {
+    if (!face_ok(w) || j < 0 || j >= nr) return zero<R>();
+#if defined(QDS_EMU)
+    QDS_CHECK(gidx(field, k, w, j) < state_len, "face read");
+#endif
+    return ldg(o + gidx(field, k, w, j));
+  }
+  QDS_HD C<R> prev(int k, int w) const {
+    if (!face_ok(w)) return zero<R>();
+    return ldg(o + (size_t)NFIELD * P + (size_t)k * nx + slot(w));
+  }
+  // caller-owned source arrays [M][nx][nr] (native staggered positions),
+  // indexed in window order (not by ring slot)
+  QDS_HD C<R> srcv(const C<R> *a, int k, int w, int j) const {
+    if (!a || !cell_ok(w) || j < 0 || j >= nr) return zero<R>();
+    if (per) { w %= nx; if (w < 0) w += nx; }
+    return ldg(a + ((size_t)k * nx + w) * nr + j);
+  }
+  QDS_HD void store(int field, int k, int w, int j, C<R> v) const {
+    if (mw && w == 0) v = zero<R>();  // the rear column becomes the new front
+#if defined(QDS_EMU)
+    QDS_CHECK(gidx(field, k, w, j) < state_len, "store");
+#endif
+    n[gidx(field, k, w, j)] = v;
+  }
+  QDS_HD void store_prev(int k, int w, C<R> v) const {
+    if (mw && w == 0) v = zero<R>();
+    n[(size_t)NFIELD * P + (size_t)k * nx + slot(w)] = v;
+  }
+  QDS_HD bool owned(int lx, int lr) const {
+    return lx >= 0 && lx < g.TX && lr >= 0 && lr < g.TR && x0 + lx < nx && r0 + lr < nr;
+  }
+
+  // transverse fields at time n of group grp (0 or 9), Eq. reconstruct_fields
+  QDS_HD C<R> Er(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TRP, k, w, j) + cell(grp + TRM, k, w, j)); }
+  QDS_HD C<R> Bt(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TRP, k, w, j) - cell(grp + TRM, k, w, j)); }
+  QDS_HD C<R> Et(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) + cell(grp + TTM, k, w, j)); }
+  QDS_HD C<R> Br(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) - cell(grp + TTM, k, w, j)); }
+
+  // ---------------- shared-memory planes ----------------
+  QDS_HD C<R> &sA(int pl, int k, int lx, int lr) const {  // pl 0: Ex0n, 1: Bx0n
+    int i = L.off_a + ((pl * M + k) * g.a_nx() + (lx - g.a_x0())) * g.a_nr() + (lr - g.a_r0());
+#if defined(QDS_EMU)
+    QDS_CHECK(lx >= g.a_x0() && lx < g.a_x0() + g.a_nx() && lr >= g.a_r0() && lr < g.a_r0() + g.a_nr(), "sA");
+#endif
+    return sm[i];
+  }
+  QDS_HD C<R> &sG(int k, int lx, int lr) const {
+    int i = L.off_j + (k * g.g_nx() + (lx - g.g_x0())) * g.g_nr() + (lr - g.g_r0());
+#if defined(QDS_EMU)
+    QDS_CHECK(lx >= g.g_x0() && lx < g.g_x0() + g.g_nx() && lr >= g.g_r0() && lr < g.g_r0() + g.g_nr(), "sG");
+#endif
+    return sm[i];
+  }
+  QDS_HD C<R> &sT(int pl, int k, int lx, int lr) const {  // 0..3 T0 new, 4 Tap new, 5 Tam new
+    int i = L.off_t + ((pl * M + k) * g.t_nx() + (lx - g.t_x0())) * g.t_nr() + (lr - g.t_r0());
+#if defined(QDS_EMU)
+    QDS_CHECK(lx >= g.t_x0() && lx < g.t_x0() + g.t_nx() && lr >= g.t_r0() && lr < g.t_r0() + g.t_nr(), "sT");
+#endif
+    return sm[i];
+  }
+  QDS_HD C<R> &sP(int k, int lx, int lr) const {
+    int i = L.off_p + (k * g.p_nx() + (lx - g.p_x0())) * g.p_nr() + (lr - g.p_r0());
+#if defined(QDS_EMU)
+    QDS_CHECK(lx >= g.p_x0() && lx < g.p_x0() + g.p_nx() && lr >= g.p_r0() && lr < g.p_r0() + g.p_nr(), "sP");
+#endif
+    return sm[i];
+  }
+  QDS_HD C<R> &sJ(int pl, int k, int lx, int lr) const {  // 0 Ex1n 1 Bx1n 2 jax 3 jar 4 jat
+    int i = L.off_j + ((pl * M + k) * g.j_nx() + (lx - g.j_x0())) * g.j_nr() + (lr - g.j_r0());
+#if defined(QDS_EMU)
+    QDS_CHECK(lx >= g.j_x0() && lx < g.j_x0() + g.j_nx() && lr >= g.j_r0() && lr < g.j_r0() + g.j_nr(), "sJ");
+#endif
+    return sm[i];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Mode convolution C_m{A, B} (Eq. mode_convolution) for retained modes
+// 0..M-1, negative modes being conjugates (Eq. fourier_decomp).
+// ---------------------------------------------------------------------------
+template <class R, int M>
+QDS_HD C<R> conv(int m, const C<R> *A, const C<R> *B) {
+  if (m == 0) {
+    C<R> s = A[0] * B[0];
+    R acc = R(0);
+#pragma unroll
+    for (int k = 1; k < M; k++) acc += A[k].re * B[k].re + A[k].im * B[k].im;
+    s.re += R(0.5) * acc;
+    return s;
+  }
+  C<R> s = zero<R>();
+#pragma unroll
+  for (int k = 0; k <= m && k < M; k++) {      // k + l = m
+    int l = m - k;
+    if (l < M) s += A[k] * B[l];
+  }
+#pragma unroll
+  for (int l = 0; l + m < M; l++) s += mul_cj(A[l + m], B[l]);   // k - l = m
+#pragma unroll
+  for (int k = 0; k + m < M; k++) s += mul_cj(B[k + m], A[k]);   // l - k = m
+  return R(0.5) * s;
+}
+
+// ---------------------------------------------------------------------------
+// Longitudinal leapfrog (Eqs. Ex_update, Gammax_explicit, Phix_explicit,
+// axis_Ex) for one mode at face w.  The radial operators are written in
+// conservative form, (1/r) d(r F)/dr = (r_+ F_+ - r_- F_-)/(r dr), which is
+// algebraically the paper's average-plus-centred-difference form.
+// ---------------------------------------------------------------------------
+template <class R, int M>
+QDS_HD C<R> ex_update(const Tile<R, M> &t, int grp, int k, int w, int j, C<R> jx) {
+  C<R> e0 = t.face(grp + EX, k, w, j);
+  if (j == 0) {
+    if (k != 0) return zero<R>();
+    C<R> b = R(0.5) * (t.Bt(grp, k, w, 0) + t.Bt(grp, k, w + 1, 0));
+    return e0 + t.h * (R(4) * t.idr * b - jx);
+  }
+  R rj = R(j) * t.dr;
+  C<R> bhi = R(0.5) * (t.Bt(grp, k, w, j) + t.Bt(grp, k, w + 1, j));
+  C<R> blo = R(0.5) * (t.Bt(grp, k, w, j - 1) + t.Bt(grp, k, w + 1, j - 1));
+  C<R> br = R(0.5) * (t.Br(grp, k, w, j) + t.Br(grp, k, w + 1, j));
+  C<R> curl = ((R(j) + R(0.5)) * bhi - (R(j) - R(0.5)) * blo) * (R(1) / (R(j) * t.dr));
+  C<R> gx = curl + imul(R(k) / rj, br) - jx;
+  return e0 + t.h * gx;
+}
+
+template <class R, int M>
+QDS_HD C<R> bx_interior(const Tile<R, M> &t, int grp, int k, int w, int j) {
+  C<R> b0 = t.face(grp + BX, k, w, j);
+  R rh = (R(j) + R(0.5)) * t.dr;
+  C<R> elo = R(0.5) * (t.Et(grp, k, w, j) + t.Et(grp, k, w + 1, j));
+  C<R> ehi = (j + 1 < t.nr) ? R(0.5) * (t.Et(grp, k, w, j + 1) + t.Et(grp, k, w + 1, j + 1)) : zero<R>();
+  C<R> er = R(0.5) * (t.Er(grp, k, w, j) + t.Er(grp, k, w + 1, j));
+  C<R> curl = (R(j + 1) * ehi - R(j) * elo) * (R(1) / ((R(j) + R(0.5)) * t.dr));
+  return b0 - t.h * (curl + imul(R(k) / rh, er));
+}
+
+// Outer half row J+1/2, Eq. em_r_open_bx by the box scheme over
+// [r_{J-1/2}, r_{J+1/2}] x [t^{n-1/2}, t^{n+1/2}], right side at (x_{w+1/2}, r_J, t^n).
+template <class R, int M>
+QDS_HD C<R> bx_outer(const Tile<R, M> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
+  const int J = t.J;
+  R rJ = R(J) * t.dr;
+  C<R> dxbr = t.ih * (t.Br(grp, k, w + 1, J) - t.Br(grp, k, w, J));
+  C<R> eth = R(0.5) * (t.Et(grp, k, w, J) + t.Et(grp, k, w + 1, J));
+  C<R> er = R(0.25) * (t.Er(grp, k, w, J - 1) + t.Er(grp, k, w, J) + t.Er(grp, k, w + 1, J - 1) + t.Er(grp, k, w + 1, J));
+  C<R> rhs = R(0.5) * dxbr - (R(0.5) / rJ) * (eth + imul(R(k), er)) - R(0.5) * jt_face;
+  C<R> bo = t.face(grp + BX, k, w, J), bi = t.face(grp + BX, k, w, J - 1);
+  R a = R(0.5) * t.ih, b = R(0.5) * t.idr;
+  C<R> num = rhs - (a - b) * b_in_new + (a - b) * bo + (a + b) * bi;
+  return num * (R(1) / (a + b));
+}
+
+// ---------------------------------------------------------------------------
+// Face quantities consumed by the characteristic shift: group 0 reads them
+// from the tile's shared memory and x-averages the caller's cell currents;
+// group 1 (the regenerated field) reads E_x1, B_x1 and j_a from shared memory.
+// ---------------------------------------------------------------------------
+template <class R, int M>
+struct Faces0 {
+  const Tile<R, M> &t;
+  QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sA(0, k, lx, lr); }
+  QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sA(1, k, lx, lr); }
+  QDS_HD C<R> jr(int k, int lx, int lr) const {
+    int w = t.x0 + lx, j = t.r0 + lr;
+    if (!t.I->jr || !t.face_ok(w)) return zero<R>();
+    return R(0.5) * (t.srcv(t.I->jr, k, w, j) + t.srcv(t.I->jr, k, w + 1, j));
+  }
+  QDS_HD C<R> jt(int k, int lx, int lr) const {
+    int w = t.x0 + lx, j = t.r0 + lr;
+    if (!t.I->jt || !t.face_ok(w)) return zero<R>();
+    return R(0.5) * (t.srcv(t.I->jt, k, w, j) + t.srcv(t.I->jt, k, w + 1, j));
+  }
+  QDS_HD C<R> jx(int k, int lx, int lr) const {
+    int w = t.x0 + lx, j = t.r0 + lr;
+    if (!t.face_ok(w)) return zero<R>();
+    return t.srcv(t.I->jx, k, w, j);
+  }
+};
+
+template <class R, int M>
+struct Faces1 {
+  const Tile<R, M> &t;
+  QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sJ(0, k, lx, lr); }
+  QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sJ(1, k, lx, lr); }
+  QDS_HD C<R> jx(int k, int lx, int lr) const { return t.sJ(2, k, lx, lr); }
+  QDS_HD C<R> jr(int k, int lx, int lr) const { return t.sJ(3, k, lx, lr); }
+  QDS_HD C<R> jt(int k, int lx, int lr) const { return t.sJ(4, k, lx, lr); }
+};
+
+// ---------------------------------------------------------------------------
+// Characteristic shift of the transport variables (Eqs. Trp_update,
+// Trm_update, Ttp_update, Ttm_update): T_r^+ and T_th^- arrive from the cell
+// behind through face c-1, T_r^- and T_th^+ from the cell ahead through face
+// c.  Axis rules of Sec. 2.3 (Eq. axis_Ttheta; T_th^(m!=1) = 0 on the axis).
+// ---------------------------------------------------------------------------
+template <class R, int M, class FS>
+QDS_HD void tr_interior(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
+                        C<R> &tp, C<R> &tm) {
+  const int c = t.x0 + lx, j = t.r0 + lr;
+  R rh = (R(j) + R(0.5)) * t.dr;
+  C<R> sp = zero<R>(), sm = zero<R>();
+  if (t.face_ok(c - 1)) {
+    C<R> ehi = (j + 1 < t.nr) ? fs.ex(k, lx - 1, lr + 1) : zero<R>();
+    C<R> gr = -imul(R(k) / rh, fs.bx(k, lx - 1, lr)) - fs.jr(k, lx - 1, lr);
+    sp = gr + t.idr * (ehi - fs.ex(k, lx - 1, lr));
+  }
+  if (t.face_ok(c)) {
+    C<R> ehi = (j + 1 < t.nr) ? fs.ex(k, lx, lr + 1) : zero<R>();
+    C<R> gr = -imul(R(k) / rh, fs.bx(k, lx, lr)) - fs.jr(k, lx, lr);
+    sm = gr - t.idr * (ehi - fs.ex(k, lx, lr));
+  }
+  tp = t.cell(grp + TRP, k, c - 1, j) + t.h * sp;
+  tm = t.cell(grp + TRM, k, c + 1, j) + t.h * sm;
+}
+
+// Outer half row: E_r by the shift with the Gamma_r source alone, B_theta by
+// the box scheme of Eq. em_r_open_bt over [r_{J-1/2}, r_{J+1/2}] x [t^n, t^{n+1}]
+// with its right side from time-n fields.
+template <class R, int M, class FS>
+QDS_HD void tr_outer(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
+                     int lr_J, C<R> &tp, C<R> &tm) {
+  const int c = t.x0 + lx, J = t.J;
+  R rh = (R(J) + R(0.5)) * t.dr, rJ = R(J) * t.dr;
+  C<R> gl = zero<R>(), gr = zero<R>();
+  if (t.face_ok(c - 1)) gl = -imul(R(k) / rh, fs.bx(k, lx - 1, lr_J)) - fs.jr(k, lx - 1, lr_J);
+  if (t.face_ok(c)) gr = -imul(R(k) / rh, fs.bx(k, lx, lr_J)) - fs.jr(k, lx, lr_J);
+  C<R> er_new = R(0.5) * (t.cell(grp + TRP, k, c - 1, J) + t.cell(grp + TRM, k, c + 1, J) + t.h * (gl + gr));
+  C<R> erl = R(0.5) * (t.Er(grp, k, c - 1, J - 1) + t.Er(grp, k, c - 1, J));
+  C<R> err = R(0.5) * (t.Er(grp, k, c + 1, J - 1) + t.Er(grp, k, c + 1, J));
+  C<R> bth = R(0.5) * (t.Bt(grp, k, c, J - 1) + t.Bt(grp, k, c, J));
+  C<R> br = t.Br(grp, k, c, J);
+  C<R> jxl = t.face_ok(c - 1) ? fs.jx(k, lx - 1, lr_J) : zero<R>();
+  C<R> jxr = t.face_ok(c) ? fs.jx(k, lx, lr_J) : zero<R>();
+  C<R> rhs = (R(-0.25) * t.ih) * (err - erl) - (R(0.5) / rJ) * (bth + imul(R(k), br)) + R(0.25) * (jxl + jxr);
+  C<R> bo = t.Bt(grp, k, c, J), bi = t.Bt(grp, k, c, J - 1);
+  R a = R(0.5) * t.ih, b = R(0.5) * t.idr;
+  C<R> bt_new = (rhs - (a - b) * bt_in_new + (a - b) * bo + (a + b) * bi) * (R(1) / (a + b));
+  tp = er_new + bt_new;
+  tm = er_new - bt_new;
+}
+
+template <class R, int M, class FS>
+QDS_HD void tt_update(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
+                      C<R> &tp, C<R> &tm) {
+  const int c = t.x0 + lx, j = t.r0 + lr;
+  if (j == 0 && k != 1) { tp = zero<R>(); tm = zero<R>(); return; }
+  C<R> sp = zero<R>(), sm = zero<R>();
+  for (int side = 0; side < 2; side++) {
+    const int lf = side == 0 ? lx : lx - 1;  // + from face c, - from face c-1
+    if (!t.face_ok(t.x0 + lf)) continue;
+    C<R> g, p;
+    if (j == 0) {
+      g = -(R(2) * t.idr) * fs.bx(k, lf, lr) - fs.jt(k, lf, lr);
+      p = imul(t.idr, fs.ex(k, lf, lr + 1) - fs.ex(k, lf, lr));
+    } else {
+      g = -t.idr * (fs.bx(k, lf, lr) - fs.bx(k, lf, lr - 1)) - fs.jt(k, lf, lr);
+      p = imul(R(k) / (R(j) * t.dr), fs.ex(k, lf, lr));
+    }
+    if (side == 0) sp = g + p; else sm = g - p;
+  }
+  tp = t.cell(grp + TTP, k, c + 1, j) + t.h * sp;
+  tm = t.cell(grp + TTM, k, c - 1, j) + t.h * sm;
+}
+
+
+// ---------------------------------------------------------------------------
+// Axion source and Klein-Gordon operator at face w, half row j, time n:
+//   S_a^(m) = sum_alpha C_m{E_alpha, B_alpha}  (Eqs. source_mode_zero/_m),
+//   Gamma_a = (1/r) d/dr (r dphi/dr) - m^2 phi / r^2 - m_a^2 phi + g S_a.
+// Every field component is averaged onto (x_{w+1/2}, r_{j+1/2}); E_x and B_x
+// also over the levels n -+ 1/2.  Beyond the outermost half row the
+// exterior phi comes from the outgoing condition (d_t + c d_r) phi = 0
+// centred at r_J (Eq. axion_r_ghost) with d_t phi taken half a step back.
+// ---------------------------------------------------------------------------
+template <class R, int M>
+QDS_HD void source_point(const Tile<R, M> &t, int lx, int lr) {
+  const int w = t.x0 + lx, j = t.r0 + lr;
+  if (!t.face_ok(w) || j < 0 || j >= t.nr) {
+    for (int k = 0; k < M; k++) t.sG(k, lx, lr) = zero<R>();
+    return;
+  }
+  const bool top = (j == t.J);
+  C<R> eX[M], bX[M], eR[M], bR[M], eT[M], bT[M];
+#pragma unroll
+  for (int k = 0; k < M; k++) {
+    C<R> eo = t.face(EX, k, w, j), en = t.sA(0, k, lx, lr), eo1, en1;
+    if (!top) { eo1 = t.face(EX, k, w, j + 1); en1 = t.sA(0, k, lx, lr + 1); }
+    else if (t.closed) { eo1 = zero<R>(); en1 = zero<R>(); }
+    else { eo1 = eo; en1 = en; }
+    eX[k] = R(0.25) * (eo + eo1 + en + en1);
+    bX[k] = R(0.5) * (t.face(BX, k, w, j) + t.sA(1, k, lx, lr));
+    eR[k] = R(0.5) * (t.Er(0, k, w, j) + t.Er(0, k, w + 1, j));
+    bT[k] = R(0.5) * (t.Bt(0, k, w, j) + t.Bt(0, k, w + 1, j));
+    C<R> et = R(0.5) * (t.Et(0, k, w, j) + t.Et(0, k, w + 1, j));
+    C<R> br = R(0.5) * (t.Br(0, k, w, j) + t.Br(0, k, w + 1, j));
+    C<R> et1, br1;
+    if (!top) {
+      et1 = R(0.5) * (t.Et(0, k, w, j + 1) + t.Et(0, k, w + 1, j + 1));
+      br1 = R(0.5) * (t.Br(0, k, w, j + 1) + t.Br(0, k, w + 1, j + 1));
+    } else if (t.closed) { et1 = zero<R>(); br1 = zero<R>(); }
+    else { et1 = et; br1 = br; }
+    eT[k] = R(0.5) * (et + et1);
+    bR[k] = R(0.5) * (br + br1);
+  }
+  const R idr2 = t.idr * t.idr;
+  const R rh = (R(j) + R(0.5)) * t.dr;
+#pragma unroll
+  for (int m = 0; m < M; m++) {
+    C<R> S = conv<R, M>(m, eX, bX) + conv<R, M>(m, eR, bR) + conv<R, M>(m, eT, bT);
+    S += t.srcv(t.I->sext, m, w, j);
+    C<R> pc = t.face(PHI, m, w, j);
+    C<R> pm = (j > 0) ? t.face(PHI, m, w, j - 1) : zero<R>();  // weight j = 0 on the axis
+    C<R> pp;
+    if (!top) pp = t.face(PHI, m, w, j + 1);
+    else if (t.closed) pp = pc;
+    else pp = t.face(PHI, m, w, j - 1) - (R(2) * t.dr * t.ih) * (pc - t.prev(m, w));
+    C<R> lap = (R(j + 1) * (pp - pc) - R(j) * (pc - pm)) * (idr2 / (R(j) + R(0.5)));
+    C<R> ga = lap - (R(m * m) / (rh * rh) + t.I->ma2) * pc + t.I->gs * S;
+    t.sG(m, lx, lr) = ga;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Axion current j_a = g (B0 d_t phi - E0 x grad phi) (Eqs. jax_mode,
+// jar_mode, jat_mode), with (d_theta phi)^(l) = -i l phi^(l):
+//   j_a,x at (x_{w+1/2}, r_j, t^n), j_a,r at (x_{w+1/2}, r_{j+1/2}, t^{n+1/2}),
+//   j_a,theta at (x_{w+1/2}, r_j, t^{n+1/2}).
+// d_t phi = (c/2)(T_a^+ + T_a^-), d_x phi = (1/2)(T_a^- - T_a^+) (Eq. phi_update).
+// Below the axis a scalar on half rows mirrors with parity (-1)^l; E_r and
+// B_theta below the axis follow the T_r ghost of Eq. axis_Tr.
+// ---------------------------------------------------------------------------
+template <class R, int M>
+QDS_HD void current_point(const Tile<R, M> &t, int lx, int lr) {
+  const int w = t.x0 + lx, j = t.r0 + lr;
+  if (!t.face_ok(w) || j < 0 || j >= t.nr) {
+    for (int k = 0; k < M; k++) for (int q = 2; q < 5; q++) t.sJ(q, k, lx, lr) = zero<R>();
+    return;
+  }
+  const bool top = (j == t.J);
+  const int j1 = top ? -1 : j + 1;  // row above, -1: beyond the last row
+  const R gj = t.I->gj;
+  const R ih = t.ih;
+  // ---- j_a,x at (w, j, n) ----
+  {
+    C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      const R par = (k & 1) ? R(-1) : R(1);
+      C<R> bx_hi = R(0.5) * (t.face(BX, k, w, j) + t.sA(1, k, lx, lr));
+      C<R> bx_lo = (j > 0) ? R(0.5) * (t.face(BX, k, w, j - 1) + t.sA(1, k, lx, lr - 1)) : par * bx_hi;
+      a1[k] = R(0.5) * (bx_lo + bx_hi);
+      C<R> dt_hi = R(0.125) * (t.cell(TAP, k, w, j) + t.cell(TAM, k, w, j) + t.cell(TAP, k, w + 1, j) + t.cell(TAM, k, w + 1, j) +
+                               t.sT(4, k, lx, lr) + t.sT(5, k, lx, lr) + t.sT(4, k, lx + 1, lr) + t.sT(5, k, lx + 1, lr));
+      C<R> dt_lo;
+      if (j > 0)
+        dt_lo = R(0.125) * (t.cell(TAP, k, w, j - 1) + t.cell(TAM, k, w, j - 1) + t.cell(TAP, k, w + 1, j - 1) + t.cell(TAM, k, w + 1, j - 1) +
+                            t.sT(4, k, lx, lr - 1) + t.sT(5, k, lx, lr - 1) + t.sT(4, k, lx + 1, lr - 1) + t.sT(5, k, lx + 1, lr - 1));
+      else dt_lo = par * dt_hi;
+      b1[k] = R(0.5) * (dt_lo + dt_hi);
+      C<R> er_hi = R(0.5) * (t.Er(0, k, w, j) + t.Er(0, k, w + 1, j)), er_lo;
+      if (j > 0) er_lo = R(0.5) * (t.Er(0, k, w, j - 1) + t.Er(0, k, w + 1, j - 1));
+      else if (k == 1) er_lo = imul(R(1), t.Et(0, k, w, 0) + t.Et(0, k, w + 1, 0)) - er_hi;
+      else er_lo = -er_hi;
+      a2[k] = R(0.5) * (er_lo + er_hi);
+      C<R> ph = t.face(PHI, k, w, j);
+      C<R> pl = (j > 0) ? t.face(PHI, k, w, j - 1) : par * ph;
+      if (j > 0) b2[k] = imul(-R(k) * R(0.5) / (R(j) * t.dr), pl + ph);
+      else b2[k] = (k == 1) ? imul(-t.idr, ph - pl) : zero<R>();
+      a3[k] = R(0.5) * (t.Et(0, k, w, j) + t.Et(0, k, w + 1, j));
+      b3[k] = t.idr * (ph - pl);
+    }
+#pragma unroll
+    for (int m = 0; m < M; m++)
+      t.sJ(2, m, lx, lr) = gj * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2) + conv<R, M>(m, a3, b3));
+  }
+  // time-(n+1/2) transverse fields: mean of level n (global) and n+1 (shared)
+  auto ER5 = [&](int k, int dl, int jj) -> C<R> {  // dl: 0 cell w, 1 cell w+1
+    C<R> o = t.Er(0, k, w + dl, jj);
+    C<R> nw = R(0.5) * (t.sT(0, k, lx + dl, jj - t.r0) + t.sT(1, k, lx + dl, jj - t.r0));
+    return R(0.5) * (o + nw);
+  };
+  auto BT5 = [&](int k, int dl, int jj) -> C<R> {
+    C<R> o = t.Bt(0, k, w + dl, jj);
+    C<R> nw = R(0.5) * (t.sT(0, k, lx + dl, jj - t.r0) - t.sT(1, k, lx + dl, jj - t.r0));
+    return R(0.5) * (o + nw);
+  };
+  auto ET5 = [&](int k, int dl, int jj) -> C<R> {
+    C<R> o = t.Et(0, k, w + dl, jj);
+    C<R> nw = R(0.5) * (t.sT(2, k, lx + dl, jj - t.r0) + t.sT(3, k, lx + dl, jj - t.r0));
+    return R(0.5) * (o + nw);
+  };
+  auto BR5 = [&](int k, int dl, int jj) -> C<R> {
+    C<R> o = t.Br(0, k, w + dl, jj);
+    C<R> nw = R(0.5) * (t.sT(2, k, lx + dl, jj - t.r0) - t.sT(3, k, lx + dl, jj - t.r0));
+    return R(0.5) * (o + nw);
+  };
+  auto DXPHI = [&](int k, int jj) -> C<R> {  // (1/2)(T_a^- - T_a^+) at n+1/2, mean of cells w, w+1
+    int l = jj - t.r0;
+    return R(0.25) * (t.sT(5, k, lx, l) - t.sT(4, k, lx, l) + t.sT(5, k, lx + 1, l) - t.sT(4, k, lx + 1, l));
+  };
+  // ---- j_a,r at (w, j + 1/2, n + 1/2) ----
+  {
+    C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      C<R> br_lo = R(0.5) * (BR5(k, 0, j) + BR5(k, 1, j));
+      C<R> et_lo = R(0.5) * (ET5(k, 0, j) + ET5(k, 1, j));
+      C<R> br_hi, et_hi;
+      if (j1 >= 0) { br_hi = R(0.5) * (BR5(k, 0, j1) + BR5(k, 1, j1)); et_hi = R(0.5) * (ET5(k, 0, j1) + ET5(k, 1, j1)); }
+      else if (t.closed) { br_hi = zero<R>(); et_hi = zero<R>(); }
+      else { br_hi = br_lo; et_hi = et_lo; }
+      a1[k] = R(0.5) * (br_lo + br_hi);
+      a2[k] = R(0.5) * (et_lo + et_hi);
+      C<R> po = t.face(PHI, k, w, j), pn = t.sP(k, lx, lr);
+      b1[k] = ih * (pn - po);
+      b2[k] = DXPHI(k, j);
+      C<R> ex_lo = t.sA(0, k, lx, lr), ex_hi;
+      if (j1 >= 0) ex_hi = t.sA(0, k, lx, lr + 1);
+      else ex_hi = t.closed ? zero<R>() : ex_lo;
+      a3[k] = R(0.5) * (ex_lo + ex_hi);
+      b3[k] = imul(-R(k) * R(0.5) / ((R(j) + R(0.5)) * t.dr), po + pn);
+    }
+#pragma unroll
+    for (int m = 0; m < M; m++)
+      t.sJ(3, m, lx, lr) = gj * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2) + conv<R, M>(m, a3, b3));
+  }
+  // ---- j_a,theta at (w, j, n + 1/2) ----
+  {
+    C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) {
+      const R par = (k & 1) ? R(-1) : R(1);
+      C<R> bt_hi = R(0.5) * (BT5(k, 0, j) + BT5(k, 1, j));
+      C<R> er_hi = R(0.5) * (ER5(k, 0, j) + ER5(k, 1, j));
+      C<R> bt_lo, er_lo;
+      if (j > 0) {
+        bt_lo = R(0.5) * (BT5(k, 0, j - 1) + BT5(k, 1, j - 1));
+        er_lo = R(0.5) * (ER5(k, 0, j - 1) + ER5(k, 1, j - 1));
+      } else if (k == 1) {
+        C<R> br0 = R(0.5) * (BR5(k, 0, 0) + BR5(k, 1, 0));
+        C<R> et0 = R(0.5) * (ET5(k, 0, 0) + ET5(k, 1, 0));
+        bt_lo = imul(R(-2), br0) - bt_hi;
+        er_lo = imul(R(2), et0) - er_hi;
+      } else {
+        bt_lo = -bt_hi;
+        er_lo = -er_hi;
+      }
+      a1[k] = R(0.5) * (bt_lo + bt_hi);
+      a3[k] = R(0.5) * (er_lo + er_hi);
+      C<R> dh = ih * (t.sP(k, lx, lr) - t.face(PHI, k, w, j));
+      C<R> dl = (j > 0) ? ih * (t.sP(k, lx, lr - 1) - t.face(PHI, k, w, j - 1)) : par * dh;
+      b1[k] = R(0.5) * (dl + dh);
+      a2[k] = t.sA(0, k, lx, lr);
+      C<R> pbh = R(0.5) * (t.face(PHI, k, w, j) + t.sP(k, lx, lr));
+      C<R> pbl = (j > 0) ? R(0.5) * (t.face(PHI, k, w, j - 1) + t.sP(k, lx, lr - 1)) : par * pbh;
+      b2[k] = t.idr * (pbh - pbl);
+      C<R> xh = DXPHI(k, j);
+      C<R> xl = (j > 0) ? DXPHI(k, j - 1) : par * xh;
+      b3[k] = R(0.5) * (xl + xh);
+    }
+#pragma unroll
+    for (int m = 0; m < M; m++)
+      t.sJ(4, m, lx, lr) = gj * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2) + conv<R, M>(m, a3, b3));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stage dispatcher.  The kernel runs every stage over all threads of the CTA
+// with a barrier in between; the host emulator runs them in the same order.
+// ---------------------------------------------------------------------------
+enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, N_STAGE };
+
+template <class R, int M>
+QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
+  const Geo &g = t.g;
+  const uint32_t fl = t.I->flags;
+  const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0;
+  if (st == ST_LEAP0) {
+    const int nxr = g.a_nx(), nrr = g.a_nr(), npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) {
+      const int lx = g.a_x0() + q / nrr, lr = g.a_r0() + q % nrr;
+      const int w = t.x0 + lx, j = t.r0 + lr;
+      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        C<R> ex = zero<R>(), bx = zero<R>();
+        if (live) {
+          ex = ex_update(t, 0, k, w, j, t.srcv(t.I->jx, k, w, j));
+          if (j < t.J || t.closed) bx = bx_interior(t, 0, k, w, j);
+          else {
+            C<R> jtf = R(0.5) * (t.srcv(t.I->jt, k, w, j) + t.srcv(t.I->jt, k, w + 1, j));
+            bx = bx_outer(t, 0, k, w, jtf, bx_interior(t, 0, k, w, j - 1));
+          }
+        }
+        t.sA(0, k, lx, lr) = ex;
+        t.sA(1, k, lx, lr) = bx;
+        if (t.owned(lx, lr)) { t.store(EX, k, w, j, ex); t.store(BX, k, w, j, bx); }
+      }
+    }
+  } else if (st == ST_SOURCE) {
+    if (!ax) return;
+    const int nxr = g.g_nx(), nrr = g.g_nr(), npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) source_point(t, g.g_x0() + q / nrr, g.g_r0() + q % nrr);
+  } else if (st == ST_SHIFT0) {
+    Faces0<R, M> fs{t};
+    const int xa = ax ? g.t_x0() : 0, nxr = ax ? g.t_nx() : g.TX;
+    const int ra = ax ? g.t_r0() : 0, nrr = ax ? g.t_nr() : g.TR;
+    const int npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) {
+      const int lx = xa + q / nrr, lr = ra + q % nrr;
+      const int c = t.x0 + lx, j = t.r0 + lr;
+      const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
+      const bool own = t.owned(lx, lr);
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        C<R> tp = zero<R>(), tm = zero<R>(), up = zero<R>(), um = zero<R>();
+        C<R> ap = zero<R>(), am = zero<R>();
+        if (live) {
+          if (j < t.J || t.closed) tr_interior(t, fs, 0, k, lx, lr, tp, tm);
+          else {
+            C<R> ip, im_;
+            tr_interior(t, fs, 0, k, lx, lr - 1, ip, im_);
+            tr_outer(t, fs, 0, k, lx, R(0.5) * (ip - im_), lr, tp, tm);
+          }
+          tt_update(t, fs, 0, k, lx, lr, up, um);
+          if (ax) {
+            ap = t.cell(TAP, k, c - 1, j) + t.h * t.sG(k, lx - 1, lr);
+            am = t.cell(TAM, k, c + 1, j) + t.h * t.sG(k, lx, lr);
+          }
+        }
+        if (ax) {
+          t.sT(0, k, lx, lr) = tp; t.sT(1, k, lx, lr) = tm;
+          t.sT(2, k, lx, lr) = up; t.sT(3, k, lx, lr) = um;
+          t.sT(4, k, lx, lr) = ap; t.sT(5, k, lx, lr) = am;
+        }
+        if (own) {
+          t.store(TRP, k, c, j, tp); t.store(TRM, k, c, j, tm);
+          t.store(TTP, k, c, j, up); t.store(TTM, k, c, j, um);
+          if (ax) { t.store(TAP, k, c, j, ap); t.store(TAM, k, c, j, am); }
+        }
+      }
+    }
+  } else if (st == ST_PHI) {
+    if (!ax) return;
+    const int nxr = g.p_nx(), nrr = g.p_nr(), npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) {
+      const int lx = g.p_x0() + q / nrr, lr = g.p_r0() + q % nrr;
+      const int w = t.x0 + lx, j = t.r0 + lr;
+      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        C<R> v = zero<R>();
+        if (live)
+          v = t.face(PHI, k, w, j) + (R(0.25) * t.h) * (t.sT(5, k, lx + 1, lr) + t.sT(5, k, lx, lr) +
+                                                       t.sT(4, k, lx + 1, lr) + t.sT(4, k, lx, lr));
+        t.sP(k, lx, lr) = v;
+        if (t.owned(lx, lr)) {
+          t.store(PHI, k, w, j, v);
+          if (j == t.J) t.store_prev(k, w, live ? t.face(PHI, k, w, j) : zero<R>());
+        }
+      }
+    }
+  } else if (st == ST_CURRENT) {
+    if (!ar) return;
+    const int nxr = g.j_nx(), nrr = g.j_nr(), npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) current_point(t, g.j_x0() + q / nrr, g.j_r0() + q % nrr);
+  } else if (st == ST_LEAP1) {
+    if (!ar) return;
+    const int nxr = g.j_nx(), nrr = g.j_nr(), npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) {
+      const int lx = g.j_x0() + q / nrr, lr = g.j_r0() + q % nrr;
+      const int w = t.x0 + lx, j = t.r0 + lr;
+      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        C<R> ex = zero<R>(), bx = zero<R>();
+        if (live) {
+          ex = ex_update(t, 9, k, w, j, t.sJ(2, k, lx, lr));
+          if (j < t.J || t.closed) bx = bx_interior(t, 9, k, w, j);
+          else bx = bx_outer(t, 9, k, w, t.sJ(4, k, lx, lr), bx_interior(t, 9, k, w, j - 1));
+        }
+        t.sJ(0, k, lx, lr) = ex;
+        t.sJ(1, k, lx, lr) = bx;
+        if (t.owned(lx, lr)) { t.store(EX1, k, w, j, ex); t.store(BX1, k, w, j, bx); }
+      }
+    }
+  } else if (st == ST_SHIFT1) {
+    if (!ar) return;
+    Faces1<R, M> fs{t};
+    const int npt = g.TX * g.TR;
+    for (int q = tid; q < npt; q += nth) {
+      const int lx = q / g.TR, lr = q % g.TR;
+      if (!t.owned(lx, lr)) continue;
+      const int c = t.x0 + lx, j = t.r0 + lr;
+#pragma unroll
+      for (int k = 0; k < M; k++) {
+        C<R> tp, tm, up, um;
+        if (j < t.J || t.closed) tr_interior(t, fs, 9, k, lx, lr, tp, tm);
+        else {
+          C<R> ip, im_;
+          tr_interior(t, fs, 9, k, lx, lr - 1, ip, im_);
+          tr_outer(t, fs, 9, k, lx, R(0.5) * (ip - im_), lr, tp, tm);
+        }
+        tt_update(t, fs, 9, k, lx, lr, up, um);
+        t.store(TRP1, k, c, j, tp); t.store(TRM1, k, c, j, tm);
+        t.store(TTP1, k, c, j, up); t.store(TTM1, k, c, j, um);
+      }
+    }
+  }
+}
+
+}  // namespace qds

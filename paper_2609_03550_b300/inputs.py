@@ -53,11 +53,11 @@ class Laser:
     x0: float
     pol: str = "y"
 
-    def amplitude(self, x, r):
+    def amplitude(self, x, r, xp=np):
         k = 2.0 * math.pi / self.lam
-        return (self.a0 * k * np.exp(-(r ** 2) / self.w0 ** 2)
-                * np.exp(-2.0 * math.log(2.0) * (x - self.x0) ** 2 / self.fwhm ** 2)
-                * np.cos(k * (x - self.x0)))
+        return (self.a0 * k * xp.exp(-(r ** 2) / self.w0 ** 2)
+                * xp.exp(-2.0 * math.log(2.0) * (x - self.x0) ** 2 / self.fwhm ** 2)
+                * xp.cos(k * (x - self.x0)))
 
 
 def add_lasers(buf, M, nx, nr, dr, lasers, x_offset=0.0):
@@ -65,14 +65,23 @@ def add_lasers(buf, M, nx, nr, dr, lasers, x_offset=0.0):
     E_theta - B_r = -2i A p with p = 1 (y) or i (z); T_r^- = T_theta^+ = 0."""
     if M < 2:
         return buf
-    F = view_fields(buf, M, nx, nr)
-    x = (np.arange(nx) + x_offset)[:, None]
-    r_half = ((np.arange(nr) + 0.5) * dr)[None, :]
-    r_int = (np.arange(nr) * dr)[None, :]
+    xp = np
+    if not isinstance(buf, np.ndarray):  # a torch tensor: build on its device
+        import torch as xp
+    F = buf[: N_FIELDS * M * nx * nr].reshape(N_FIELDS, M, nx, nr)
+    if xp is np:
+        x = (np.arange(nx) + x_offset)[:, None]
+        r_half = ((np.arange(nr) + 0.5) * dr)[None, :]
+        r_int = (np.arange(nr) * dr)[None, :]
+    else:
+        kw = dict(dtype=xp.float64, device=buf.device)
+        x = (xp.arange(nx, **kw) + x_offset)[:, None]
+        r_half = ((xp.arange(nr, **kw) + 0.5) * dr)[None, :]
+        r_int = (xp.arange(nr, **kw) * dr)[None, :]
     for L in lasers:
         p = 1.0 if L.pol == "y" else 1j
-        F[FIELDS.index("Trp"), 1] += 2.0 * p * L.amplitude(x, r_half)
-        F[FIELDS.index("Ttm"), 1] += -2j * p * L.amplitude(x, r_int)
+        F[FIELDS.index("Trp"), 1] += 2.0 * p * L.amplitude(x, r_half, xp)
+        F[FIELDS.index("Ttm"), 1] += -2j * p * L.amplitude(x, r_int, xp)
     return buf
 
 
@@ -128,9 +137,18 @@ class Workload:
     h: float = 1.0
     extra: dict = field(default_factory=dict)
 
-    def initial_state(self):
-        buf = empty_state(self.M, self.nx, self.nr)
+    def initial_state(self, device=None):
+        """Canonical complex128 initial state: numpy on the host, or a torch
+        tensor built on ``device``."""
+        if device is None:
+            buf = empty_state(self.M, self.nx, self.nr)
+        else:
+            import torch
+            buf = torch.zeros(state_size(self.M, self.nx, self.nr), dtype=torch.complex128, device=device)
         return add_lasers(buf, self.M, self.nx, self.nr, self.dr, self.lasers)
+
+    def cell_modes(self):
+        return self.nx * self.nr * self.M
 
 
 def vacuum_pulse():
@@ -142,35 +160,40 @@ def vacuum_pulse():
 
 
 def driven_wake():
-    """Wakefield-shaped driven run: nx=2048, nr=256, modes {0,1,2}, 2000 steps;
+    """Wakefield-shaped driven run: nx=2048, nr=256, modes {0,1,2}, 2000 steps,
+    dr = 5 dx (mode 2 needs dr >= 2.25 dx);
     m=1 pulse a0=2, lambda 32, waist 40 dr, FWHM 128, x0 = 1536; m=0 current
     of a Gaussian electron bunch (sigma_x 8, sigma_r 6 dr, density peak 0.05)
     256 cells behind the pulse moving at c, plus 1% uniform noise on j_x, j_r,
     j_theta redrawn every step (seed 1)."""
-    return Workload("driven_wake_2048x256_m3", 2048, 256, 3, 2.0, 2000,
-                    [Laser(2.0, 32.0, 80.0, 128.0, 1536.0, "y")],
-                    bunch=dict(rho=-0.05, sx=8.0, sr=12.0, x0=1280.0, noise=0.01, seed=1))
+    dr = 5.0
+    return Workload("driven_wake_2048x256_m3", 2048, 256, 3, dr, 2000,
+                    [Laser(2.0, 32.0, 40 * dr, 128.0, 1536.0, "y")],
+                    bunch=dict(rho=-0.05, sx=8.0, sr=6 * dr, x0=1280.0, noise=0.01, seed=1))
 
 
 def two_colour(nx=8192, nr=256, steps=20000):
     """Two-colour axion generation: EM modes {0,1} + axion + regenerated
-    fields, moving window; pulse 1 lambda 16 a0 0.5 (y), pulse 2 omega2 =
+    fields, moving window, dr = 5 dx; pulse 1 lambda 16 a0 0.5 (y), pulse 2 omega2 =
     0.8 omega1 (lambda 20) a0 0.5 (z), waist 32 dr, FWHM 4 lambda1, both at
     x0 = 0.75 nx; vacuum phase matching of omega1 - omega2 gives m_a = 0;
     g = 1e-6."""
     x0 = 0.75 * nx
-    return Workload(f"two_colour_{nx}x{nr}_m2", nx, nr, 2, 2.0, steps,
-                    [Laser(0.5, 16.0, 64.0, 64.0, x0, "y"), Laser(0.5, 20.0, 64.0, 64.0, x0, "z")],
+    dr = 5.0
+    return Workload(f"two_colour_{nx}x{nr}_m2", nx, nr, 2, dr, steps,
+                    [Laser(0.5, 16.0, 32 * dr, 64.0, x0, "y"), Laser(0.5, 20.0, 32 * dr, 64.0, x0, "z")],
                     axion=True, arem=True, moving_window=True, g=1e-6, m_a=0.0)
 
 
-def batched_scan(n=512, seed=2, steps=1000):
+def batched_scan(n=512, seed=2, steps=1000, dr=5.0):
     """Batched vacuum two-colour scan: per instance (draw order nx, nr, m_max,
     omega2/omega1, g from numpy PCG64(seed)): nx log-uniform [512, 4096], nr
     log-uniform [32, 256], m_max uniform {1,2,3} (modes 0..m_max, so the m=1
     pulses are always represented), omega2/omega1 uniform [0.5, 0.9], g
     log-uniform [1e-8, 1e-4]; m_a = 0; pulse 1 lambda 16 a0 0.5 (y), pulse 2
-    (z) a0 0.5, waist min(32 dr, R/4), FWHM 64, x0 = 0.75 nx; moving window."""
+    (z) a0 0.5, waist min(32 dr, R/4), FWHM 64, x0 = 0.75 nx; moving window;
+    dr = 5 dx (the paper's mesh ratio dx = lambda/10, dr = lambda/2; m_max = 3
+    needs dr >= 3.25 dx for stability)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for b in range(n):
@@ -179,7 +202,6 @@ def batched_scan(n=512, seed=2, steps=1000):
         mmax = int(rng.integers(1, 4))
         ratio = float(rng.uniform(0.5, 0.9))
         g = float(math.exp(rng.uniform(math.log(1e-8), math.log(1e-4))))
-        dr = 2.0
         w0 = min(32 * dr, 0.25 * nr * dr)
         x0 = 0.75 * nx
         lam1 = 16.0

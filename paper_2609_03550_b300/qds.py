@@ -1,0 +1,199 @@
+"""Python binding of the QDS field-step library (include/qds.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels
+of libqds.so.  PyTorch provides the device memory (state, sources, outputs)
+and the stream.  There is no CPU path: without the built library or a CUDA
+device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqds.so")
+
+AXION, AREM, MOVING_WINDOW, X_PERIODIC, R_CLOSED, FP32, SCALE_G = 1, 2, 4, 8, 16, 32, 64
+FIELDS = ("Trp", "Trm", "Ttp", "Ttm", "Ex", "Bx", "phi", "Tap", "Tam",
+          "Trp1", "Trm1", "Ttp1", "Ttm1", "Ex1", "Bx1")
+N_FIELDS = 15
+
+
+class QDSError(RuntimeError):
+    pass
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("nr", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+                ("modes", ctypes.POINTER(ctypes.c_int32)), ("dx", ctypes.c_double),
+                ("dr", ctypes.c_double), ("dt", ctypes.c_double), ("omega0", ctypes.c_double),
+                ("m_a", ctypes.c_double), ("g", ctypes.c_double), ("flags", ctypes.c_uint32)]
+
+
+class _Sources(ctypes.Structure):
+    _fields_ = [("jx", ctypes.c_void_p), ("jr", ctypes.c_void_p), ("jth", ctypes.c_void_p),
+                ("s_ext", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libqds.so; raises if it is missing (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise QDSError(f"{LIB_PATH} is not built; run paper_2609_03550_b300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER(_Params)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        H = ctypes.c_void_p
+        sig = {
+            "qds_state_bytes": (sz, [P]),
+            "qds_batch_state_bytes": (sz, [i, P]),
+            "qds_create": (i, [P, vp, sz, ctypes.POINTER(H)]),
+            "qds_batch_create": (i, [i, P, vp, sz, ctypes.POINTER(H)]),
+            "qds_set_state": (i, [H, vp, vp]),
+            "qds_get_state": (i, [H, vp, vp]),
+            "qds_set_state_i": (i, [H, i, vp, vp]),
+            "qds_get_state_i": (i, [H, i, vp, vp]),
+            "qds_step": (i, [H, ctypes.POINTER(_Sources), i, vp]),
+            "qds_diagnostics": (i, [H, ctypes.POINTER(ctypes.c_double), vp, vp]),
+            "qds_diagnostics_i": (i, [H, i, ctypes.POINTER(ctypes.c_double), vp, vp]),
+            "qds_num_instances": (i, [H]),
+            "qds_diagnostics_all": (i, [H, vp, vp]),
+            "qds_set_tile": (i, [H, i, i]),
+            "qds_get_tile": (i, [H, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+            "qds_free": (None, [H]),
+            "qds_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise QDSError(f"qds error {rc}: {lib().qds_last_error().decode()}")
+
+
+@dataclass
+class Params:
+    """Statement of one solve (Sec. 2): grid, retained modes, axion."""
+    nx: int
+    nr: int
+    n_modes: int
+    dr: float
+    dx: float = 1.0
+    m_a: float = 0.0
+    g: float = 0.0
+    flags: int = 0
+    omega0: float = 1.0
+
+    def c(self) -> _Params:
+        return _Params(self.nx, self.nr, self.n_modes, None, self.dx, self.dr, self.dx, self.omega0,
+                       self.m_a, self.g, self.flags)
+
+    @property
+    def fp32(self):
+        return bool(self.flags & FP32)
+
+    def state_elems(self):
+        return N_FIELDS * self.n_modes * self.nx * self.nr + self.n_modes * self.nx
+
+
+def state_bytes(p: Params) -> int:
+    return lib().qds_state_bytes(ctypes.byref(p.c()))
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class QDSSolver:
+    """One or several independent QDS solves on the current CUDA device."""
+
+    def __init__(self, params, device="cuda"):
+        if not torch.cuda.is_available():
+            raise QDSError("QDSSolver needs a CUDA device")
+        plist = params if isinstance(params, (list, tuple)) else [params]
+        self.params = list(plist)
+        L = lib()
+        arr = (_Params * len(plist))(*[p.c() for p in plist])
+        nbytes = L.qds_batch_state_bytes(len(plist), arr)
+        if nbytes == 0:
+            _check(L.qds_create(ctypes.byref(arr[0]), None, 0, ctypes.byref(ctypes.c_void_p())))
+            raise QDSError("invalid parameters")
+        self.device = torch.device(device)
+        self.state = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.state.data_ptr()
+        off = (-base) % 256
+        self._state_ptr = base + off
+        self._nbytes = nbytes
+        self.h = ctypes.c_void_p()
+        _check(L.qds_batch_create(len(plist), arr, ctypes.c_void_p(self._state_ptr), nbytes, ctypes.byref(self.h)))
+        self._keep = []
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.qds_free(self.h)
+            self.h = None
+
+    @property
+    def rdtype(self):
+        return torch.complex64 if self.params[0].fp32 else torch.complex128
+
+    def set_state(self, canon: torch.Tensor, i: int = 0, stream=None):
+        """canon: complex128 device tensor in the canonical layout (physical units)."""
+        p = self.params[i]
+        assert canon.dtype == torch.complex128 and canon.is_cuda and canon.numel() == p.state_elems()
+        canon = canon.contiguous()
+        _check(lib().qds_set_state_i(self.h, i, ctypes.c_void_p(canon.data_ptr()), _stream_ptr(stream)))
+        self._keep = [canon]
+
+    def get_state(self, i: int = 0, stream=None) -> torch.Tensor:
+        p = self.params[i]
+        out = torch.empty(p.state_elems(), dtype=torch.complex128, device=self.device)
+        _check(lib().qds_get_state_i(self.h, i, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def step(self, nsteps=1, jx=None, jr=None, jth=None, s_ext=None, stream=None):
+        def ptr(t):
+            if t is None:
+                return None
+            assert t.is_cuda and t.dtype == self.rdtype and t.is_contiguous()
+            return t.data_ptr()
+        src = _Sources(ptr(jx), ptr(jr), ptr(jth), ptr(s_ext))
+        self._src_keep = (jx, jr, jth, s_ext)
+        _check(lib().qds_step(self.h, ctypes.byref(src), int(nsteps), _stream_ptr(stream)))
+
+    def diagnostics(self, i: int = 0, profile=False, stream=None):
+        out = (ctypes.c_double * 4)()
+        prof = torch.zeros(self.params[i].nx, dtype=torch.float64, device=self.device) if profile else None
+        _check(lib().qds_diagnostics_i(self.h, i, out, None if prof is None else ctypes.c_void_p(prof.data_ptr()),
+                                       _stream_ptr(stream)))
+        d = dict(em0=out[0], axion=out[1], em1=out[2], cross=out[3])
+        if profile:
+            d["profile"] = prof
+        return d
+
+    def diagnostics_all(self, out=None, stream=None):
+        """Energies of every instance, [n, 4] float64 device tensor (async)."""
+        if out is None:
+            out = torch.empty((len(self.params), 4), dtype=torch.float64, device=self.device)
+        _check(lib().qds_diagnostics_all(self.h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def set_tile(self, tx, tr):
+        _check(lib().qds_set_tile(self.h, int(tx), int(tr)))
+
+    def tile(self):
+        a, b, c, d = (ctypes.c_int() for _ in range(4))
+        _check(lib().qds_get_tile(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+        return dict(tx=a.value, tr=b.value, ntiles=c.value, smem=d.value)

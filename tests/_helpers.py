@@ -1,0 +1,53 @@
+"""Shared test helpers (no method arithmetic)."""
+import numpy as np
+
+import oracle
+from paper_2609_03550_b300 import inputs as I
+
+GROUPS = (("em", 0, 6), ("axion", 6, 9), ("arem", 9, 15))
+
+
+def group_errors(got, ref, M, nx, nr):
+    """Relative L2 error per field group; phi_prev counts with the axion."""
+    n = M * nx * nr
+    out = {}
+    for name, a, b in GROUPS:
+        sg = got[a * n:b * n]
+        sr = ref[a * n:b * n]
+        if name == "axion":
+            sg = np.concatenate([sg, got[15 * n:]])
+            sr = np.concatenate([sr, ref[15 * n:]])
+        den = np.linalg.norm(sr)
+        out[name] = (np.linalg.norm(sg - sr) / den) if den > 0 else np.linalg.norm(sg)
+    return out
+
+
+def oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=(None, None, None, None)):
+    st = oracle.State(M, nx, nr, buf)
+    oracle.step(dict(nx=nx, nr=nr, M=M, h=1.0, dr=dr, g=g, m_a=m_a, flags=flags & 31), st, *src, nsteps=nsteps)
+    return st.buf
+
+
+def parity_cases():
+    """(M, flags) combinations covering every boundary mode."""
+    out = []
+    for M in (1, 2, 3, 4):
+        for flags in (0, oracle.AXION, oracle.AXION | oracle.AREM,
+                      oracle.AXION | oracle.AREM | oracle.MOVING_WINDOW,
+                      oracle.AXION | oracle.AREM | oracle.X_PERIODIC,
+                      oracle.AXION | oracle.AREM | oracle.R_CLOSED):
+            out.append((M, flags))
+    return out
+
+
+def random_case(seed, M, nx, nr):
+    rng = np.random.default_rng(seed)
+    buf = I.random_state(rng, M, nx, nr)
+    src = I.random_sources(rng, M, nx, nr, 0.3)
+    sext = 0.2 * (rng.standard_normal((M, nx, nr)) + 1j * rng.standard_normal((M, nx, nr)))
+    sext[0] = sext[0].real
+    return buf, src + [np.ascontiguousarray(sext)]
+
+
+def stable_dr(M, m_a=0.0):
+    return max(1.5, (M - 1) + 0.25) * (1 + m_a)

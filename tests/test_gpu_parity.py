@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  FP64: relative L2 <= 1e-12 per field group.  FP32
+(axion and regenerated fields carried as phi/g, E1/g^2): relative L2 <= 1e-5
+for the fields and <= 1e-4 for the axion group."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2609_03550_b300 import inputs as I  # noqa: E402
+from paper_2609_03550_b300 import qds as Q  # noqa: E402
+from tests._helpers import group_errors, oracle_run, parity_cases, random_case, stable_dr  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=None):
+    p = Q.Params(nx, nr, M, dr, g=g, m_a=m_a, flags=flags)
+    s = Q.QDSSolver(p, device=DEV)
+    if tile:
+        s.set_tile(*tile)
+    s.set_state(torch.from_numpy(buf).to(DEV))
+    kw = {}
+    if src is not None:
+        dt = s.rdtype
+        for name, a in zip(("jx", "jr", "jth", "s_ext"), src):
+            if a is not None:
+                kw[name] = torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(dt)
+    s.step(nsteps, **kw)
+    torch.cuda.synchronize()
+    return s.get_state().cpu().numpy(), s
+
+
+@pytest.mark.parametrize("M,flags", parity_cases())
+def test_fp64_parity_random_states(M, flags):
+    nx, nr = 37, 21
+    dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
+    buf, src = random_case(M * 100 + flags, M, nx, nr)
+    for nsteps in (3, 20):  # 20 steps replays a captured graph
+        ref = oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src)
+        got, _ = gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src)
+        for name, e in group_errors(got, ref, M, nx, nr).items():
+            assert e < 1e-12, (nsteps, name, e)
+
+
+@pytest.mark.parametrize("tile", [(4, 8), (8, 16), (16, 8), (3, 5)])
+def test_fp64_parity_tile_shapes(tile):
+    M, nx, nr, flags = 3, 45, 27, 1 | 2 | 4
+    dr = stable_dr(M)
+    buf, src = random_case(11, M, nx, nr)
+    ref = oracle_run(buf, M, nx, nr, dr, flags, 5, g=0.2, src=src)
+    got, _ = gpu_run(buf, M, nx, nr, dr, flags, 5, g=0.2, src=src, tile=tile)
+    for name, e in group_errors(got, ref, M, nx, nr).items():
+        assert e < 1e-12, (name, e)
+
+
+@pytest.mark.parametrize("M", [2, 3, 4])
+def test_fp32_scaled_parity(M):
+    nx, nr = 64, 24
+    dr, g = stable_dr(M), 1e-6
+    flags = 1 | 2 | 4
+    buf, src = random_case(70 + M, M, nx, nr)
+    n = M * nx * nr
+    buf[6 * n:9 * n] *= g
+    buf[15 * n:] *= g
+    buf[9 * n:15 * n] *= g * g
+    src[3] = None
+    ref = oracle_run(buf, M, nx, nr, dr, flags, 10, g=g, src=src)
+    got, _ = gpu_run(buf, M, nx, nr, dr, flags | Q.FP32, 10, g=g, src=src)
+    e = group_errors(got, ref, M, nx, nr)
+    assert e["em"] < 1e-5 and e["arem"] < 1e-5 and e["axion"] < 1e-4, e
+
+
+def test_vacuum_pulse_full_run():
+    wl = I.vacuum_pulse()
+    buf = wl.initial_state()
+    flags = Q.MOVING_WINDOW
+    ref = oracle_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, wl.steps)
+    got, s = gpu_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, wl.steps)
+    e = group_errors(got, ref, wl.M, wl.nx, wl.nr)
+    assert e["em"] < 1e-12, e
+
+
+def test_driven_wake_with_per_step_currents():
+    wl = I.driven_wake()
+    wl.nx, wl.nr = 512, 64          # trimmed box, bunch and pulse inside
+    wl.dr = 5.0
+    wl.lasers[0].x0 = 384.0
+    wl.lasers[0].w0 = 100.0
+    wl.bunch["x0"] = 128.0
+    nsteps = 30
+    buf = wl.initial_state()
+    ref_state = __import__("oracle").State(wl.M, wl.nx, wl.nr, buf)
+    import oracle
+    for prec, tol in ((0, 1e-12), (Q.FP32, 1e-5)):
+        st = oracle.State(wl.M, wl.nx, wl.nr, buf)
+        p = Q.Params(wl.nx, wl.nr, wl.M, wl.dr, flags=prec)
+        s = Q.QDSSolver(p, device=DEV)
+        s.set_state(torch.from_numpy(buf).to(DEV))
+        for n in range(nsteps):
+            jx, jr, jt = I.bunch_currents(wl, n)
+            oracle.step(dict(nx=wl.nx, nr=wl.nr, M=wl.M, h=1.0, dr=wl.dr, flags=0), st, jx, jr, jt)
+            tj = [torch.from_numpy(a).to(DEV).to(s.rdtype) for a in (jx, jr, jt)]
+            s.step(1, jx=tj[0], jr=tj[1], jth=tj[2])
+        torch.cuda.synchronize()
+        got = s.get_state().cpu().numpy()
+        e = group_errors(got, st.buf, wl.M, wl.nx, wl.nr)
+        assert e["em"] < tol, (prec, e)
+    del ref_state
+
+
+@pytest.mark.parametrize("prec", [0, Q.FP32])
+def test_two_colour_reduced(prec):
+    wl = I.two_colour(nx=512, nr=64)
+    wl.M, wl.dr = 3, 5.0
+    for L in wl.lasers:
+        L.w0, L.x0 = 80.0, 384.0
+    flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
+    buf = wl.initial_state()
+    ref = oracle_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, 100, g=wl.g)
+    got, s = gpu_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags | prec, 100, g=wl.g)
+    e = group_errors(got, ref, wl.M, wl.nx, wl.nr)
+    if prec == 0:
+        assert max(e.values()) < 1e-12, e
+    else:
+        assert e["em"] < 1e-5 and e["arem"] < 1e-5 and e["axion"] < 1e-4, e
+
+
+def test_diagnostics_match_oracle():
+    import oracle
+    M, nx, nr = 3, 40, 18
+    dr = stable_dr(M)
+    buf, _ = random_case(5, M, nx, nr)
+    flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
+    got, s = gpu_run(buf, M, nx, nr, dr, flags, 7, g=0.5, m_a=0.2)
+    st = oracle.State(M, nx, nr, buf)
+    pp = dict(nx=nx, nr=nr, M=M, h=1.0, dr=dr, g=0.5, m_a=0.2, flags=flags)
+    oracle.step(pp, st, nsteps=7)
+    d_ref = oracle.diagnostics(pp, st, profile=True)
+    d_got = s.diagnostics(profile=True)
+    for k in ("em0", "axion", "em1", "cross"):
+        assert abs(d_got[k] - d_ref[k]) <= 1e-12 * abs(d_ref[k]), k
+    prof = d_got["profile"].cpu().numpy()
+    assert np.allclose(prof, d_ref["profile"], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("which", ["driven_wake", "two_colour"])
+def test_full_size_first_steps(which):
+    """Full-size grids of the benchmark workloads, in the launch
+    configuration the benchmark uses, three steps against the oracle."""
+    import oracle
+    if which == "driven_wake":
+        wl = I.driven_wake()
+        wl.dr = 5.0
+        flags = 0
+    else:
+        wl = I.two_colour()
+        wl.dr = 5.0
+        flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
+    buf = wl.initial_state()
+    ref = oracle_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, 3, g=wl.g)
+    for prec in (0, Q.FP32):
+        got, _ = gpu_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags | prec, 3, g=wl.g)
+        e = group_errors(got, ref, wl.M, wl.nx, wl.nr)
+        lim = 1e-12 if prec == 0 else 1e-5
+        assert e["em"] < lim, (prec, e)
+        if flags & Q.AXION:
+            assert e["axion"] < (1e-12 if prec == 0 else 1e-4), (prec, e)
+
+
+def test_batched_uneven_instances_match_single_runs():
+    import oracle
+    wls = I.batched_scan(n=512, steps=20)[:6]
+    for wl in wls:
+        wl.dr = 5.0
+    flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
+    params = [Q.Params(w.nx, w.nr, w.M, w.dr, g=w.g, flags=flags) for w in wls]
+    s = Q.QDSSolver(params, device=DEV)
+    bufs = [w.initial_state() for w in wls]
+    for i, b in enumerate(bufs):
+        s.set_state(torch.from_numpy(b).to(DEV), i=i)
+    s.step(20)
+    torch.cuda.synchronize()
+    for i, (w, b) in enumerate(zip(wls, bufs)):
+        ref = oracle_run(b, w.M, w.nx, w.nr, w.dr, flags, 20, g=w.g)
+        got = s.get_state(i).cpu().numpy()
+        e = group_errors(got, ref, w.M, w.nx, w.nr)
+        assert e["em"] < 1e-12 and e["axion"] < 1e-12, (i, e)
