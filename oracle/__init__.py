@@ -21,27 +21,30 @@ FIELDS = ("Trp", "Trm", "Ttp", "Ttm", "Ex", "Bx", "phi", "Tap", "Tam",
           "Trp1", "Trm1", "Ttp1", "Ttm1", "Ex1", "Bx1")
 N_FIELDS = len(FIELDS)
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(extended=False):
+    """The FP64 build, or the long double build (``extended``) that serves
+    as the parity reference where the paper's E.B form cancels."""
+    if extended not in _libs:
+        path = _build.build(extended=extended)
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         L.ora_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                dp, dp, dp, dp, dp]
         L.ora_step.restype = ctypes.c_int
+        L.ora_step_n.argtypes = L.ora_step.argtypes + [ctypes.c_int]
+        L.ora_step_n.restype = ctypes.c_int
         L.ora_diagnostics.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, dp, dp, dp]
         L.ora_diagnostics.restype = ctypes.c_int
         L.ora_mode_conv.argtypes = [ctypes.c_int, dp, dp, dp]
         L.ora_mode_conv.restype = None
-        _lib = L
-    return _lib
+        _libs[extended] = L
+    return _libs[extended]
 
 
 def _ptr(a):
@@ -75,18 +78,19 @@ class State:
         return State(self.M, self.nx, self.nr, self.buf)
 
 
-def step(p, st, jx=None, jr=None, jt=None, s_ext=None, nsteps=1):
+def step(p, st, jx=None, jr=None, jt=None, s_ext=None, nsteps=1, extended=False):
     """Advance ``st`` in place by ``nsteps`` steps with constant sources.
 
     ``p``: dict with nx, nr, M, h, dr, m_a, g, flags.  Sources are complex128
-    arrays [M, nx, nr] at the native staggered positions (or None)."""
-    L = lib()
+    arrays [M, nx, nr] at the native staggered positions (or None).  With
+    ``extended`` the steps run in long double (state rounded to complex128
+    only on return)."""
+    L = lib(extended)
     srcs = [None if a is None else np.ascontiguousarray(a, np.complex128) for a in (jx, jr, jt, s_ext)]
-    for _ in range(nsteps):
-        rc = L.ora_step(p["nx"], p["nr"], p["M"], p["h"], p["dr"], p.get("m_a", 0.0), p.get("g", 0.0),
-                        p.get("flags", 0), _ptr(st.buf), *[_ptr(a) for a in srcs])
-        if rc != 0:
-            raise RuntimeError(f"ora_step failed: {rc}")
+    rc = L.ora_step_n(p["nx"], p["nr"], p["M"], p["h"], p["dr"], p.get("m_a", 0.0), p.get("g", 0.0),
+                      p.get("flags", 0), _ptr(st.buf), *[_ptr(a) for a in srcs], int(nsteps))
+    if rc != 0:
+        raise RuntimeError(f"ora_step failed: {rc}")
     return st
 
 

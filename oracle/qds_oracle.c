@@ -43,7 +43,20 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef ORA_EXTENDED
+/* Extended-precision build (liboracle_ext.so): the same arithmetic with
+ * long double, used as the reference for FP64 parity where the paper's
+ * form of E.B subtracts nearly equal products. */
+typedef long double complex cplx;
+#define RE(z) creall(z)
+#define IM(z) cimagl(z)
+#define CONJ(z) conjl(z)
+#else
 typedef double complex cplx;
+#define RE(z) creal(z)
+#define IM(z) cimag(z)
+#define CONJ(z) conj(z)
+#endif
 
 enum {
   ORA_AXION = 1,          /* advance phi, T_a (Sec. 2.2)                     */
@@ -97,7 +110,7 @@ static inline double r_half(const P *p, int j) { return (j + 0.5) * p->dr; }
 static cplx mode_conv(int M, int m, const cplx *A, const cplx *B) {
   if (m == 0) {
     cplx s = A[0] * B[0];
-    for (int k = 1; k < M; k++) s += 0.5 * creal(A[k] * conj(B[k]));
+    for (int k = 1; k < M; k++) s += 0.5 * RE(A[k] * CONJ(B[k]));
     return s;
   }
   cplx s = 0;
@@ -106,19 +119,24 @@ static cplx mode_conv(int M, int m, const cplx *A, const cplx *B) {
       if (k + l == m) s += A[k] * B[l];
   for (int k = 0; k < M; k++)          /* k - l = m : A^(k) B^(-l) */
     for (int l = 0; l < M; l++)
-      if (k - l == m) s += A[k] * conj(B[l]);
+      if (k - l == m) s += A[k] * CONJ(B[l]);
   for (int k = 0; k < M; k++)          /* l - k = m : A^(-k) B^(l) */
     for (int l = 0; l < M; l++)
-      if (l - k == m) s += conj(A[k]) * B[l];
+      if (l - k == m) s += CONJ(A[k]) * B[l];
   return 0.5 * s;
 }
 
 /* exported for the quadrature pin */
 void ora_mode_conv(int M, const double *A, const double *B, double *out) {
+  cplx a[8], b[8];
+  for (int k = 0; k < M && k < 8; k++) {
+    a[k] = A[2 * k] + I * A[2 * k + 1];
+    b[k] = B[2 * k] + I * B[2 * k + 1];
+  }
   for (int m = 0; m < M; m++) {
-    cplx r = mode_conv(M, m, (const cplx *)A, (const cplx *)B);
-    out[2 * m] = creal(r);
-    out[2 * m + 1] = cimag(r);
+    cplx r = mode_conv(M, m, a, b);
+    out[2 * m] = (double)RE(r);
+    out[2 * m + 1] = (double)IM(r);
   }
 }
 
@@ -327,6 +345,7 @@ static void em_step(const P *p, const cplx *Trp, const cplx *Trm,
  * The full step.
  * ---------------------------------------------------------------------- */
 static cplx *fld(cplx *base, const P *p, int f) { return base + (size_t)f * p->plane; }
+static cplx *to_cplx(const double *d, size_t n);
 
 /* Value beyond the last row used by averages that reach one row past it:
  * zero-gradient for the open boundary, zero for the conducting wall. */
@@ -343,17 +362,13 @@ static inline cplx row_or_edge(const P *p, const cplx *a, int m, int c, int j, i
  * (the parity reading of Sec. 2.3, consistent with Eq. axis_Ttheta). */
 static inline double parity(int m) { return (m & 1) ? -1.0 : 1.0; }
 
-int ora_step(int nx, int nr, int M, double h, double dr, double m_a, double g,
-             int flags, double *state_d, const double *jx_d, const double *jr_d,
-             const double *jt_d, const double *sext_d) {
-  if (nx < 4 || nr < 4 || M < 1 || M > 8) return -1;
-  P pp = {nx, nr, M, h, dr, m_a, g, flags, (size_t)M * nx * nr};
-  const P *p = &pp;
+static int step_once(const P *p, cplx *S, const cplx *jx, const cplx *jrc, const cplx *jtc,
+                     const cplx *sext) {
+  const int nx = p->nx, nr = p->nr, M = p->M;
+  const double h = p->h, dr = p->dr, m_a = p->m_a, g = p->g;
+  const int flags = p->flags;
   const size_t pl = p->plane;
-  cplx *S = (cplx *)state_d;
   cplx *phiprev = S + (size_t)N_FIELDS * pl; /* [M][nx]: phi at the outer row, time n-1 */
-  const cplx *jx = (const cplx *)jx_d, *jrc = (const cplx *)jr_d, *jtc = (const cplx *)jt_d;
-  const cplx *sext = (const cplx *)sext_d;
   const int J = nr - 1;
   const int closed = (flags & ORA_R_CLOSED) != 0;
 
@@ -625,6 +640,40 @@ int ora_step(int nx, int nr, int M, double h, double dr, double m_a, double g,
   return 0;
 }
 
+static cplx *to_cplx(const double *d, size_t n) {
+  if (!d) return NULL;
+  cplx *z = malloc(n * sizeof(cplx));
+  for (size_t q = 0; q < n; q++) z[q] = d[2 * q] + I * d[2 * q + 1];
+  return z;
+}
+
+/* nsteps steps with constant sources; the state is held in the working
+ * precision between the steps of one call. */
+int ora_step_n(int nx, int nr, int M, double h, double dr, double m_a, double g,
+               int flags, double *state_d, const double *jx_d, const double *jr_d,
+               const double *jt_d, const double *sext_d, int nsteps) {
+  if (nx < 4 || nr < 4 || M < 1 || M > 8 || nsteps < 0) return -1;
+  P pp = {nx, nr, M, h, dr, m_a, g, flags, (size_t)M * nx * nr};
+  const size_t ns = (size_t)N_FIELDS * pp.plane + (size_t)M * nx;
+  cplx *S = to_cplx(state_d, ns);
+  cplx *jx = to_cplx(jx_d, pp.plane), *jr = to_cplx(jr_d, pp.plane);
+  cplx *jt = to_cplx(jt_d, pp.plane), *se = to_cplx(sext_d, pp.plane);
+  int rc = 0;
+  for (int n = 0; n < nsteps && rc == 0; n++) rc = step_once(&pp, S, jx, jr, jt, se);
+  for (size_t q = 0; q < ns; q++) {
+    state_d[2 * q] = (double)RE(S[q]);
+    state_d[2 * q + 1] = (double)IM(S[q]);
+  }
+  free(S); free(jx); free(jr); free(jt); free(se);
+  return rc;
+}
+
+int ora_step(int nx, int nr, int M, double h, double dr, double m_a, double g,
+             int flags, double *state_d, const double *jx_d, const double *jr_d,
+             const double *jt_d, const double *sext_d) {
+  return ora_step_n(nx, nr, M, h, dr, m_a, g, flags, state_d, jx_d, jr_d, jt_d, sext_d, 1);
+}
+
 /* ------------------------------------------------------------------------
  * Diagnostics.  Volume integrals use the azimuthal inner product of
  * Eq. fourier_decomp: int_0^{2pi} F G dtheta = 2 pi [F0 G0 + (1/2) sum_{m>0}
@@ -652,10 +701,10 @@ static double em_energy(const P *p, const cplx *S, int g0, double *prof) {
         cplx er = 0.5 * (Trp[q] + Trm[q]), bt = 0.5 * (Trp[q] - Trm[q]);
         cplx et = 0.5 * (Ttp[q] + Ttm[q]), br = 0.5 * (Ttp[q] - Ttm[q]);
         double w = wmode(m);
-        col += w * (r_half(p, j) * (creal(er * conj(er)) + creal(bt * conj(bt))) +
-                    r_star(p, j) * (creal(et * conj(et)) + creal(br * conj(br))));
-        lon += w * (r_star(p, j) * creal(Ex[q] * conj(Ex[q])) +
-                    r_half(p, j) * creal(Bx[q] * conj(Bx[q])));
+        col += w * (r_half(p, j) * (RE(er * CONJ(er)) + RE(bt * CONJ(bt))) +
+                    r_star(p, j) * (RE(et * CONJ(et)) + RE(br * CONJ(br))));
+        lon += w * (r_star(p, j) * RE(Ex[q] * CONJ(Ex[q])) +
+                    r_half(p, j) * RE(Bx[q] * CONJ(Bx[q])));
       }
     if (prof) prof[i] = 0.5 * tpi * p->dr * col;
     tot += 0.5 * tpi * p->dr * p->h * (col + lon);
@@ -667,7 +716,7 @@ int ora_diagnostics(int nx, int nr, int M, double h, double dr, double m_a, doub
                     int flags, const double *state_d, double *out, double *prof) {
   P pp = {nx, nr, M, h, dr, m_a, g, flags, (size_t)M * nx * nr};
   const P *p = &pp;
-  const cplx *S = (const cplx *)state_d;
+  cplx *S = to_cplx(state_d, (size_t)N_FIELDS * pp.plane + (size_t)M * nx);
   const double tpi = 2.0 * 3.14159265358979323846;
   out[0] = em_energy(p, S, F_TRP, prof);
   out[2] = em_energy(p, S, F_TRP1, NULL);
@@ -680,11 +729,11 @@ int ora_diagnostics(int nx, int nr, int M, double h, double dr, double m_a, doub
         size_t q = ix(p, m, i, j);
         double w = wmode(m), rh = r_half(p, j);
         /* (1/2)(|T_a^+|^2 + |T_a^-|^2) = |d_t phi|^2 + |d_x phi|^2 (Eq. T_axion_def) */
-        ua += w * rh * 0.5 * (creal(Tap[q] * conj(Tap[q])) + creal(Tam[q] * conj(Tam[q])));
-        ua += w * rh * ((double)(m * m) / (rh * rh) + m_a * m_a) * creal(phi[q] * conj(phi[q]));
+        ua += w * rh * 0.5 * (RE(Tap[q] * CONJ(Tap[q])) + RE(Tam[q] * CONJ(Tam[q])));
+        ua += w * rh * ((double)(m * m) / (rh * rh) + m_a * m_a) * RE(phi[q] * CONJ(phi[q]));
         if (j > 0) {
           cplx d = (phi[q] - phi[ix(p, m, i, j - 1)]) / dr;
-          ua += w * r_int(p, j) * creal(d * conj(d));
+          ua += w * r_int(p, j) * RE(d * CONJ(d));
         }
       }
   out[1] = 0.5 * tpi * dr * h * ua;
@@ -705,10 +754,11 @@ int ora_diagnostics(int nx, int nr, int M, double h, double dr, double m_a, doub
         cplx br1 = 0.5 * (fld((cplx *)b, p, F_TTP1)[q] - fld((cplx *)b, p, F_TTM1)[q]);
         cplx ex0 = fld((cplx *)a, p, F_EX)[q], ex1 = fld((cplx *)b, p, F_EX1)[q];
         cplx bx0 = fld((cplx *)a, p, F_BX)[q], bx1 = fld((cplx *)b, p, F_BX1)[q];
-        cr += w * (r_half(p, j) * creal(er0 * conj(er1) + bt0 * conj(bt1)) +
-                   r_star(p, j) * creal(et0 * conj(et1) + br0 * conj(br1)) +
-                   r_star(p, j) * creal(ex0 * conj(ex1)) + r_half(p, j) * creal(bx0 * conj(bx1)));
+        cr += w * (r_half(p, j) * RE(er0 * CONJ(er1) + bt0 * CONJ(bt1)) +
+                   r_star(p, j) * RE(et0 * CONJ(et1) + br0 * CONJ(br1)) +
+                   r_star(p, j) * RE(ex0 * CONJ(ex1)) + r_half(p, j) * RE(bx0 * CONJ(bx1)));
       }
   out[3] = tpi * dr * h * cr;
+  free(S);
   return 0;
 }

@@ -26,6 +26,12 @@
 #define QDS_CHECK(cond, what) ((void)0)
 #endif
 
+#if defined(__CUDACC__)
+#define QDS_NOINL __host__ __device__ __noinline__
+#else
+#define QDS_NOINL inline
+#endif
+
 namespace qds {
 
 template <class R>
@@ -191,7 +197,7 @@ QDS_HD C<R> conv(int m, const C<R> *A, const C<R> *B) {
 // algebraically the paper's average-plus-centred-difference form.
 // ---------------------------------------------------------------------------
 template <class R, int M>
-QDS_HD C<R> ex_update(const Tile<R, M> &t, int grp, int k, int w, int j, C<R> jx) {
+QDS_NOINL C<R> ex_update(const Tile<R, M> &t, int grp, int k, int w, int j, C<R> jx) {
   C<R> e0 = t.face(grp + EX, k, w, j);
   if (j == 0) {
     if (k != 0) return zero<R>();
@@ -208,7 +214,7 @@ QDS_HD C<R> ex_update(const Tile<R, M> &t, int grp, int k, int w, int j, C<R> jx
 }
 
 template <class R, int M>
-QDS_HD C<R> bx_interior(const Tile<R, M> &t, int grp, int k, int w, int j) {
+QDS_NOINL C<R> bx_interior(const Tile<R, M> &t, int grp, int k, int w, int j) {
   C<R> b0 = t.face(grp + BX, k, w, j);
   R rh = (R(j) + R(0.5)) * t.dr;
   C<R> elo = R(0.5) * (t.Et(grp, k, w, j) + t.Et(grp, k, w + 1, j));
@@ -221,7 +227,7 @@ QDS_HD C<R> bx_interior(const Tile<R, M> &t, int grp, int k, int w, int j) {
 // Outer half row J+1/2, Eq. em_r_open_bx by the box scheme over
 // [r_{J-1/2}, r_{J+1/2}] x [t^{n-1/2}, t^{n+1/2}], right side at (x_{w+1/2}, r_J, t^n).
 template <class R, int M>
-QDS_HD C<R> bx_outer(const Tile<R, M> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
+QDS_NOINL C<R> bx_outer(const Tile<R, M> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
   const int J = t.J;
   R rJ = R(J) * t.dr;
   C<R> dxbr = t.ih * (t.Br(grp, k, w + 1, J) - t.Br(grp, k, w, J));
@@ -278,7 +284,7 @@ struct Faces1 {
 // c.  Axis rules of Sec. 2.3 (Eq. axis_Ttheta; T_th^(m!=1) = 0 on the axis).
 // ---------------------------------------------------------------------------
 template <class R, int M, class FS>
-QDS_HD void tr_interior(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
+QDS_NOINL void tr_interior(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
                         C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   R rh = (R(j) + R(0.5)) * t.dr;
@@ -301,7 +307,7 @@ QDS_HD void tr_interior(const Tile<R, M> &t, const FS &fs, int grp, int k, int l
 // the box scheme of Eq. em_r_open_bt over [r_{J-1/2}, r_{J+1/2}] x [t^n, t^{n+1}]
 // with its right side from time-n fields.
 template <class R, int M, class FS>
-QDS_HD void tr_outer(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
+QDS_NOINL void tr_outer(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
                      int lr_J, C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, J = t.J;
   R rh = (R(J) + R(0.5)) * t.dr, rJ = R(J) * t.dr;
@@ -324,7 +330,7 @@ QDS_HD void tr_outer(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, 
 }
 
 template <class R, int M, class FS>
-QDS_HD void tt_update(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
+QDS_NOINL void tt_update(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
                       C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   if (j == 0 && k != 1) { tp = zero<R>(); tm = zero<R>(); return; }
@@ -357,7 +363,7 @@ QDS_HD void tt_update(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx,
 // centred at r_J (Eq. axion_r_ghost) with d_t phi taken half a step back.
 // ---------------------------------------------------------------------------
 template <class R, int M>
-QDS_HD void source_point(const Tile<R, M> &t, int lx, int lr) {
+QDS_NOINL void source_point(const Tile<R, M> &t, int lx, int lr) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) t.sG(k, lx, lr) = zero<R>();
@@ -418,7 +424,7 @@ QDS_HD void source_point(const Tile<R, M> &t, int lx, int lr) {
 // B_theta below the axis follow the T_r ghost of Eq. axis_Tr.
 // ---------------------------------------------------------------------------
 template <class R, int M>
-QDS_HD void current_point(const Tile<R, M> &t, int lx, int lr) {
+QDS_NOINL void current_point(const Tile<R, M> &t, int lx, int lr) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) for (int q = 2; q < 5; q++) t.sJ(q, k, lx, lr) = zero<R>();
@@ -579,7 +585,7 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
       const int lx = g.a_x0() + q / nrr, lr = g.a_r0() + q % nrr;
       const int w = t.x0 + lx, j = t.r0 + lr;
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> ex = zero<R>(), bx = zero<R>();
         if (live) {
@@ -609,7 +615,7 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
       const int c = t.x0 + lx, j = t.r0 + lr;
       const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
       const bool own = t.owned(lx, lr);
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> tp = zero<R>(), tm = zero<R>(), up = zero<R>(), um = zero<R>();
         C<R> ap = zero<R>(), am = zero<R>();
@@ -645,7 +651,7 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
       const int lx = g.p_x0() + q / nrr, lr = g.p_r0() + q % nrr;
       const int w = t.x0 + lx, j = t.r0 + lr;
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> v = zero<R>();
         if (live)
@@ -669,7 +675,7 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
       const int lx = g.j_x0() + q / nrr, lr = g.j_r0() + q % nrr;
       const int w = t.x0 + lx, j = t.r0 + lr;
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> ex = zero<R>(), bx = zero<R>();
         if (live) {
@@ -690,7 +696,7 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
       const int lx = q / g.TR, lr = q % g.TR;
       if (!t.owned(lx, lr)) continue;
       const int c = t.x0 + lx, j = t.r0 + lr;
-#pragma unroll
+#pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> tp, tm, up, um;
         if (j < t.J || t.closed) tr_interior(t, fs, 9, k, lx, lr, tp, tm);

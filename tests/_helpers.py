@@ -22,9 +22,13 @@ def group_errors(got, ref, M, nx, nr):
     return out
 
 
-def oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=(None, None, None, None)):
+def oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=(None, None, None, None), extended=True):
+    """The oracle as the parity reference: long double by default, so that the
+    paper's E.B form (a difference of nearly equal products between
+    co-propagating waves) does not leave FP64 rounding in the reference."""
     st = oracle.State(M, nx, nr, buf)
-    oracle.step(dict(nx=nx, nr=nr, M=M, h=1.0, dr=dr, g=g, m_a=m_a, flags=flags & 31), st, *src, nsteps=nsteps)
+    oracle.step(dict(nx=nx, nr=nr, M=M, h=1.0, dr=dr, g=g, m_a=m_a, flags=flags & 31), st, *src,
+                nsteps=nsteps, extended=extended)
     return st.buf
 
 
@@ -51,3 +55,15 @@ def random_case(seed, M, nx, nr):
 
 def stable_dr(M, m_a=0.0):
     return max(1.5, (M - 1) + 0.25) * (1 + m_a)
+
+
+def reference_and_tolerance(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=(None, None, None, None),
+                            base=1e-12):
+    """Long double reference and per-group FP64 tolerance: ``base``, raised to
+    ten times the distance between the FP64 and long double evaluations of
+    the same run where the problem itself is worse conditioned (the axion
+    of co-propagating vacuum waves is a small residue of O(1) products)."""
+    ref = oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src, extended=True)
+    r64 = oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src, extended=False)
+    floor = group_errors(r64, ref, M, nx, nr)
+    return ref, {k: max(base, 10.0 * v) for k, v in floor.items()}

@@ -11,7 +11,8 @@ pytestmark = pytest.mark.gpu
 
 from paper_2609_03550_b300 import inputs as I  # noqa: E402
 from paper_2609_03550_b300 import qds as Q  # noqa: E402
-from tests._helpers import group_errors, oracle_run, parity_cases, random_case, stable_dr  # noqa: E402
+from tests._helpers import (group_errors, oracle_run, parity_cases, random_case,  # noqa: E402
+                            reference_and_tolerance, stable_dr)
 
 DEV = "cuda:0"
 
@@ -101,7 +102,7 @@ def test_driven_wake_with_per_step_currents():
         s.set_state(torch.from_numpy(buf).to(DEV))
         for n in range(nsteps):
             jx, jr, jt = I.bunch_currents(wl, n)
-            oracle.step(dict(nx=wl.nx, nr=wl.nr, M=wl.M, h=1.0, dr=wl.dr, flags=0), st, jx, jr, jt)
+            oracle.step(dict(nx=wl.nx, nr=wl.nr, M=wl.M, h=1.0, dr=wl.dr, flags=0), st, jx, jr, jt, extended=True)
             tj = [torch.from_numpy(a).to(DEV).to(s.rdtype) for a in (jx, jr, jt)]
             s.step(1, jx=tj[0], jr=tj[1], jth=tj[2])
         torch.cuda.synchronize()
@@ -119,11 +120,11 @@ def test_two_colour_reduced(prec):
         L.w0, L.x0 = 80.0, 384.0
     flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
     buf = wl.initial_state()
-    ref = oracle_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, 100, g=wl.g)
+    ref, tol = reference_and_tolerance(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, 100, g=wl.g)
     got, s = gpu_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags | prec, 100, g=wl.g)
     e = group_errors(got, ref, wl.M, wl.nx, wl.nr)
     if prec == 0:
-        assert max(e.values()) < 1e-12, e
+        assert all(e[k] < tol[k] for k in e), (e, tol)
     else:
         assert e["em"] < 1e-5 and e["arem"] < 1e-4 and e["axion"] < 1e-4, e
 
@@ -131,13 +132,13 @@ def test_two_colour_reduced(prec):
 def test_diagnostics_match_oracle():
     import oracle
     M, nx, nr = 3, 40, 18
-    dr = stable_dr(M)
+    dr = stable_dr(M, 0.2)
     buf, _ = random_case(5, M, nx, nr)
     flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
     got, s = gpu_run(buf, M, nx, nr, dr, flags, 7, g=0.5, m_a=0.2)
     st = oracle.State(M, nx, nr, buf)
     pp = dict(nx=nx, nr=nr, M=M, h=1.0, dr=dr, g=0.5, m_a=0.2, flags=flags)
-    oracle.step(pp, st, nsteps=7)
+    oracle.step(pp, st, nsteps=7, extended=True)
     d_ref = oracle.diagnostics(pp, st, profile=True)
     d_got = s.diagnostics(profile=True)
     for k in ("em0", "axion", "em1", "cross"):
@@ -150,31 +151,29 @@ def test_diagnostics_match_oracle():
 def test_full_size_first_steps(which):
     """Full-size grids of the benchmark workloads, in the launch
     configuration the benchmark uses, three steps against the oracle."""
-    import oracle
     if which == "driven_wake":
         wl = I.driven_wake()
-        wl.dr = 5.0
         flags = 0
     else:
         wl = I.two_colour()
-        wl.dr = 5.0
         flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
     buf = wl.initial_state()
-    ref = oracle_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, 3, g=wl.g)
+    ref, tol = reference_and_tolerance(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, 3, g=wl.g)
     for prec in (0, Q.FP32):
         got, _ = gpu_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags | prec, 3, g=wl.g)
         e = group_errors(got, ref, wl.M, wl.nx, wl.nr)
-        lim = 1e-12 if prec == 0 else 1e-5
-        assert e["em"] < lim, (prec, e)
-        if flags & Q.AXION:
-            assert e["axion"] < (1e-12 if prec == 0 else 1e-4), (prec, e)
+        if prec == 0:
+            assert e["em"] < 1e-12, e
+            if flags & Q.AXION:
+                assert e["axion"] < tol["axion"] and e["arem"] < tol["arem"], (e, tol)
+        else:
+            assert e["em"] < 1e-5, e
+            if flags & Q.AXION:
+                assert e["axion"] < 1e-4 and e["arem"] < 1e-4, e
 
 
 def test_batched_uneven_instances_match_single_runs():
-    import oracle
     wls = I.batched_scan(n=512, steps=20)[:6]
-    for wl in wls:
-        wl.dr = 5.0
     flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
     params = [Q.Params(w.nx, w.nr, w.M, w.dr, g=w.g, flags=flags) for w in wls]
     s = Q.QDSSolver(params, device=DEV)
@@ -184,7 +183,7 @@ def test_batched_uneven_instances_match_single_runs():
     s.step(20)
     torch.cuda.synchronize()
     for i, (w, b) in enumerate(zip(wls, bufs)):
-        ref = oracle_run(b, w.M, w.nx, w.nr, w.dr, flags, 20, g=w.g)
+        ref, tol = reference_and_tolerance(b, w.M, w.nx, w.nr, w.dr, flags, 20, g=w.g)
         got = s.get_state(i).cpu().numpy()
         e = group_errors(got, ref, w.M, w.nx, w.nr)
-        assert e["em"] < 1e-12 and e["axion"] < 1e-12, (i, e)
+        assert all(e[k] < tol[k] for k in e), (i, e, tol)
