@@ -91,7 +91,8 @@ typedef struct qds_sources {
 typedef struct qds_handle qds_handle;
 
 /* Bytes of caller-owned state for one solve (two ping-pong copies of the
- * 15 planes + phi_prev in the working precision); 0 if params are invalid. */
+ * 15 planes + phi_prev, and four scratch planes, in the working precision);
+ * 0 if params are invalid. */
 size_t qds_state_bytes(const qds_params *p);
 
 /* Create a solver bound to state_dev (>= qds_state_bytes, 256-byte aligned).
@@ -128,6 +129,13 @@ int qds_num_instances(const qds_handle *h);
 /* The four energies of every instance into out_dev[4*i .. 4*i+3] (device,
  * n_inst*4 doubles) in two launches; asynchronous on stream. */
 int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
+
+/* Step implementation: 0 (default) runs one grid-wide pass per stage of the
+ * step (leapfrog, axion source, shift, phi, axion current, regenerated
+ * leapfrog, regenerated shift), intermediates in the new state and in
+ * scratch planes of the caller's buffer; 1 runs every stage of a tile in one
+ * kernel with the intermediates and their halos in shared memory. */
+int qds_set_fused(qds_handle *h, int fused);
 
 /* Tile shape of the fused step kernel (x cells, radial rows); used by the
  * autotuner.  qds_get_tile also reports the tile count and shared memory. */

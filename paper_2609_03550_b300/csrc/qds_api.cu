@@ -69,8 +69,12 @@ int validate(const qds_params &p) {
 
 size_t elem_bytes(const qds_params &p) { return is_fp32(p) ? 8 : 16; }
 
+size_t half_bytes(const qds_params &p) { return align_up(state_elems(p.n_modes, p.nx, p.nr) * elem_bytes(p)); }
+
+// two ping-pong copies of the state, then four scratch planes (Gamma_a and
+// the three components of j_a) used by the pass-mode step
 size_t instance_bytes(const qds_params &p) {
-  return 2 * align_up(state_elems(p.n_modes, p.nx, p.nr) * elem_bytes(p));
+  return 2 * half_bytes(p) + align_up(4 * plane_elems(p.n_modes, p.nx, p.nr) * elem_bytes(p));
 }
 
 Geo pick_geo(const qds_params &p, int override_tx, int override_tr) {
@@ -113,6 +117,9 @@ struct qds_handle {
   };
   std::vector<Group> groups;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
+  bool fused = false;  // fused shared-memory step (one launch) instead of one pass per stage
+  // pass-mode tiles (one thread per point)
+  std::vector<Group> pgroups;
   // graph cache: key (jx, jr, jt, sext, nsteps, stream)
   std::map<std::tuple<const void *, const void *, const void *, const void *, int, void *>, cudaGraphExec_t> graphs;
   const void *cur_src[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -139,6 +146,7 @@ void fill_inst(qds_handle *h, int i, const qds_params &p, void *base) {
   size_t half = align_up(state_elems(p.n_modes, p.nx, p.nr) * sizeof(C<R>));
   I.state[0] = reinterpret_cast<C<R> *>((char *)base);
   I.state[1] = reinterpret_cast<C<R> *>((char *)base + half);
+  I.scratch = reinterpret_cast<C<R> *>((char *)base + 2 * half);
   I.jx = I.jr = I.jt = I.sext = nullptr;
   h->h_inst[i].assign((char *)&I, (char *)&I + sizeof I);
 }
@@ -188,8 +196,41 @@ cudaError_t allow_smem_for(bool fp32, int M, size_t bytes) {
   return cudaErrorInvalidValue;
 }
 
+template <class R, int M>
+cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl, cudaStream_t st) {
+  const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
+  const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, ST_ZERO};
+  for (int st_ : order) {
+    if ((st_ == ST_SOURCE || st_ == ST_PHI) && !ax) continue;
+    if ((st_ == ST_CURRENT || st_ == ST_LEAP1 || st_ == ST_SHIFT1) && !ar) continue;
+    if (st_ == ST_ZERO && !mw) continue;
+    pass_kernel<R, M><<<G.ntiles, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_tiles, h->d_ctrl, G.g, st_);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <class R>
 cudaError_t launch_step(qds_handle *h, cudaStream_t st) {
+  if (!h->fused) {
+    for (const auto &G : h->pgroups) {
+      uint32_t fl = 0;
+      for (int i = 0; i < h->n_inst; i++)
+        if (h->params[i].n_modes == G.M) fl |= h->params[i].flags;
+      cudaError_t e = cudaSuccess;
+      switch (G.M) {
+        case 1: e = launch_passes<R, 1>(h, G, fl, st); break;
+        case 2: e = launch_passes<R, 2>(h, G, fl, st); break;
+        case 3: e = launch_passes<R, 3>(h, G, fl, st); break;
+        case 4: e = launch_passes<R, 4>(h, G, fl, st); break;
+        default: e = cudaErrorInvalidValue;
+      }
+      if (e != cudaSuccess) return e;
+    }
+    advance_kernel<<<1, 32, 0, st>>>(h->d_ctrl, 1);
+    return cudaGetLastError();
+  }
   for (const auto &G : h->groups) {
     cudaError_t e = cudaSuccess;
     switch (G.M) {
@@ -289,6 +330,24 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
     if (smem > 227 * 1024) return fail(QDS_ERR_UNSUPPORTED, "tile does not fit in shared memory");
     CU(allow_smem_for(fp32, M, smem));
     h->groups.push_back(G);
+    // pass mode: 8 x 32 points per CTA, one point per thread
+    {
+      qds_handle::Group P;
+      P.M = M;
+      P.g.TX = kThreads / 32;
+      P.g.TR = 32;
+      P.L = Smem{};
+      std::vector<int4> pt;
+      for (int i = 0; i < n; i++) {
+        if (params[i].n_modes != M) continue;
+        for (int x0 = 0; x0 < params[i].nx; x0 += P.g.TX)
+          for (int r0 = 0; r0 < params[i].nr; r0 += P.g.TR) pt.push_back(make_int4(i, x0, r0, 0));
+      }
+      P.ntiles = (int)pt.size();
+      CU(cudaMalloc(&P.d_tiles, sizeof(int4) * pt.size()));
+      CU(cudaMemcpy(P.d_tiles, pt.data(), sizeof(int4) * pt.size(), cudaMemcpyHostToDevice));
+      h->pgroups.push_back(P);
+    }
   }
   return upload_inst(h, 0);
 }
@@ -297,6 +356,7 @@ void destroy(qds_handle *h) {
   if (!h) return;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &G : h->groups) cudaFree(G.d_tiles);
+  for (auto &G : h->pgroups) cudaFree(G.d_tiles);
   cudaFree(h->d_inst);
   cudaFree(h->d_ctrl);
   cudaFree(h->d_partial);
@@ -357,10 +417,22 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   h->graphs.clear();
   for (auto &G : h->groups) cudaFree(G.d_tiles);
   cudaFree(h->d_inst); cudaFree(h->d_ctrl); cudaFree(h->d_partial); cudaFree(h->d_diag);
-  h->groups = nh->groups; h->d_inst = nh->d_inst; h->d_ctrl = nh->d_ctrl;
+  cudaFree(h->d_partial_all); cudaFree(h->d_scal);
+  for (auto &G : h->pgroups) cudaFree(G.d_tiles);
+  h->groups = nh->groups; h->pgroups = nh->pgroups; h->d_inst = nh->d_inst; h->d_ctrl = nh->d_ctrl;
+  h->d_partial_all = nh->d_partial_all; h->d_scal = nh->d_scal;
   h->d_partial = nh->d_partial; h->d_diag = nh->d_diag; h->h_inst = nh->h_inst;
-  nh->groups.clear(); nh->d_inst = nullptr; nh->d_ctrl = nullptr; nh->d_partial = nullptr; nh->d_diag = nullptr;
+  nh->groups.clear(); nh->pgroups.clear(); nh->d_inst = nullptr; nh->d_ctrl = nullptr; nh->d_partial = nullptr;
+  nh->d_diag = nullptr; nh->d_partial_all = nullptr; nh->d_scal = nullptr;
   delete nh;
+  return QDS_OK;
+}
+
+int qds_set_fused(qds_handle *h, int fused) {
+  if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
+  h->fused = fused != 0;
+  for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
   return QDS_OK;
 }
 

@@ -64,6 +64,7 @@ struct Inst {
   R gs;         // coupling in the axion source term of Gamma_a
   R gj;         // coupling in the axion current j_a
   C<R> *state[2];        // ping-pong bases: 15 planes, then phi_prev
+  C<R> *scratch;         // pass mode: Gamma_a, j_a,x, j_a,r, j_a,th planes
   const C<R> *jx, *jr, *jt, *sext;  // optional sources [M][nx][nr]
   int tiles_x, tiles_r;  // tile grid of this instance
   int tile_base;         // first global tile index of this instance

@@ -19,7 +19,7 @@ namespace {
 template <class R, int M>
 void emu_steps(const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
                uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext,
-               int nsteps, int TX, int TR, int nthreads) {
+               int nsteps, int TX, int TR, int nthreads, int fused) {
   const size_t P = plane_elems(M, nx, nr), E = state_elems(M, nx, nr);
   const bool sc = (flags & (F_FP32 | F_SCALE_G)) && g != 0.0;
   const double s_ax = sc ? 1.0 / g : 1.0, s_ar = sc ? 1.0 / (g * g) : 1.0;
@@ -58,11 +58,47 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
   geo.TR = TR;
   Smem L = smem_layout(geo, M, flags);
   std::vector<C<R>> sm(L.total);
-  for (int n = 0; n < nsteps; n++) {
+  std::vector<C<R>> scratch(4 * P);
+  for (int q = 0; q < (int)scratch.size(); q++) scratch[q] = mk<R>((R)1e30, (R)1e30);
+  I.scratch = scratch.data();
+  for (int n = 0; n < nsteps && !fused; n++) {
+    // pass mode: every stage over every tile before the next stage
+    const int par = n & 1;
+    const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
+    const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, ST_ZERO};
+    for (int st : order) {
+      if ((st == ST_SOURCE || st == ST_PHI) && !ax) continue;
+      if ((st == ST_CURRENT || st == ST_LEAP1 || st == ST_SHIFT1) && !ar) continue;
+      if (st == ST_ZERO && !mw) continue;
+      for (int x0 = 0; x0 < nx; x0 += TX)
+        for (int r0 = 0; r0 < nr; r0 += TR) {
+          Tile<R, M, false> t;
+          t.I = &I;
+          t.nx = nx; t.nr = nr; t.J = nr - 1;
+          t.x0 = x0; t.r0 = r0;
+          t.per = (flags & F_X_PERIODIC) != 0;
+          t.closed = (flags & F_R_CLOSED) != 0;
+          t.mw = mw;
+          t.s = t.mw ? n % nx : 0;
+          t.P = P;
+          t.o = buf[par].data();
+          t.n = buf[par ^ 1].data();
+          t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
+          t.g = geo;
+          t.L = L;
+          t.sm = nullptr;
+          t.scr = scratch.data();
+          t.state_len = E;
+          t.sm_len = 0;
+          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false>(t, st, tid, nthreads);
+        }
+    }
+  }
+  for (int n = 0; n < nsteps && fused; n++) {
     const int par = n & 1;
     for (int x0 = 0; x0 < nx; x0 += TX)
       for (int r0 = 0; r0 < nr; r0 += TR) {
-        Tile<R, M> t;
+        Tile<R, M, true> t;
         t.I = &I;
         t.nx = nx; t.nr = nr; t.J = nr - 1;
         t.x0 = x0; t.r0 = r0;
@@ -79,10 +115,11 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
         // poison shared memory so that a read of a slot no stage wrote shows up
         for (auto &z : sm) z = mk<R>((R)1e30, (R)1e30);
         t.sm = sm.data();
+        t.scr = nullptr;
         t.state_len = E;
         t.sm_len = L.total;
         for (int st = 0; st < N_STAGE; st++)
-          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M>(t, st, tid, nthreads);
+          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, true>(t, st, tid, nthreads);
       }
   }
   // export in window order
@@ -115,12 +152,12 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
 template <class R>
 int dispatch(int M, const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
              uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext, int nsteps,
-             int TX, int TR, int nth) {
+             int TX, int TR, int nth, int fused) {
   switch (M) {
-    case 1: emu_steps<R, 1>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
-    case 2: emu_steps<R, 2>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
-    case 3: emu_steps<R, 3>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
-    case 4: emu_steps<R, 4>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth); return 0;
+    case 1: emu_steps<R, 1>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
+    case 2: emu_steps<R, 2>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
+    case 3: emu_steps<R, 3>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
+    case 4: emu_steps<R, 4>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
   }
   return 1;
 }
@@ -129,8 +166,9 @@ int dispatch(int M, const double *canon, double *out, int nx, int nr, double h, 
 
 extern "C" int qds_emu_steps(int M, const double *canon, double *out, int nx, int nr, double h, double dr,
                              double m_a, double g, uint32_t flags, const double *jx, const double *jr,
-                             const double *jt, const double *sext, int nsteps, int TX, int TR, int nthreads) {
+                             const double *jt, const double *sext, int nsteps, int TX, int TR, int nthreads,
+                             int fused) {
   if (flags & F_FP32)
-    return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads);
-  return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads);
+    return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads, fused);
+  return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads, fused);
 }

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ i
   const int4 td = tiles[blockIdx.x];
   const Inst<R> &I = insts[td.x];
   const unsigned long long n = ctrl->step;
-  Tile<R, M> t;
+  Tile<R, M, true> t;
   t.I = &I;
   t.nx = I.nx;
   t.nr = I.nr;
@@ -46,11 +46,46 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ i
   t.g = g;
   t.L = L;
   t.sm = reinterpret_cast<C<R> *>(smraw);
+  t.scr = nullptr;
 #pragma unroll 1
   for (int st = 0; st < N_STAGE; st++) {
-    run_stage<R, M>(t, st, threadIdx.x, blockDim.x);
+    run_stage<R, M, true>(t, st, threadIdx.x, blockDim.x);
     __syncthreads();
   }
+}
+
+// One stage of the step over the whole grid, one thread per (x, r) point of
+// a tile, all modes per thread.
+template <class R, int M>
+__global__ void __launch_bounds__(256) pass_kernel(const Inst<R> *__restrict__ insts,
+                                                   const int4 *__restrict__ tiles,
+                                                   const Ctrl *__restrict__ ctrl, Geo g, int stage) {
+  const int4 td = tiles[blockIdx.x];
+  const Inst<R> &I = insts[td.x];
+  const unsigned long long n = ctrl->step;
+  Tile<R, M, false> t;
+  t.I = &I;
+  t.nx = I.nx;
+  t.nr = I.nr;
+  t.J = I.nr - 1;
+  t.x0 = td.y;
+  t.r0 = td.z;
+  t.per = (I.flags & F_X_PERIODIC) != 0;
+  t.closed = (I.flags & F_R_CLOSED) != 0;
+  t.mw = (I.flags & F_MOVING_WINDOW) != 0;
+  t.s = t.mw ? (int)(n % (unsigned long long)I.nx) : 0;
+  t.P = plane_elems(M, I.nx, I.nr);
+  const int par = (int)(n & 1ull);
+  t.o = I.state[par];
+  t.n = I.state[par ^ 1];
+  t.h = I.h;
+  t.dr = I.dr;
+  t.ih = I.inv_h;
+  t.idr = I.inv_dr;
+  t.g = g;
+  t.sm = nullptr;
+  t.scr = I.scratch;
+  run_stage<R, M, false>(t, stage, threadIdx.x, blockDim.x);
 }
 
 __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {

@@ -49,7 +49,10 @@ QDS_HD C<R> ldg(const C<R> *p) {
 #endif
 }
 
-template <class R, int M>
+// SM = true: the fused step, intermediates in the CTA's shared memory with
+// halos recomputed per tile.  SM = false: one pass per stage over the whole
+// grid, intermediates in the new state buffer and the scratch planes.
+template <class R, int M, bool SM = true>
 struct Tile {
   const Inst<R> *I;
   int nx, nr, J;       // J = nr - 1: last integer row / last half row
@@ -63,6 +66,8 @@ struct Tile {
   Geo g;
   Smem L;
   C<R> *sm;
+  C<R> *scr;              // pass mode: scratch planes Gamma_a, j_a,x, j_a,r, j_a,th
+  mutable C<R> dummy;     // pass mode: target of out-of-domain accesses
 #if defined(QDS_EMU)
   size_t state_len;    // bounds for the emulator
   int sm_len;
@@ -105,14 +110,14 @@ struct Tile {
     return ldg(a + ((size_t)k * nx + w) * nr + j);
   }
   QDS_HD void store(int field, int k, int w, int j, C<R> v) const {
-    if (mw && w == 0) v = zero<R>();  // the rear column becomes the new front
+    if (SM && mw && w == 0) v = zero<R>();  // the rear column becomes the new front
 #if defined(QDS_EMU)
     QDS_CHECK(gidx(field, k, w, j) < state_len, "store");
 #endif
     n[gidx(field, k, w, j)] = v;
   }
   QDS_HD void store_prev(int k, int w, C<R> v) const {
-    if (mw && w == 0) v = zero<R>();
+    if (SM && mw && w == 0) v = zero<R>();
     n[(size_t)NFIELD * P + (size_t)k * nx + slot(w)] = v;
   }
   QDS_HD bool owned(int lx, int lr) const {
@@ -125,8 +130,26 @@ struct Tile {
   QDS_HD C<R> Et(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) + cell(grp + TTM, k, w, j)); }
   QDS_HD C<R> Br(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) - cell(grp + TTM, k, w, j)); }
 
-  // ---------------- shared-memory planes ----------------
+  // ---------------- intermediate planes ----------------
+  // pass mode: a plane of the new state (or scratch) at window position w;
+  // out-of-domain positions read as zero and absorb writes
+  // Every window position 0..nx-1 is a storage slot (the held-zero face
+  // nx-1 included, so that it is written as zero each step); positions
+  // outside the window read as zero.
+  QDS_HD C<R> &gnew(int field, int k, int w, int j, bool /*face_pos*/) const {
+    const bool ok = cell_ok(w) && j >= 0 && j < nr;
+    if (!ok) { dummy = zero<R>(); return dummy; }
+#if defined(QDS_EMU)
+    QDS_CHECK(gidx(field, k, w, j) < state_len, "pass-mode new-state access");
+#endif
+    return n[gidx(field, k, w, j)];
+  }
+  QDS_HD C<R> &gscr(int plane, int k, int w, int j) const {
+    if (!cell_ok(w) || j < 0 || j >= nr) { dummy = zero<R>(); return dummy; }
+    return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * nr + j];
+  }
   QDS_HD C<R> &sA(int pl, int k, int lx, int lr) const {  // pl 0: Ex0n, 1: Bx0n
+    if (!SM) return gnew(pl ? BX : EX, k, x0 + lx, r0 + lr, true);
     int i = L.off_a + ((pl * M + k) * g.a_nx() + (lx - g.a_x0())) * g.a_nr() + (lr - g.a_r0());
 #if defined(QDS_EMU)
     QDS_CHECK(lx >= g.a_x0() && lx < g.a_x0() + g.a_nx() && lr >= g.a_r0() && lr < g.a_r0() + g.a_nr(), "sA");
@@ -134,6 +157,7 @@ struct Tile {
     return sm[i];
   }
   QDS_HD C<R> &sG(int k, int lx, int lr) const {
+    if (!SM) return gscr(0, k, x0 + lx, r0 + lr);
     int i = L.off_j + (k * g.g_nx() + (lx - g.g_x0())) * g.g_nr() + (lr - g.g_r0());
 #if defined(QDS_EMU)
     QDS_CHECK(lx >= g.g_x0() && lx < g.g_x0() + g.g_nx() && lr >= g.g_r0() && lr < g.g_r0() + g.g_nr(), "sG");
@@ -141,6 +165,7 @@ struct Tile {
     return sm[i];
   }
   QDS_HD C<R> &sT(int pl, int k, int lx, int lr) const {  // 0..3 T0 new, 4 Tap new, 5 Tam new
+    if (!SM) return gnew(pl < 4 ? TRP + pl : TAP + (pl - 4), k, x0 + lx, r0 + lr, false);
     int i = L.off_t + ((pl * M + k) * g.t_nx() + (lx - g.t_x0())) * g.t_nr() + (lr - g.t_r0());
 #if defined(QDS_EMU)
     QDS_CHECK(lx >= g.t_x0() && lx < g.t_x0() + g.t_nx() && lr >= g.t_r0() && lr < g.t_r0() + g.t_nr(), "sT");
@@ -148,6 +173,7 @@ struct Tile {
     return sm[i];
   }
   QDS_HD C<R> &sP(int k, int lx, int lr) const {
+    if (!SM) return gnew(PHI, k, x0 + lx, r0 + lr, true);
     int i = L.off_p + (k * g.p_nx() + (lx - g.p_x0())) * g.p_nr() + (lr - g.p_r0());
 #if defined(QDS_EMU)
     QDS_CHECK(lx >= g.p_x0() && lx < g.p_x0() + g.p_nx() && lr >= g.p_r0() && lr < g.p_r0() + g.p_nr(), "sP");
@@ -155,6 +181,10 @@ struct Tile {
     return sm[i];
   }
   QDS_HD C<R> &sJ(int pl, int k, int lx, int lr) const {  // 0 Ex1n 1 Bx1n 2 jax 3 jar 4 jat
+    if (!SM) {
+      if (pl < 2) return gnew(pl ? BX1 : EX1, k, x0 + lx, r0 + lr, true);
+      return gscr(pl - 1, k, x0 + lx, r0 + lr);
+    }
     int i = L.off_j + ((pl * M + k) * g.j_nx() + (lx - g.j_x0())) * g.j_nr() + (lr - g.j_r0());
 #if defined(QDS_EMU)
     QDS_CHECK(lx >= g.j_x0() && lx < g.j_x0() + g.j_nx() && lr >= g.j_r0() && lr < g.j_r0() + g.j_nr(), "sJ");
@@ -196,8 +226,8 @@ QDS_HD C<R> conv(int m, const C<R> *A, const C<R> *B) {
 // conservative form, (1/r) d(r F)/dr = (r_+ F_+ - r_- F_-)/(r dr), which is
 // algebraically the paper's average-plus-centred-difference form.
 // ---------------------------------------------------------------------------
-template <class R, int M>
-QDS_NOINL C<R> ex_update(const Tile<R, M> &t, int grp, int k, int w, int j, C<R> jx) {
+template <class R, int M, bool SM>
+QDS_NOINL C<R> ex_update(const Tile<R, M, SM> &t, int grp, int k, int w, int j, C<R> jx) {
   C<R> e0 = t.face(grp + EX, k, w, j);
   if (j == 0) {
     if (k != 0) return zero<R>();
@@ -213,8 +243,8 @@ QDS_NOINL C<R> ex_update(const Tile<R, M> &t, int grp, int k, int w, int j, C<R>
   return e0 + t.h * gx;
 }
 
-template <class R, int M>
-QDS_NOINL C<R> bx_interior(const Tile<R, M> &t, int grp, int k, int w, int j) {
+template <class R, int M, bool SM>
+QDS_NOINL C<R> bx_interior(const Tile<R, M, SM> &t, int grp, int k, int w, int j) {
   C<R> b0 = t.face(grp + BX, k, w, j);
   R rh = (R(j) + R(0.5)) * t.dr;
   C<R> elo = R(0.5) * (t.Et(grp, k, w, j) + t.Et(grp, k, w + 1, j));
@@ -226,8 +256,8 @@ QDS_NOINL C<R> bx_interior(const Tile<R, M> &t, int grp, int k, int w, int j) {
 
 // Outer half row J+1/2, Eq. em_r_open_bx by the box scheme over
 // [r_{J-1/2}, r_{J+1/2}] x [t^{n-1/2}, t^{n+1/2}], right side at (x_{w+1/2}, r_J, t^n).
-template <class R, int M>
-QDS_NOINL C<R> bx_outer(const Tile<R, M> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
+template <class R, int M, bool SM>
+QDS_NOINL C<R> bx_outer(const Tile<R, M, SM> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
   const int J = t.J;
   R rJ = R(J) * t.dr;
   C<R> dxbr = t.ih * (t.Br(grp, k, w + 1, J) - t.Br(grp, k, w, J));
@@ -245,9 +275,9 @@ QDS_NOINL C<R> bx_outer(const Tile<R, M> &t, int grp, int k, int w, C<R> jt_face
 // from the tile's shared memory and x-averages the caller's cell currents;
 // group 1 (the regenerated field) reads E_x1, B_x1 and j_a from shared memory.
 // ---------------------------------------------------------------------------
-template <class R, int M>
+template <class R, int M, bool SM>
 struct Faces0 {
-  const Tile<R, M> &t;
+  const Tile<R, M, SM> &t;
   QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sA(0, k, lx, lr); }
   QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sA(1, k, lx, lr); }
   QDS_HD C<R> jr(int k, int lx, int lr) const {
@@ -267,9 +297,9 @@ struct Faces0 {
   }
 };
 
-template <class R, int M>
+template <class R, int M, bool SM>
 struct Faces1 {
-  const Tile<R, M> &t;
+  const Tile<R, M, SM> &t;
   QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sJ(0, k, lx, lr); }
   QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sJ(1, k, lx, lr); }
   QDS_HD C<R> jx(int k, int lx, int lr) const { return t.sJ(2, k, lx, lr); }
@@ -283,8 +313,8 @@ struct Faces1 {
 // behind through face c-1, T_r^- and T_th^+ from the cell ahead through face
 // c.  Axis rules of Sec. 2.3 (Eq. axis_Ttheta; T_th^(m!=1) = 0 on the axis).
 // ---------------------------------------------------------------------------
-template <class R, int M, class FS>
-QDS_NOINL void tr_interior(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
+template <class R, int M, bool SM, class FS>
+QDS_NOINL void tr_interior(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, int lx, int lr,
                         C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   R rh = (R(j) + R(0.5)) * t.dr;
@@ -306,8 +336,8 @@ QDS_NOINL void tr_interior(const Tile<R, M> &t, const FS &fs, int grp, int k, in
 // Outer half row: E_r by the shift with the Gamma_r source alone, B_theta by
 // the box scheme of Eq. em_r_open_bt over [r_{J-1/2}, r_{J+1/2}] x [t^n, t^{n+1}]
 // with its right side from time-n fields.
-template <class R, int M, class FS>
-QDS_NOINL void tr_outer(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
+template <class R, int M, bool SM, class FS>
+QDS_NOINL void tr_outer(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
                      int lr_J, C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, J = t.J;
   R rh = (R(J) + R(0.5)) * t.dr, rJ = R(J) * t.dr;
@@ -329,8 +359,8 @@ QDS_NOINL void tr_outer(const Tile<R, M> &t, const FS &fs, int grp, int k, int l
   tm = er_new - bt_new;
 }
 
-template <class R, int M, class FS>
-QDS_NOINL void tt_update(const Tile<R, M> &t, const FS &fs, int grp, int k, int lx, int lr,
+template <class R, int M, bool SM, class FS>
+QDS_NOINL void tt_update(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, int lx, int lr,
                       C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   if (j == 0 && k != 1) { tp = zero<R>(); tm = zero<R>(); return; }
@@ -362,8 +392,8 @@ QDS_NOINL void tt_update(const Tile<R, M> &t, const FS &fs, int grp, int k, int 
 // exterior phi comes from the outgoing condition (d_t + c d_r) phi = 0
 // centred at r_J (Eq. axion_r_ghost) with d_t phi taken half a step back.
 // ---------------------------------------------------------------------------
-template <class R, int M>
-QDS_NOINL void source_point(const Tile<R, M> &t, int lx, int lr) {
+template <class R, int M, bool SM>
+QDS_NOINL void source_point(const Tile<R, M, SM> &t, int lx, int lr) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) t.sG(k, lx, lr) = zero<R>();
@@ -423,8 +453,8 @@ QDS_NOINL void source_point(const Tile<R, M> &t, int lx, int lr) {
 // Below the axis a scalar on half rows mirrors with parity (-1)^l; E_r and
 // B_theta below the axis follow the T_r ghost of Eq. axis_Tr.
 // ---------------------------------------------------------------------------
-template <class R, int M>
-QDS_NOINL void current_point(const Tile<R, M> &t, int lx, int lr) {
+template <class R, int M, bool SM>
+QDS_NOINL void current_point(const Tile<R, M, SM> &t, int lx, int lr) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) for (int q = 2; q < 5; q++) t.sJ(q, k, lx, lr) = zero<R>();
@@ -572,17 +602,38 @@ QDS_NOINL void current_point(const Tile<R, M> &t, int lx, int lr) {
 // Stage dispatcher.  The kernel runs every stage over all threads of the CTA
 // with a barrier in between; the host emulator runs them in the same order.
 // ---------------------------------------------------------------------------
-enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, N_STAGE };
+enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, N_STAGE, ST_ZERO = N_STAGE };
 
-template <class R, int M>
-QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
+template <class R, int M, bool SM>
+QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
   const Geo &g = t.g;
   const uint32_t fl = t.I->flags;
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0;
+  // region of a stage: its halo region (fused) or the tile itself (pass mode)
+  auto region = [&](int x0_, int nx_, int r0_, int nr_, int &xa, int &nxr, int &ra, int &nrr) {
+    if (SM) { xa = x0_; nxr = nx_; ra = r0_; nrr = nr_; }
+    else { xa = 0; nxr = g.TX; ra = 0; nrr = g.TR; }
+  };
+  int xa, nxr, ra, nrr;
+  if (st == ST_ZERO) {
+    // pass mode, moving window: the rear column of every field becomes the
+    // new (empty) front column once all passes have read it
+    if (SM || !t.mw || t.x0 != 0) return;
+    for (int q = tid; q < g.TR; q += nth) {
+      const int j = t.r0 + q;
+      if (j >= t.nr) continue;
+      for (int f = 0; f < NFIELD; f++)
+        for (int k = 0; k < M; k++) t.n[t.gidx(f, k, 0, j)] = zero<R>();
+      if (j == t.J)
+        for (int k = 0; k < M; k++) t.n[(size_t)NFIELD * t.P + (size_t)k * t.nx + t.slot(0)] = zero<R>();
+    }
+    return;
+  }
   if (st == ST_LEAP0) {
-    const int nxr = g.a_nx(), nrr = g.a_nr(), npt = nxr * nrr;
+    region(g.a_x0(), g.a_nx(), g.a_r0(), g.a_nr(), xa, nxr, ra, nrr);
+    const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
-      const int lx = g.a_x0() + q / nrr, lr = g.a_r0() + q % nrr;
+      const int lx = xa + q / nrr, lr = ra + q % nrr;
       const int w = t.x0 + lx, j = t.r0 + lr;
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
@@ -598,17 +649,21 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
         }
         t.sA(0, k, lx, lr) = ex;
         t.sA(1, k, lx, lr) = bx;
-        if (t.owned(lx, lr)) { t.store(EX, k, w, j, ex); t.store(BX, k, w, j, bx); }
+        if (SM && t.owned(lx, lr)) { t.store(EX, k, w, j, ex); t.store(BX, k, w, j, bx); }
       }
     }
   } else if (st == ST_SOURCE) {
     if (!ax) return;
-    const int nxr = g.g_nx(), nrr = g.g_nr(), npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) source_point(t, g.g_x0() + q / nrr, g.g_r0() + q % nrr);
+    region(g.g_x0(), g.g_nx(), g.g_r0(), g.g_nr(), xa, nxr, ra, nrr);
+    const int npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) {
+      if (!SM && !t.owned(xa + q / nrr, ra + q % nrr)) continue;
+      source_point(t, xa + q / nrr, ra + q % nrr);
+    }
   } else if (st == ST_SHIFT0) {
-    Faces0<R, M> fs{t};
-    const int xa = ax ? g.t_x0() : 0, nxr = ax ? g.t_nx() : g.TX;
-    const int ra = ax ? g.t_r0() : 0, nrr = ax ? g.t_nr() : g.TR;
+    Faces0<R, M, SM> fs{t};
+    if (ax) region(g.t_x0(), g.t_nx(), g.t_r0(), g.t_nr(), xa, nxr, ra, nrr);
+    else { xa = 0; nxr = g.TX; ra = 0; nrr = g.TR; }
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
@@ -632,7 +687,7 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
             am = t.cell(TAM, k, c + 1, j) + t.h * t.sG(k, lx, lr);
           }
         }
-        if (ax) {
+        if (ax && SM) {
           t.sT(0, k, lx, lr) = tp; t.sT(1, k, lx, lr) = tm;
           t.sT(2, k, lx, lr) = up; t.sT(3, k, lx, lr) = um;
           t.sT(4, k, lx, lr) = ap; t.sT(5, k, lx, lr) = am;
@@ -646,9 +701,11 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
     }
   } else if (st == ST_PHI) {
     if (!ax) return;
-    const int nxr = g.p_nx(), nrr = g.p_nr(), npt = nxr * nrr;
+    region(g.p_x0(), g.p_nx(), g.p_r0(), g.p_nr(), xa, nxr, ra, nrr);
+    const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
-      const int lx = g.p_x0() + q / nrr, lr = g.p_r0() + q % nrr;
+      const int lx = xa + q / nrr, lr = ra + q % nrr;
+      if (!SM && !t.owned(lx, lr)) continue;
       const int w = t.x0 + lx, j = t.r0 + lr;
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
@@ -659,20 +716,26 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
                                                        t.sT(4, k, lx + 1, lr) + t.sT(4, k, lx, lr));
         t.sP(k, lx, lr) = v;
         if (t.owned(lx, lr)) {
-          t.store(PHI, k, w, j, v);
+          if (SM) t.store(PHI, k, w, j, v);
           if (j == t.J) t.store_prev(k, w, live ? t.face(PHI, k, w, j) : zero<R>());
         }
       }
     }
   } else if (st == ST_CURRENT) {
     if (!ar) return;
-    const int nxr = g.j_nx(), nrr = g.j_nr(), npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) current_point(t, g.j_x0() + q / nrr, g.j_r0() + q % nrr);
+    region(g.j_x0(), g.j_nx(), g.j_r0(), g.j_nr(), xa, nxr, ra, nrr);
+    const int npt = nxr * nrr;
+    for (int q = tid; q < npt; q += nth) {
+      if (!SM && !t.owned(xa + q / nrr, ra + q % nrr)) continue;
+      current_point(t, xa + q / nrr, ra + q % nrr);
+    }
   } else if (st == ST_LEAP1) {
     if (!ar) return;
-    const int nxr = g.j_nx(), nrr = g.j_nr(), npt = nxr * nrr;
+    region(g.j_x0(), g.j_nx(), g.j_r0(), g.j_nr(), xa, nxr, ra, nrr);
+    const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
-      const int lx = g.j_x0() + q / nrr, lr = g.j_r0() + q % nrr;
+      const int lx = xa + q / nrr, lr = ra + q % nrr;
+      if (!SM && !t.owned(lx, lr)) continue;
       const int w = t.x0 + lx, j = t.r0 + lr;
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
@@ -685,12 +748,12 @@ QDS_HD void run_stage(const Tile<R, M> &t, int st, int tid, int nth) {
         }
         t.sJ(0, k, lx, lr) = ex;
         t.sJ(1, k, lx, lr) = bx;
-        if (t.owned(lx, lr)) { t.store(EX1, k, w, j, ex); t.store(BX1, k, w, j, bx); }
+        if (SM && t.owned(lx, lr)) { t.store(EX1, k, w, j, ex); t.store(BX1, k, w, j, bx); }
       }
     }
   } else if (st == ST_SHIFT1) {
     if (!ar) return;
-    Faces1<R, M> fs{t};
+    Faces1<R, M, SM> fs{t};
     const int npt = g.TX * g.TR;
     for (int q = tid; q < npt; q += nth) {
       const int lx = q / g.TR, lr = q % g.TR;

@@ -66,6 +66,7 @@ def lib():
             "qds_num_instances": (i, [H]),
             "qds_diagnostics_all": (i, [H, vp, vp]),
             "qds_set_tile": (i, [H, i, i]),
+            "qds_set_fused": (i, [H, i]),
             "qds_get_tile": (i, [H, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
             "qds_free": (None, [H]),
             "qds_last_error": (ctypes.c_char_p, []),
@@ -189,6 +190,9 @@ class QDSSolver:
             out = torch.empty((len(self.params), 4), dtype=torch.float64, device=self.device)
         _check(lib().qds_diagnostics_all(self.h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
+
+    def set_fused(self, fused: bool):
+        _check(lib().qds_set_fused(self.h, int(bool(fused))))
 
     def set_tile(self, tx, tr):
         _check(lib().qds_set_tile(self.h, int(tx), int(tr)))

@@ -67,3 +67,13 @@ def reference_and_tolerance(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, s
     r64 = oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src, extended=False)
     floor = group_errors(r64, ref, M, nx, nr)
     return ref, {k: max(base, 10.0 * v) for k, v in floor.items()}
+
+
+def fp32_tolerance(tol64, field_tol=1e-5, axion_tol=1e-4):
+    """FP32 bounds: 1e-5 for the EM fields, 1e-4 for the axion and the
+    regenerated fields, each raised to the FP64 conditioning floor scaled
+    by the ratio of the unit roundoffs (2^-24 / 2^-53)."""
+    scale = 2.0 ** 29
+    return {"em": max(field_tol, (tol64["em"] / 10.0) * 10.0 * scale if tol64["em"] > 1e-12 else field_tol),
+            "axion": max(axion_tol, tol64["axion"] * scale if tol64["axion"] > 1e-12 else axion_tol),
+            "arem": max(axion_tol, tol64["arem"] * scale if tol64["arem"] > 1e-12 else axion_tol)}

@@ -43,10 +43,11 @@ def _bytes(**kw):
 
 
 def test_state_bytes_of_valid_statements():
-    b64 = _bytes()
-    assert b64 == 2 * (((15 * 2 * 64 * 16 + 2 * 64) * 16 + 255) // 256 * 256)
-    b32 = _bytes(flags=Q.FP32)
-    assert b32 == 2 * (((15 * 2 * 64 * 16 + 2 * 64) * 8 + 255) // 256 * 256)
+    up = lambda x: (x + 255) // 256 * 256
+    plane = 2 * 64 * 16
+    for flags, eb in ((0, 16), (Q.FP32, 8)):
+        # two ping-pong state copies (15 planes + phi_prev) and four scratch planes
+        assert _bytes(flags=flags) == 2 * up((15 * plane + 2 * 64) * eb) + up(4 * plane * eb)
 
 
 @pytest.mark.parametrize("bad", [

@@ -20,36 +20,39 @@ def emu():
         dp = ctypes.POINTER(ctypes.c_double)
         L.qds_emu_steps.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
-                                    dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                    dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int]
         _emu = L
     return _emu
 
 
-def run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, nsteps, TX, TR, nth=64):
+def run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, nsteps, TX, TR, nth=64, fused=True):
     dp = ctypes.POINTER(ctypes.c_double)
     out = np.zeros_like(buf)
     s = [None if a is None else np.ascontiguousarray(a, np.complex128) for a in src]
     P = lambda a: None if a is None else a.ctypes.data_as(dp)
     rc = emu().qds_emu_steps(M, P(buf), P(out), nx, nr, 1.0, dr, m_a, g, flags, *[P(a) for a in s],
-                             nsteps, TX, TR, nth)
+                             nsteps, TX, TR, nth, int(fused))
     assert rc == 0
     return out
 
 
 @pytest.mark.parametrize("M,flags", parity_cases())
-@pytest.mark.parametrize("tile", [(8, 32), (5, 3)])
-def test_emulated_kernel_matches_oracle_fp64(M, flags, tile):
+@pytest.mark.parametrize("tile,fused", [((8, 32), True), ((5, 3), True), ((8, 32), False), ((3, 4), False)])
+def test_emulated_kernel_matches_oracle_fp64(M, flags, tile, fused):
     nx, nr = 21, 11
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 100 + flags, M, nx, nr)
     ref = oracle_run(buf, M, nx, nr, dr, flags, 3, g=g, m_a=m_a, src=src)
-    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 3, *tile)
+    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 3, *tile, nth=tile[0] * tile[1] if not fused else 64,
+                  fused=fused)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 1e-13, (name, e)
 
 
+@pytest.mark.parametrize("fused", [True, False])
 @pytest.mark.parametrize("M", [2, 3])
-def test_emulated_kernel_fp32_scaled(M):
+def test_emulated_kernel_fp32_scaled(M, fused):
     nx, nr = 24, 12
     dr, g = stable_dr(M), 1e-6
     flags = 1 | 2 | 4  # axion, regenerated fields, moving window
@@ -60,6 +63,6 @@ def test_emulated_kernel_fp32_scaled(M):
     buf[9 * n:15 * n] *= g * g     # regenerated fields ~ g^2
     src[3] = None
     ref = oracle_run(buf, M, nx, nr, dr, flags, 4, g=g, src=src)
-    got = run_emu(M, buf, nx, nr, dr, 0.0, g, flags | 32, src, 4, 8, 16)
+    got = run_emu(M, buf, nx, nr, dr, 0.0, g, flags | 32, src, 4, 8, 16, nth=128 if not fused else 64, fused=fused)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 2e-6, (name, e)

@@ -11,17 +11,19 @@ pytestmark = pytest.mark.gpu
 
 from paper_2609_03550_b300 import inputs as I  # noqa: E402
 from paper_2609_03550_b300 import qds as Q  # noqa: E402
-from tests._helpers import (group_errors, oracle_run, parity_cases, random_case,  # noqa: E402
-                            reference_and_tolerance, stable_dr)
+from tests._helpers import (fp32_tolerance, group_errors, oracle_run, parity_cases,  # noqa: E402
+                            random_case, reference_and_tolerance, stable_dr)
 
 DEV = "cuda:0"
 
 
-def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=None):
+def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=None, fused=False):
     p = Q.Params(nx, nr, M, dr, g=g, m_a=m_a, flags=flags)
     s = Q.QDSSolver(p, device=DEV)
     if tile:
         s.set_tile(*tile)
+    if fused or tile:
+        s.set_fused(True)
     s.set_state(torch.from_numpy(buf).to(DEV))
     kw = {}
     if src is not None:
@@ -34,14 +36,15 @@ def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=No
     return s.get_state().cpu().numpy(), s
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("M,flags", parity_cases())
-def test_fp64_parity_random_states(M, flags):
+def test_fp64_parity_random_states(M, flags, fused):
     nx, nr = 37, 21
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 100 + flags, M, nx, nr)
     for nsteps in (3, 20):  # 20 steps replays a captured graph
         ref = oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src)
-        got, _ = gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src)
+        got, _ = gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src, fused=fused)
         for name, e in group_errors(got, ref, M, nx, nr).items():
             assert e < 1e-12, (nsteps, name, e)
 
@@ -167,9 +170,10 @@ def test_full_size_first_steps(which):
             if flags & Q.AXION:
                 assert e["axion"] < tol["axion"] and e["arem"] < tol["arem"], (e, tol)
         else:
-            assert e["em"] < 1e-5, e
+            t32 = fp32_tolerance(tol)
+            assert e["em"] < t32["em"], (e, t32)
             if flags & Q.AXION:
-                assert e["axion"] < 1e-4 and e["arem"] < 1e-4, e
+                assert e["axion"] < t32["axion"] and e["arem"] < t32["arem"], (e, t32)
 
 
 def test_batched_uneven_instances_match_single_runs():
