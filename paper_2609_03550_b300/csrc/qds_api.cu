@@ -46,6 +46,8 @@ bool is_scaled(const qds_params &p) { return (p.flags & (QDS_FP32 | QDS_SCALE_G)
 // ghost needs dr >= 1.5 dx, and a mass widens both by (1 + dx m_a)).
 int validate(const qds_params &p) {
   if (p.nx < 8 || p.nr < 4) return fail(QDS_ERR_INVALID_ARG, "nx must be >= 8 and nr >= 4");
+  if ((double)15 * p.n_modes * p.nx * p.nr + (double)p.n_modes * p.nx > 2147483647.0)
+    return fail(QDS_ERR_INVALID_ARG, "one instance must hold fewer than 2^31 state elements");
   if (p.n_modes < 1 || p.n_modes > 4) return fail(QDS_ERR_INVALID_ARG, "n_modes must be 1..4");
   if (p.modes)
     for (int k = 0; k < p.n_modes; k++)
@@ -196,18 +198,24 @@ cudaError_t allow_smem_for(bool fp32, int M, size_t bytes) {
   return cudaErrorInvalidValue;
 }
 
+template <class R, int M, int ST>
+cudaError_t launch_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  pass_kernel<R, M, ST><<<G.ntiles, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_tiles, h->d_ctrl, G.g);
+  return cudaGetLastError();
+}
+
 template <class R, int M>
 cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl, cudaStream_t st) {
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
-  const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, ST_ZERO};
-  for (int st_ : order) {
-    if ((st_ == ST_SOURCE || st_ == ST_PHI) && !ax) continue;
-    if ((st_ == ST_CURRENT || st_ == ST_LEAP1 || st_ == ST_SHIFT1) && !ar) continue;
-    if (st_ == ST_ZERO && !mw) continue;
-    pass_kernel<R, M><<<G.ntiles, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_tiles, h->d_ctrl, G.g, st_);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e;
+  if ((e = launch_pass<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
+  if (ax && (e = launch_pass<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
+  if ((e = launch_pass<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
+  if (ax && (e = launch_pass<R, M, ST_PHI>(h, G, st)) != cudaSuccess) return e;
+  if (ar && (e = launch_pass<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
+  if (ar && (e = launch_pass<R, M, ST_LEAP1>(h, G, st)) != cudaSuccess) return e;
+  if (ar && (e = launch_pass<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
+  if (mw && (e = launch_pass<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -457,7 +465,7 @@ int qds_set_state_i(qds_handle *h, int i, const void *src, void *stream) {
   const double g = p.g;
   const bool sc = is_scaled(p);
   const double s_ax = sc ? 1.0 / g : 1.0, s_ar = sc ? 1.0 / (g * g) : 1.0;
-  const size_t half = instance_bytes(p) / 2;
+  const size_t half = half_bytes(p);
   char *b = h->state + h->inst_off[i];
   if (h->fp32)
     import_kernel<float><<<592, kThreads, 0, st>>>((const double2 *)src, (C<float> *)b, (C<float> *)(b + half),
@@ -479,7 +487,7 @@ int qds_get_state_i(qds_handle *h, int i, void *dst, void *stream) {
   const qds_params &p = h->params[i];
   const bool sc = is_scaled(p);
   const double s_ax = sc ? p.g : 1.0, s_ar = sc ? p.g * p.g : 1.0;
-  const size_t half = instance_bytes(p) / 2;
+  const size_t half = half_bytes(p);
   char *b = h->state + h->inst_off[i];
   if (h->fp32)
     export_kernel<float><<<592, kThreads, 0, st>>>((const C<float> *)b, (const C<float> *)(b + half), h->d_ctrl,
@@ -548,7 +556,7 @@ int qds_diagnostics_i(qds_handle *h, int i, double *out_host, double *profile_de
   const qds_params &p = h->params[i];
   const bool sc = is_scaled(p);
   const double g2 = sc ? p.g * p.g : 1.0;
-  const size_t half = instance_bytes(p) / 2;
+  const size_t half = half_bytes(p);
   char *b = h->state + h->inst_off[i];
   const double pref = 3.14159265358979323846 * p.dr * p.dx;
   if (h->fp32)

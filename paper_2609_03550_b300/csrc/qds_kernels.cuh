@@ -54,12 +54,13 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ i
   }
 }
 
-// One stage of the step over the whole grid, one thread per (x, r) point of
-// a tile, all modes per thread.
-template <class R, int M>
+// One stage ST of the step over the whole grid, one thread per (x, r) point
+// of a tile, all modes per thread; each stage is its own kernel so that it
+// carries only its own registers.
+template <class R, int M, int ST>
 __global__ void __launch_bounds__(256) pass_kernel(const Inst<R> *__restrict__ insts,
                                                    const int4 *__restrict__ tiles,
-                                                   const Ctrl *__restrict__ ctrl, Geo g, int stage) {
+                                                   const Ctrl *__restrict__ ctrl, Geo g) {
   const int4 td = tiles[blockIdx.x];
   const Inst<R> &I = insts[td.x];
   const unsigned long long n = ctrl->step;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(256) pass_kernel(const Inst<R> *__restrict__ i
   t.g = g;
   t.sm = nullptr;
   t.scr = I.scratch;
-  run_stage<R, M, false>(t, stage, threadIdx.x, blockDim.x);
+  run_stage<R, M, false>(t, ST, threadIdx.x, blockDim.x);
 }
 
 __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {

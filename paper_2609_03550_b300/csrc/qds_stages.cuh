@@ -27,7 +27,7 @@
 #endif
 
 #if defined(__CUDACC__)
-#define QDS_NOINL __host__ __device__ __noinline__
+#define QDS_NOINL __host__ __device__ __forceinline__
 #else
 #define QDS_NOINL inline
 #endif
@@ -74,15 +74,35 @@ struct Tile {
 #endif
 
   // ---------------- index helpers ----------------
+  // Element offsets within one instance fit in 32 bits (checked at create).
+  // The ring slots of the columns cw-1 .. cw+2 around the point being
+  // computed are cached (set_point); other columns take the general path.
+  int cw;              // window position the cache refers to
+  int cs0, cs1, cs2, cs3;  // slot(cw-1) .. slot(cw+2), -1 outside the window
   QDS_HD bool cell_ok(int w) const { return per || (w >= 0 && w < nx); }
   QDS_HD bool face_ok(int w) const { return per || (w >= 0 && w <= nx - 2); }
-  QDS_HD int slot(int w) const {
+  QDS_HD int slot_slow(int w) const {
     if (per) { w %= nx; if (w < 0) w += nx; return w; }
     int q = w + s;
     return q >= nx ? q - nx : q;
   }
+  QDS_HD void set_point(int w) {
+    cw = w;
+    cs0 = cell_ok(w - 1) ? slot_slow(w - 1) : -1;
+    cs1 = cell_ok(w) ? slot_slow(w) : -1;
+    cs2 = cell_ok(w + 1) ? slot_slow(w + 1) : -1;
+    cs3 = cell_ok(w + 2) ? slot_slow(w + 2) : -1;
+  }
+  QDS_HD int slot(int w) const {
+    const int d = w - cw;
+    if (d == -1) return cs0;
+    if (d == 0) return cs1;
+    if (d == 1) return cs2;
+    if (d == 2) return cs3;
+    return slot_slow(w);
+  }
   QDS_HD size_t gidx(int field, int k, int w, int j) const {
-    return (size_t)field * P + ((size_t)k * nx + slot(w)) * nr + j;
+    return (size_t)((unsigned)field * (unsigned)P + ((unsigned)k * (unsigned)nx + (unsigned)slot(w)) * (unsigned)nr + (unsigned)j);
   }
   QDS_HD C<R> cell(int field, int k, int w, int j) const {
     if (!cell_ok(w) || j < 0 || j >= nr) return zero<R>();
@@ -605,7 +625,7 @@ QDS_NOINL void current_point(const Tile<R, M, SM> &t, int lx, int lr) {
 enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, N_STAGE, ST_ZERO = N_STAGE };
 
 template <class R, int M, bool SM>
-QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
+QDS_HD void run_stage(Tile<R, M, SM> t, int st, int tid, int nth) {
   const Geo &g = t.g;
   const uint32_t fl = t.I->flags;
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0;
@@ -619,6 +639,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
     // pass mode, moving window: the rear column of every field becomes the
     // new (empty) front column once all passes have read it
     if (SM || !t.mw || t.x0 != 0) return;
+    t.set_point(0);
     for (int q = tid; q < g.TR; q += nth) {
       const int j = t.r0 + q;
       if (j >= t.nr) continue;
@@ -635,6 +656,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
     for (int q = tid; q < npt; q += nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
       const int w = t.x0 + lx, j = t.r0 + lr;
+      t.set_point(w);
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
       for (int k = 0; k < M; k++) {
@@ -658,6 +680,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
       if (!SM && !t.owned(xa + q / nrr, ra + q % nrr)) continue;
+      t.set_point(t.x0 + xa + q / nrr);
       source_point(t, xa + q / nrr, ra + q % nrr);
     }
   } else if (st == ST_SHIFT0) {
@@ -668,6 +691,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
     for (int q = tid; q < npt; q += nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
       const int c = t.x0 + lx, j = t.r0 + lr;
+      t.set_point(c - 1);  // the shift reads cells c-1 .. c+1
       const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
       const bool own = t.owned(lx, lr);
 #pragma unroll 1
@@ -707,6 +731,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
       if (!SM && !t.owned(lx, lr)) continue;
       const int w = t.x0 + lx, j = t.r0 + lr;
+      t.set_point(w);
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
       for (int k = 0; k < M; k++) {
@@ -727,6 +752,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
       if (!SM && !t.owned(xa + q / nrr, ra + q % nrr)) continue;
+      t.set_point(t.x0 + xa + q / nrr);
       current_point(t, xa + q / nrr, ra + q % nrr);
     }
   } else if (st == ST_LEAP1) {
@@ -737,6 +763,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
       if (!SM && !t.owned(lx, lr)) continue;
       const int w = t.x0 + lx, j = t.r0 + lr;
+      t.set_point(w);
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
       for (int k = 0; k < M; k++) {
@@ -759,6 +786,7 @@ QDS_HD void run_stage(const Tile<R, M, SM> &t, int st, int tid, int nth) {
       const int lx = q / g.TR, lr = q % g.TR;
       if (!t.owned(lx, lr)) continue;
       const int c = t.x0 + lx, j = t.r0 + lr;
+      t.set_point(c - 1);
 #pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> tp, tm, up, um;
