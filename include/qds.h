@@ -145,6 +145,32 @@ int qds_get_tile(qds_handle *h, int *tx, int *tr, int *ntiles, int *smem_bytes);
 void qds_free(qds_handle *h);
 const char *qds_last_error(void);
 
+/* ---------------------------------------------------------------------------
+ * No-allocation step (this entry point has no counterpart in the paper; it
+ * serves callers that cannot allocate device memory: code inside runtimes
+ * or memory pools that forbid allocation after start-up, plug-ins that must
+ * not grow a host application's device footprint, real-time loops where an
+ * allocation may stall or fail).
+ *
+ * Imports the canonical complex128 state state_in_dev, advances it nsteps
+ * steps (pass-mode kernels, no sources) and exports it to state_out_dev
+ * (which may equal state_in_dev).  work_dev (>= qds_state_bytes(p) bytes,
+ * 256-byte aligned, caller-owned) holds the two working copies of the
+ * state.  The descriptor, step counter, tile table and the four scratch
+ * planes live in one static device array of QDS_NOALLOC_SCRATCH_BYTES
+ * bytes that every GPU loading the library holds until exit; a statement
+ * whose scratch does not fit returns QDS_ERR_INVALID_ARG.  No cudaMalloc,
+ * cudaFree or graph instantiation is made.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the array: the call rewrites the descriptor and clears the
+ * scratch on entry, synchronises the stream once during that set-up, and
+ * calls that overlap on the GPU (other streams, other threads) race.
+ * ------------------------------------------------------------------------- */
+#define QDS_NOALLOC_SCRATCH_BYTES (32u << 20)
+int qds_advance_noalloc(const qds_params *p, const void *state_in_dev, void *state_out_dev,
+                        void *work_dev, size_t work_bytes, int nsteps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,10 @@ Geo pick_geo(const qds_params &p, int override_tx, int override_tr) {
 
 }  // namespace
 
+// Internal (not part of the C ABI): lets the other translation unit of the
+// library report through qds_last_error().
+__attribute__((visibility("hidden"))) void qds_internal_set_error(const std::string &m) { g_err = m; }
+
 struct qds_handle {
   int n_inst = 0;
   std::vector<qds_params> params;

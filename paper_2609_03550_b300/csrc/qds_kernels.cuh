@@ -89,11 +89,11 @@ __global__ void __launch_bounds__(256) pass_kernel(const Inst<R> *__restrict__ i
   run_stage<R, M, false>(t, ST, threadIdx.x, blockDim.x);
 }
 
-__global__ void advance_kernel(Ctrl *ctrl, int nsteps) {
+static __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {
   if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->step += (unsigned long long)nsteps;
 }
 
-__global__ void reset_kernel(Ctrl *ctrl) {
+static __global__ void reset_kernel(Ctrl *ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) { ctrl->step = 0; ctrl->err = 0; }
 }
 
@@ -250,7 +250,7 @@ __global__ void diag_partial_all_kernel(const Inst<R> *__restrict__ insts, const
 }
 
 // scal[i] = {pi dr dx, g^2 or 1, g^4 or 1, g^2 or 1} per instance
-__global__ void diag_final_all_kernel(const double *partial, int nblk, const double4 *scal, int n, double *out) {
+static __global__ void diag_final_all_kernel(const double *partial, int nblk, const double4 *scal, int n, double *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Neu s[4];
@@ -263,7 +263,7 @@ __global__ void diag_final_all_kernel(const double *partial, int nblk, const dou
   out[4 * i + 3] = 2.0 * f.x * s[3].val() * f.w;
 }
 
-__global__ void diag_final_kernel(const double *partial, int nblk, double pref, double s_ax2, double s_ar2,
+static __global__ void diag_final_kernel(const double *partial, int nblk, double pref, double s_ax2, double s_ar2,
                                   double s_cross, double *out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Neu s[4];

@@ -70,6 +70,7 @@ def lib():
             "qds_get_tile": (i, [H, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
             "qds_free": (None, [H]),
             "qds_last_error": (ctypes.c_char_p, []),
+            "qds_advance_noalloc": (i, [P, vp, vp, vp, sz, i, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
