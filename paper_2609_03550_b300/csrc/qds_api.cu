@@ -118,8 +118,9 @@ struct qds_handle {
     int M;
     Geo g;
     Smem L;
-    int4 *d_tiles = nullptr;
+    int4 *d_tiles = nullptr;  // pass mode: interior tiles first, then edge tiles
     int ntiles = 0;
+    int n_interior = 0;       // pass mode: tiles whose halo lies inside the window
   };
   std::vector<Group> groups;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
@@ -204,7 +205,11 @@ cudaError_t allow_smem_for(bool fp32, int M, size_t bytes) {
 
 template <class R, int M, int ST>
 cudaError_t launch_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
-  pass_kernel<R, M, ST><<<G.ntiles, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_tiles, h->d_ctrl, G.g);
+  if (G.n_interior > 0)
+    pass_kernel<R, M, ST, true><<<G.n_interior, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_tiles, h->d_ctrl, G.g);
+  if (G.ntiles > G.n_interior)
+    pass_kernel<R, M, ST, false><<<G.ntiles - G.n_interior, kThreads, 0, st>>>(
+        (const Inst<R> *)h->d_inst, G.d_tiles + G.n_interior, h->d_ctrl, G.g);
   return cudaGetLastError();
 }
 
@@ -349,12 +354,19 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
       P.g.TX = kThreads / 32;
       P.g.TR = 32;
       P.L = Smem{};
-      std::vector<int4> pt;
+      std::vector<int4> pt, edge;
       for (int i = 0; i < n; i++) {
         if (params[i].n_modes != M) continue;
+        const bool per = (params[i].flags & QDS_X_PERIODIC) != 0;
         for (int x0 = 0; x0 < params[i].nx; x0 += P.g.TX)
-          for (int r0 = 0; r0 < params[i].nr; r0 += P.g.TR) pt.push_back(make_int4(i, x0, r0, 0));
+          for (int r0 = 0; r0 < params[i].nr; r0 += P.g.TR) {
+            // interior: columns x0-2 .. x0+TX+1 are cells and x0+TX is a real face
+            const bool inner = per ? (params[i].nx >= P.g.TX + 4) : (x0 >= 2 && x0 + P.g.TX + 2 <= params[i].nx - 1);
+            (inner ? pt : edge).push_back(make_int4(i, x0, r0, 0));
+          }
       }
+      P.n_interior = (int)pt.size();
+      pt.insert(pt.end(), edge.begin(), edge.end());
       P.ntiles = (int)pt.size();
       CU(cudaMalloc(&P.d_tiles, sizeof(int4) * pt.size()));
       CU(cudaMemcpy(P.d_tiles, pt.data(), sizeof(int4) * pt.size(), cudaMemcpyHostToDevice));

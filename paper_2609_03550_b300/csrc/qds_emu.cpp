@@ -72,7 +72,9 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
       if (st == ST_ZERO && !mw) continue;
       for (int x0 = 0; x0 < nx; x0 += TX)
         for (int r0 = 0; r0 < nr; r0 += TR) {
-          Tile<R, M, false> t;
+          const bool per_ = (flags & F_X_PERIODIC) != 0;
+          const bool inner = per_ ? (nx >= TX + 4) : (x0 >= 2 && x0 + TX + 2 <= nx - 1);
+          Tile<R, M, false, false> t;
           t.I = &I;
           t.nx = nx; t.nr = nr; t.J = nr - 1;
           t.x0 = x0; t.r0 = r0;
@@ -90,7 +92,13 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
           t.scr = scratch.data();
           t.state_len = E;
           t.sm_len = 0;
-          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false>(t, st, tid, nthreads);
+          if (inner) {
+            Tile<R, M, false, true> tf;
+            std::memcpy((void *)&tf, (const void *)&t, sizeof t);
+            for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false, true>(tf, st, tid, nthreads);
+          } else {
+            for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false, false>(t, st, tid, nthreads);
+          }
         }
     }
   }

@@ -57,14 +57,18 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ i
 // One stage ST of the step over the whole grid, one thread per (x, r) point
 // of a tile, all modes per thread; each stage is its own kernel so that it
 // carries only its own registers.
-template <class R, int M, int ST>
-__global__ void __launch_bounds__(256) pass_kernel(const Inst<R> *__restrict__ insts,
-                                                   const int4 *__restrict__ tiles,
-                                                   const Ctrl *__restrict__ ctrl, Geo g) {
+//
+// FAST: the tile list holds only tiles whose halo lies inside the window
+// (checks skipped).  The heavy stages (axion source and current) keep their
+// registers; the light ones are held to three CTAs per SM.
+template <class R, int M, int ST, bool FAST>
+__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 2 : 3)
+    pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
+                const Ctrl *__restrict__ ctrl, Geo g) {
   const int4 td = tiles[blockIdx.x];
   const Inst<R> &I = insts[td.x];
   const unsigned long long n = ctrl->step;
-  Tile<R, M, false> t;
+  Tile<R, M, false, FAST> t;
   t.I = &I;
   t.nx = I.nx;
   t.nr = I.nr;
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(256) pass_kernel(const Inst<R> *__restrict__ i
   t.g = g;
   t.sm = nullptr;
   t.scr = I.scratch;
-  run_stage<R, M, false>(t, ST, threadIdx.x, blockDim.x);
+  run_stage<R, M, false, FAST>(t, ST, threadIdx.x, blockDim.x);
 }
 
 static __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {
@@ -169,21 +173,35 @@ struct Neu {
   __device__ double val() const { return s + c; }
 };
 
+// Compensated (Neumaier) running sum in the working precision R; the
+// per-thread sums are then combined in FP64.
 template <class R>
-__device__ __forceinline__ double nrm(C<R> a) { return (double)a.re * a.re + (double)a.im * a.im; }
+struct NeuR {
+  R s = R(0), c = R(0);
+  __device__ void add(R x) {
+    R t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  __device__ double val() const { return (double)s + (double)c; }
+};
+
 template <class R>
-__device__ __forceinline__ double dotre(C<R> a, C<R> b) { return (double)a.re * b.re + (double)a.im * b.im; }
+__device__ __forceinline__ R nrmR(C<R> a) { return a.re * a.re + a.im * a.im; }
+template <class R>
+__device__ __forceinline__ R dotR(C<R> a, C<R> b) { return a.re * b.re + a.im * b.im; }
 
 // Energy densities of one (mode, x, r) element of one instance, added to the
 // four accumulators em0, axion, em1, cross (without the common prefactor).
 template <class R>
-__device__ __forceinline__ void diag_element(const C<R> *S, size_t P, size_t q, int nx, int nr, double dr,
-                                             double ma2, Neu &a0, Neu &a1, Neu &a2, Neu &a3) {
+__device__ __forceinline__ void diag_element(const C<R> *S, size_t P, size_t q, int nx, int nr, R dr,
+                                             R ma2, NeuR<R> &a0, NeuR<R> &a1, NeuR<R> &a2, NeuR<R> &a3) {
   const int j = (int)(q % nr);
   const int k = (int)(q / ((size_t)nx * nr));
-  const double wm = k == 0 ? 1.0 : 0.5;
-  const double rh = (j + 0.5) * dr, rs = j == 0 ? dr / 8.0 : j * dr;
-  double e[2];
+  const R wm = k == 0 ? R(1) : R(0.5);
+  const R rh = (R(j) + R(0.5)) * dr, rs = j == 0 ? dr / R(8) : R(j) * dr;
+  R e[2];
   C<R> er[2], bt[2], et[2], br[2], ex[2], bx[2];
   for (int gi = 0; gi < 2; gi++) {
     const int o = gi ? TRP1 : TRP;
@@ -192,23 +210,24 @@ __device__ __forceinline__ void diag_element(const C<R> *S, size_t P, size_t q, 
     er[gi] = R(0.5) * (tp + tm); bt[gi] = R(0.5) * (tp - tm);
     et[gi] = R(0.5) * (up + um); br[gi] = R(0.5) * (up - um);
     ex[gi] = S[(size_t)(o + 4) * P + q]; bx[gi] = S[(size_t)(o + 5) * P + q];
-    e[gi] = rh * (nrm(er[gi]) + nrm(bt[gi])) + rs * (nrm(et[gi]) + nrm(br[gi])) + rs * nrm(ex[gi]) + rh * nrm(bx[gi]);
+    e[gi] = rh * (nrmR(er[gi]) + nrmR(bt[gi])) + rs * (nrmR(et[gi]) + nrmR(br[gi])) + rs * nrmR(ex[gi]) + rh * nrmR(bx[gi]);
   }
   a0.add(wm * e[0]);
   a2.add(wm * e[1]);
   C<R> ph = S[(size_t)PHI * P + q], ap = S[(size_t)TAP * P + q], am = S[(size_t)TAM * P + q];
-  double ua = rh * 0.5 * (nrm(ap) + nrm(am)) + rh * ((double)k * k / (rh * rh) + ma2) * nrm(ph);
+  R ua = rh * R(0.5) * (nrmR(ap) + nrmR(am)) + rh * (R(k * k) / (rh * rh) + ma2) * nrmR(ph);
   if (j > 0) {
     C<R> d = S[(size_t)PHI * P + q] - S[(size_t)PHI * P + q - 1];
-    ua += (j * dr) * nrm(d) / (dr * dr);
+    ua += (R(j) * dr) * nrmR(d) / (dr * dr);
   }
   a1.add(wm * ua);
-  double cr = rh * (dotre(er[0], er[1]) + dotre(bt[0], bt[1])) + rs * (dotre(et[0], et[1]) + dotre(br[0], br[1])) +
-              rs * dotre(ex[0], ex[1]) + rh * dotre(bx[0], bx[1]);
+  R cr = rh * (dotR(er[0], er[1]) + dotR(bt[0], bt[1])) + rs * (dotR(et[0], et[1]) + dotR(br[0], br[1])) +
+         rs * dotR(ex[0], ex[1]) + rh * dotR(bx[0], bx[1]);
   a3.add(wm * cr);
 }
 
-__device__ __forceinline__ void block_reduce4(Neu &a0, Neu &a1, Neu &a2, Neu &a3, double *dst) {
+template <class A>
+__device__ __forceinline__ void block_reduce4(A &a0, A &a1, A &a2, A &a3, double *dst) {
   __shared__ double red[4][256];
   red[0][threadIdx.x] = a0.val();
   red[1][threadIdx.x] = a1.val();
@@ -230,9 +249,9 @@ __global__ void diag_partial_kernel(const C<R> *__restrict__ b0, const C<R> *__r
                                     int M, int nx, int nr, double dr, double ma2, double *partial) {
   const C<R> *S = (ctrl->step & 1ull) ? b1 : b0;
   const size_t P = plane_elems(M, nx, nr);
-  Neu a0, a1, a2, a3;
+  NeuR<R> a0, a1, a2, a3;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x)
-    diag_element(S, P, q, nx, nr, dr, ma2, a0, a1, a2, a3);
+    diag_element<R>(S, P, q, nx, nr, (R)dr, (R)ma2, a0, a1, a2, a3);
   block_reduce4(a0, a1, a2, a3, partial + blockIdx.x * 4);
 }
 
@@ -242,10 +261,9 @@ __global__ void diag_partial_all_kernel(const Inst<R> *__restrict__ insts, const
   const Inst<R> &I = insts[blockIdx.y];
   const C<R> *S = I.state[ctrl->step & 1ull];
   const size_t P = plane_elems(I.M, I.nx, I.nr);
-  const double dr = (double)I.dr, ma2 = (double)I.ma2;
-  Neu a0, a1, a2, a3;
+  NeuR<R> a0, a1, a2, a3;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x)
-    diag_element(S, P, q, I.nx, I.nr, dr, ma2, a0, a1, a2, a3);
+    diag_element<R>(S, P, q, I.nx, I.nr, I.dr, I.ma2, a0, a1, a2, a3);
   block_reduce4(a0, a1, a2, a3, partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4);
 }
 
@@ -294,8 +312,8 @@ __global__ void profile_kernel(const C<R> *__restrict__ b0, const C<R> *__restri
     C<R> up = S[(size_t)TTP * P + e], um = S[(size_t)TTM * P + e];
     const double wm = k == 0 ? 1.0 : 0.5;
     const double rh = (j + 0.5) * dr, rs = j == 0 ? dr / 8.0 : j * dr;
-    acc.add(wm * (rh * (nrm(R(0.5) * (tp + tm)) + nrm(R(0.5) * (tp - tm))) +
-                  rs * (nrm(R(0.5) * (up + um)) + nrm(R(0.5) * (up - um)))));
+    acc.add(wm * (rh * ((double)nrmR(R(0.5) * (tp + tm)) + (double)nrmR(R(0.5) * (tp - tm))) +
+                  rs * ((double)nrmR(R(0.5) * (up + um)) + (double)nrmR(R(0.5) * (up - um)))));
   }
   __shared__ double red[256];
   red[threadIdx.x] = acc.val();

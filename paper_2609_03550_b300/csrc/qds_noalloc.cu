@@ -74,14 +74,14 @@ cudaError_t run_steps(const Inst<R> *d_inst, const int4 *d_tiles, int ntiles, Ct
   g.TX = kTX;
   g.TR = kTR;
   for (int n = 0; n < nsteps; n++) {
-    pass_kernel<R, M, ST_LEAP0><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (ax) pass_kernel<R, M, ST_SOURCE><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    pass_kernel<R, M, ST_SHIFT0><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (ax) pass_kernel<R, M, ST_PHI><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (ar) pass_kernel<R, M, ST_CURRENT><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (ar) pass_kernel<R, M, ST_LEAP1><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (ar) pass_kernel<R, M, ST_SHIFT1><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (mw) pass_kernel<R, M, ST_ZERO><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    pass_kernel<R, M, ST_LEAP0, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    if (ax) pass_kernel<R, M, ST_SOURCE, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    pass_kernel<R, M, ST_SHIFT0, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    if (ax) pass_kernel<R, M, ST_PHI, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    if (ar) pass_kernel<R, M, ST_CURRENT, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    if (ar) pass_kernel<R, M, ST_LEAP1, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    if (ar) pass_kernel<R, M, ST_SHIFT1, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
+    if (mw) pass_kernel<R, M, ST_ZERO, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
     advance_kernel<<<1, 32, 0, st>>>(d_ctrl, 1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -52,7 +52,10 @@ QDS_HD C<R> ldg(const C<R> *p) {
 // SM = true: the fused step, intermediates in the CTA's shared memory with
 // halos recomputed per tile.  SM = false: one pass per stage over the whole
 // grid, intermediates in the new state buffer and the scratch planes.
-template <class R, int M, bool SM = true>
+// FAST = true: every access of the tile (its halo included) lies inside the
+// window, so the accessors skip their checks (the formulas themselves only
+// touch rows 0..nr-1).
+template <class R, int M, bool SM = true, bool FAST = false>
 struct Tile {
   const Inst<R> *I;
   int nx, nr, J;       // J = nr - 1: last integer row / last half row
@@ -81,17 +84,19 @@ struct Tile {
   int cs0, cs1, cs2, cs3;  // slot(cw-1) .. slot(cw+2), -1 outside the window
   QDS_HD bool cell_ok(int w) const { return per || (w >= 0 && w < nx); }
   QDS_HD bool face_ok(int w) const { return per || (w >= 0 && w <= nx - 2); }
+  // slot of window position w, or -1 outside the window (non-periodic)
   QDS_HD int slot_slow(int w) const {
     if (per) { w %= nx; if (w < 0) w += nx; return w; }
+    if (w < 0 || w >= nx) return -1;
     int q = w + s;
     return q >= nx ? q - nx : q;
   }
   QDS_HD void set_point(int w) {
     cw = w;
-    cs0 = cell_ok(w - 1) ? slot_slow(w - 1) : -1;
-    cs1 = cell_ok(w) ? slot_slow(w) : -1;
-    cs2 = cell_ok(w + 1) ? slot_slow(w + 1) : -1;
-    cs3 = cell_ok(w + 2) ? slot_slow(w + 2) : -1;
+    cs0 = slot_slow(w - 1);
+    cs1 = slot_slow(w);
+    cs2 = slot_slow(w + 1);
+    cs3 = slot_slow(w + 2);
   }
   QDS_HD int slot(int w) const {
     const int d = w - cw;
@@ -101,22 +106,37 @@ struct Tile {
     if (d == 2) return cs3;
     return slot_slow(w);
   }
-  QDS_HD size_t gidx(int field, int k, int w, int j) const {
-    return (size_t)((unsigned)field * (unsigned)P + ((unsigned)k * (unsigned)nx + (unsigned)slot(w)) * (unsigned)nr + (unsigned)j);
+  QDS_HD unsigned eidx(int field, int k, int sl, int j) const {
+    return (unsigned)field * (unsigned)P + ((unsigned)k * (unsigned)nx + (unsigned)sl) * (unsigned)nr + (unsigned)j;
   }
+  QDS_HD size_t gidx(int field, int k, int w, int j) const { return eidx(field, k, slot(w), j); }
   QDS_HD C<R> cell(int field, int k, int w, int j) const {
-    if (!cell_ok(w) || j < 0 || j >= nr) return zero<R>();
+    const int sl = slot(w);
+    if (FAST) {  // the tile and its halo lie inside the window
 #if defined(QDS_EMU)
-    QDS_CHECK(gidx(field, k, w, j) < state_len, "cell read");
+      QDS_CHECK(j >= 0 && j < nr && sl >= 0, "unchecked cell access");
 #endif
-    return ldg(o + gidx(field, k, w, j));
+      return ldg(o + eidx(field, k, sl, j));
+    }
+    if (sl < 0 || (unsigned)j >= (unsigned)nr) return zero<R>();
+#if defined(QDS_EMU)
+    QDS_CHECK(eidx(field, k, sl, j) < state_len, "cell read");
+#endif
+    return ldg(o + eidx(field, k, sl, j));
   }
   QDS_HD C<R> face(int field, int k, int w, int j) const {
-    if (!face_ok(w) || j < 0 || j >= nr) return zero<R>();
+    const int sl = slot(w);
+    if (FAST) {
 #if defined(QDS_EMU)
-    QDS_CHECK(gidx(field, k, w, j) < state_len, "face read");
+      QDS_CHECK(j >= 0 && j < nr && sl >= 0 && (per || w <= nx - 2), "unchecked face access");
 #endif
-    return ldg(o + gidx(field, k, w, j));
+      return ldg(o + eidx(field, k, sl, j));
+    }
+    if (sl < 0 || (!per && w == nx - 1) || (unsigned)j >= (unsigned)nr) return zero<R>();
+#if defined(QDS_EMU)
+    QDS_CHECK(eidx(field, k, sl, j) < state_len, "face read");
+#endif
+    return ldg(o + eidx(field, k, sl, j));
   }
   QDS_HD C<R> prev(int k, int w) const {
     if (!face_ok(w)) return zero<R>();
@@ -157,6 +177,12 @@ struct Tile {
   // nx-1 included, so that it is written as zero each step); positions
   // outside the window read as zero.
   QDS_HD C<R> &gnew(int field, int k, int w, int j, bool /*face_pos*/) const {
+    if (FAST) {
+#if defined(QDS_EMU)
+      QDS_CHECK(cell_ok(w) && j >= 0 && j < nr, "unchecked new-state access");
+#endif
+      return n[eidx(field, k, slot(w), j)];
+    }
     const bool ok = cell_ok(w) && j >= 0 && j < nr;
     if (!ok) { dummy = zero<R>(); return dummy; }
 #if defined(QDS_EMU)
@@ -165,6 +191,7 @@ struct Tile {
     return n[gidx(field, k, w, j)];
   }
   QDS_HD C<R> &gscr(int plane, int k, int w, int j) const {
+    if (FAST) return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * nr + j];
     if (!cell_ok(w) || j < 0 || j >= nr) { dummy = zero<R>(); return dummy; }
     return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * nr + j];
   }
@@ -246,8 +273,8 @@ QDS_HD C<R> conv(int m, const C<R> *A, const C<R> *B) {
 // conservative form, (1/r) d(r F)/dr = (r_+ F_+ - r_- F_-)/(r dr), which is
 // algebraically the paper's average-plus-centred-difference form.
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM>
-QDS_NOINL C<R> ex_update(const Tile<R, M, SM> &t, int grp, int k, int w, int j, C<R> jx) {
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL C<R> ex_update(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, int j, C<R> jx) {
   C<R> e0 = t.face(grp + EX, k, w, j);
   if (j == 0) {
     if (k != 0) return zero<R>();
@@ -263,8 +290,8 @@ QDS_NOINL C<R> ex_update(const Tile<R, M, SM> &t, int grp, int k, int w, int j, 
   return e0 + t.h * gx;
 }
 
-template <class R, int M, bool SM>
-QDS_NOINL C<R> bx_interior(const Tile<R, M, SM> &t, int grp, int k, int w, int j) {
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL C<R> bx_interior(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, int j) {
   C<R> b0 = t.face(grp + BX, k, w, j);
   R rh = (R(j) + R(0.5)) * t.dr;
   C<R> elo = R(0.5) * (t.Et(grp, k, w, j) + t.Et(grp, k, w + 1, j));
@@ -276,8 +303,8 @@ QDS_NOINL C<R> bx_interior(const Tile<R, M, SM> &t, int grp, int k, int w, int j
 
 // Outer half row J+1/2, Eq. em_r_open_bx by the box scheme over
 // [r_{J-1/2}, r_{J+1/2}] x [t^{n-1/2}, t^{n+1/2}], right side at (x_{w+1/2}, r_J, t^n).
-template <class R, int M, bool SM>
-QDS_NOINL C<R> bx_outer(const Tile<R, M, SM> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL C<R> bx_outer(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
   const int J = t.J;
   R rJ = R(J) * t.dr;
   C<R> dxbr = t.ih * (t.Br(grp, k, w + 1, J) - t.Br(grp, k, w, J));
@@ -295,9 +322,9 @@ QDS_NOINL C<R> bx_outer(const Tile<R, M, SM> &t, int grp, int k, int w, C<R> jt_
 // from the tile's shared memory and x-averages the caller's cell currents;
 // group 1 (the regenerated field) reads E_x1, B_x1 and j_a from shared memory.
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM>
+template <class R, int M, bool SM, bool FAST>
 struct Faces0 {
-  const Tile<R, M, SM> &t;
+  const Tile<R, M, SM, FAST> &t;
   QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sA(0, k, lx, lr); }
   QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sA(1, k, lx, lr); }
   QDS_HD C<R> jr(int k, int lx, int lr) const {
@@ -317,9 +344,9 @@ struct Faces0 {
   }
 };
 
-template <class R, int M, bool SM>
+template <class R, int M, bool SM, bool FAST>
 struct Faces1 {
-  const Tile<R, M, SM> &t;
+  const Tile<R, M, SM, FAST> &t;
   QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sJ(0, k, lx, lr); }
   QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sJ(1, k, lx, lr); }
   QDS_HD C<R> jx(int k, int lx, int lr) const { return t.sJ(2, k, lx, lr); }
@@ -333,8 +360,8 @@ struct Faces1 {
 // behind through face c-1, T_r^- and T_th^+ from the cell ahead through face
 // c.  Axis rules of Sec. 2.3 (Eq. axis_Ttheta; T_th^(m!=1) = 0 on the axis).
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM, class FS>
-QDS_NOINL void tr_interior(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, int lx, int lr,
+template <class R, int M, bool SM, bool FAST, class FS>
+QDS_NOINL void tr_interior(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, int k, int lx, int lr,
                         C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   R rh = (R(j) + R(0.5)) * t.dr;
@@ -356,8 +383,8 @@ QDS_NOINL void tr_interior(const Tile<R, M, SM> &t, const FS &fs, int grp, int k
 // Outer half row: E_r by the shift with the Gamma_r source alone, B_theta by
 // the box scheme of Eq. em_r_open_bt over [r_{J-1/2}, r_{J+1/2}] x [t^n, t^{n+1}]
 // with its right side from time-n fields.
-template <class R, int M, bool SM, class FS>
-QDS_NOINL void tr_outer(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
+template <class R, int M, bool SM, bool FAST, class FS>
+QDS_NOINL void tr_outer(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
                      int lr_J, C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, J = t.J;
   R rh = (R(J) + R(0.5)) * t.dr, rJ = R(J) * t.dr;
@@ -379,8 +406,8 @@ QDS_NOINL void tr_outer(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, i
   tm = er_new - bt_new;
 }
 
-template <class R, int M, bool SM, class FS>
-QDS_NOINL void tt_update(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, int lx, int lr,
+template <class R, int M, bool SM, bool FAST, class FS>
+QDS_NOINL void tt_update(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, int k, int lx, int lr,
                       C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   if (j == 0 && k != 1) { tp = zero<R>(); tm = zero<R>(); return; }
@@ -412,8 +439,8 @@ QDS_NOINL void tt_update(const Tile<R, M, SM> &t, const FS &fs, int grp, int k, 
 // exterior phi comes from the outgoing condition (d_t + c d_r) phi = 0
 // centred at r_J (Eq. axion_r_ghost) with d_t phi taken half a step back.
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM>
-QDS_NOINL void source_point(const Tile<R, M, SM> &t, int lx, int lr) {
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) t.sG(k, lx, lr) = zero<R>();
@@ -473,8 +500,8 @@ QDS_NOINL void source_point(const Tile<R, M, SM> &t, int lx, int lr) {
 // Below the axis a scalar on half rows mirrors with parity (-1)^l; E_r and
 // B_theta below the axis follow the T_r ghost of Eq. axis_Tr.
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM>
-QDS_NOINL void current_point(const Tile<R, M, SM> &t, int lx, int lr) {
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) for (int q = 2; q < 5; q++) t.sJ(q, k, lx, lr) = zero<R>();
@@ -624,8 +651,8 @@ QDS_NOINL void current_point(const Tile<R, M, SM> &t, int lx, int lr) {
 // ---------------------------------------------------------------------------
 enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, N_STAGE, ST_ZERO = N_STAGE };
 
-template <class R, int M, bool SM>
-QDS_HD void run_stage(Tile<R, M, SM> t, int st, int tid, int nth) {
+template <class R, int M, bool SM, bool FAST = false>
+QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
   const Geo &g = t.g;
   const uint32_t fl = t.I->flags;
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0;
@@ -655,6 +682,7 @@ QDS_HD void run_stage(Tile<R, M, SM> t, int st, int tid, int nth) {
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
+      if (!SM && !t.owned(lx, lr)) continue;  // pass mode: points of the grid only
       const int w = t.x0 + lx, j = t.r0 + lr;
       t.set_point(w);
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
@@ -684,12 +712,13 @@ QDS_HD void run_stage(Tile<R, M, SM> t, int st, int tid, int nth) {
       source_point(t, xa + q / nrr, ra + q % nrr);
     }
   } else if (st == ST_SHIFT0) {
-    Faces0<R, M, SM> fs{t};
+    Faces0<R, M, SM, FAST> fs{t};
     if (ax) region(g.t_x0(), g.t_nx(), g.t_r0(), g.t_nr(), xa, nxr, ra, nrr);
     else { xa = 0; nxr = g.TX; ra = 0; nrr = g.TR; }
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
+      if (!SM && !t.owned(lx, lr)) continue;  // pass mode: points of the grid only
       const int c = t.x0 + lx, j = t.r0 + lr;
       t.set_point(c - 1);  // the shift reads cells c-1 .. c+1
       const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
@@ -780,7 +809,7 @@ QDS_HD void run_stage(Tile<R, M, SM> t, int st, int tid, int nth) {
     }
   } else if (st == ST_SHIFT1) {
     if (!ar) return;
-    Faces1<R, M, SM> fs{t};
+    Faces1<R, M, SM, FAST> fs{t};
     const int npt = g.TX * g.TR;
     for (int q = tid; q < npt; q += nth) {
       const int lx = q / g.TR, lr = q % g.TR;
