@@ -180,3 +180,72 @@ extern "C" int qds_emu_steps(int M, const double *canon, double *out, int nx, in
     return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads, fused);
   return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads, fused);
 }
+
+// ---------------------------------------------------------------------------
+// Host emulation of the adjoint step (qds_adjoint.cuh), for CPU tests only.
+#include "qds_adjoint.cuh"
+
+namespace {
+
+template <class R, int M>
+void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int nx, int nr, double h, double dr,
+                 double m_a, double g, uint32_t flags, const double *jx, const double *jt, double *dg) {
+  const size_t P = plane_elems(M, nx, nr), E = state_elems(M, nx, nr);
+  std::vector<C<R>> F(E), LN(E), LO(E), SB((size_t)N_SB * P);
+  for (size_t q = 0; q < E; q++) {
+    F[q] = mk<R>((R)fwd[2 * q], (R)fwd[2 * q + 1]);
+    LN[q] = mk<R>((R)lam_new[2 * q], (R)lam_new[2 * q + 1]);
+    LO[q] = mk<R>((R)1e30, (R)1e30);  // every entry must be written
+  }
+  std::vector<C<R>> sjx, sjt;
+  if (jx) { sjx.resize(P); for (size_t q = 0; q < P; q++) sjx[q] = mk<R>((R)jx[2 * q], (R)jx[2 * q + 1]); }
+  if (jt) { sjt.resize(P); for (size_t q = 0; q < P; q++) sjt[q] = mk<R>((R)jt[2 * q], (R)jt[2 * q + 1]); }
+  Inst<R> I;
+  std::memset(&I, 0, sizeof I);
+  I.nx = nx; I.nr = nr; I.M = M; I.flags = flags;
+  I.h = (R)h; I.dr = (R)dr; I.inv_h = (R)(1.0 / h); I.inv_dr = (R)(1.0 / dr);
+  I.ma2 = (R)(m_a * m_a);
+  I.gs = (R)g; I.gj = (R)g;
+  I.jx = jx ? sjx.data() : nullptr;
+  I.jt = jt ? sjt.data() : nullptr;
+  Adj<R, M> a;
+  Tile<R, M, false, false> &t = a.f;
+  t.I = &I;
+  t.nx = nx; t.nr = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
+  t.per = false; t.closed = false; t.mw = false;
+  t.P = P; t.o = F.data(); t.n = nullptr;
+  t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
+  t.sm = nullptr; t.scr = nullptr;
+  t.cw = -(1 << 28);  // no cached columns: every access takes the general path
+  t.state_len = E; t.sm_len = 0;
+  a.ln = LN.data(); a.lo = LO.data(); a.sb = SB.data(); a.dg = dg;
+  a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
+  a.mw = (flags & F_MOVING_WINDOW) != 0;
+  a.h = I.h; a.dr = I.dr; a.ih = I.inv_h; a.idr = I.inv_dr;
+  a.gs = I.gs; a.ma2 = I.ma2;
+  for (int st = 0; st < N_ADSTAGE; st++)
+    for (int w = 0; w < nx; w++)
+      for (int j = 0; j < nr; j++) adj_point<R, M>(a, st, w, j);
+  for (size_t q = 0; q < E; q++) {
+    lam_old[2 * q] = (double)LO[q].re;
+    lam_old[2 * q + 1] = (double)LO[q].im;
+  }
+}
+
+}  // namespace
+
+extern "C" int qds_emu_adjoint(int M, const double *fwd, const double *lam_new, double *lam_old, int nx, int nr,
+                               double h, double dr, double m_a, double g, uint32_t flags, const double *jx,
+                               const double *jt, double *dg) {
+  const bool f32 = (flags & F_FP32) != 0;
+  switch (M) {
+#define QDS_EMU_ADJ(MM)                                                                              \
+  case MM:                                                                                           \
+    if (f32) emu_adjoint<float, MM>(fwd, lam_new, lam_old, nx, nr, h, dr, m_a, g, flags, jx, jt, dg); \
+    else emu_adjoint<double, MM>(fwd, lam_new, lam_old, nx, nr, h, dr, m_a, g, flags, jx, jt, dg);    \
+    return 0;
+    QDS_EMU_ADJ(1) QDS_EMU_ADJ(2) QDS_EMU_ADJ(3) QDS_EMU_ADJ(4)
+#undef QDS_EMU_ADJ
+  }
+  return 1;
+}
