@@ -146,6 +146,31 @@ void qds_free(qds_handle *h);
 const char *qds_last_error(void);
 
 /* ---------------------------------------------------------------------------
+ * Adjoint (transpose) of one step of the EM group and the axion (Sec. 2;
+ * the transpose of the +x transport shift is the -x shift).  For a real
+ * functional L of the state the adjoint of a complex value z is
+ * dL/dRe z + i dL/dIm z.  The regenerated group does not feed back into the
+ * EM fields or the axion, so for functionals of those it has a zero adjoint
+ * and its slots in the result are zero.
+ *
+ * fwd_state_dev: the forward state of instance i at the START of the step
+ *   (canonical complex128 layout of qds_set_state, physical variables: what
+ *   qds_get_state_i returned then).  Read only.
+ * adj_state_dev: on entry the adjoint of the state after the step, on exit
+ *   the adjoint of the state before it (same layout, complex128).
+ * src: the sources that step used (jx and jth enter the linearisation,
+ *   s_ext enters dL/dg; working precision, as for qds_step); may be NULL.
+ * work_dev: caller-owned scratch of >= qds_adjoint_work_bytes(h, i) bytes,
+ *   256-byte aligned.
+ * dLdg_dev: device double to which dL/dg of this step is ADDED (may be NULL).
+ * Open boundaries only (QDS_X_PERIODIC / QDS_R_CLOSED: QDS_ERR_UNSUPPORTED);
+ * needs QDS_AXION.  Runs in the handle's precision (QDS_FP32: complex64
+ * arithmetic, results widened to complex128).  Asynchronous on stream. */
+size_t qds_adjoint_work_bytes(const qds_handle *h, int i);
+int qds_adjoint_step(qds_handle *h, int i, const qds_sources *src, const void *fwd_state_dev,
+                     void *adj_state_dev, void *work_dev, size_t work_bytes, double *dLdg_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
  * No-allocation step (this entry point has no counterpart in the paper; it
  * serves callers that cannot allocate device memory: code inside runtimes
  * or memory pools that forbid allocation after start-up, plug-ins that must

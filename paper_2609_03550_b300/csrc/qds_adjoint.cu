@@ -1,0 +1,197 @@
+// qds_adjoint.cu -- qds_adjoint_step(): one transposed step of the EM group
+// and the axion on the GPU (the transpose in qds_adjoint.cuh, one kernel per
+// transposed pass, one thread per (x, r) point of the window).
+//
+// The caller passes the forward state at the start of the step and the
+// adjoint of the state after it, both in the canonical complex128 layout in
+// physical variables (what qds_get_state returns), and gets the adjoint of
+// the state before the step in place.  The transpose runs in the handle's
+// working precision; with QDS_FP32 the state and adjoint are converted to
+// complex64 (no 1/g scaling: the adjoint has no weak-coupling cancellation).
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+
+#include "../../include/qds.h"
+#include "qds_adjoint.cuh"
+
+using namespace qds;
+
+// defined in qds_api.cu
+void qds_internal_set_error(const std::string &m);
+int qds_internal_params(const qds_handle *h, int i, qds_params *out);
+
+namespace {
+
+int fail_ad(int code, const std::string &m) {
+  qds_internal_set_error(m);
+  return code;
+}
+
+constexpr int kThr = 256;
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+// work layout: [Inst<R>] [N_SB scratch planes] [lambda^(n+1) copy]
+//              FP32 only: [forward state] [lambda^n]
+template <class R>
+struct AdjLayout {
+  size_t off_scr, off_ln, off_f, off_lo, total;
+  AdjLayout(const qds_params &p) {
+    const size_t P = plane_elems(p.n_modes, p.nx, p.nr), E = state_elems(p.n_modes, p.nx, p.nr);
+    const size_t eb = sizeof(C<R>);
+    off_scr = up256(sizeof(Inst<R>));
+    off_ln = off_scr + up256((size_t)N_SB * P * eb);
+    off_f = off_ln + up256(E * eb);
+    if (sizeof(R) == 4) {
+      off_lo = off_f + up256(E * eb);
+      total = off_lo + up256(E * eb);
+    } else {
+      off_lo = off_f;
+      total = off_f;
+    }
+  }
+};
+
+template <class R, int M, int ST>
+__global__ void __launch_bounds__(kThr) adjoint_kernel(Adj<R, M> a) {
+  const int n = a.nx * a.nr;
+  double acc = 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const int w = q / a.nr, j = q - w * a.nr;
+    adj_point<R, M>(a, ST, w, j, acc);
+  }
+  if (ST == AD_UNSRC && a.dg) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(a.dg, acc);
+  }
+}
+
+template <class R>
+__global__ void to_work_kernel(const double2 *__restrict__ src, C<R> *dst, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    double2 v = src[q];
+    dst[q] = mk<R>((R)v.x, (R)v.y);
+  }
+}
+
+template <class R>
+__global__ void from_work_kernel(const C<R> *__restrict__ src, double2 *dst, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    C<R> v = src[q];
+    dst[q] = make_double2((double)v.re, (double)v.im);
+  }
+}
+
+template <class R, int M>
+cudaError_t launch_all(Adj<R, M> a, int blocks, cudaStream_t st) {
+  adjoint_kernel<R, M, AD_UNPHI><<<blocks, kThr, 0, st>>>(a);
+  adjoint_kernel<R, M, AD_UNTA><<<blocks, kThr, 0, st>>>(a);
+  adjoint_kernel<R, M, AD_UNSHIFT><<<blocks, kThr, 0, st>>>(a);
+  adjoint_kernel<R, M, AD_UNSRC><<<blocks, kThr, 0, st>>>(a);
+  adjoint_kernel<R, M, AD_UNLEAP><<<blocks, kThr, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class R, int M>
+Adj<R, M> make_adj(const qds_params &p, const Inst<R> *d_inst, const C<R> *F, const C<R> *LN, C<R> *LO,
+                   C<R> *SB, double *dg) {
+  Adj<R, M> a;
+  std::memset(&a, 0, sizeof a);
+  const int nx = p.nx, nr = p.nr;
+  const size_t P = plane_elems(M, nx, nr);
+  Tile<R, M, false, false> &t = a.f;
+  t.I = d_inst;
+  t.nx = nx; t.nr = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
+  t.per = false; t.closed = false; t.mw = false;
+  t.P = P; t.o = F; t.n = nullptr;
+  t.h = (R)p.dx; t.dr = (R)p.dr; t.ih = (R)(1.0 / p.dx); t.idr = (R)(1.0 / p.dr);
+  t.sm = nullptr; t.scr = nullptr;
+  t.cw = -(1 << 28);  // no cached columns: every access takes the general path
+  a.ln = LN; a.lo = LO; a.sb = SB; a.dg = dg;
+  a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
+  a.mw = (p.flags & QDS_MOVING_WINDOW) != 0;
+  a.h = t.h; a.dr = t.dr; a.ih = t.ih; a.idr = t.idr;
+  a.gs = (R)p.g; a.ma2 = (R)(p.m_a * p.m_a);
+  return a;
+}
+
+template <class R>
+int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *adj, void *work, size_t work_bytes,
+            double *dg, cudaStream_t st) {
+  AdjLayout<R> L(p);
+  if (work_bytes < L.total) return fail_ad(QDS_ERR_INVALID_ARG, "adjoint work buffer too small");
+  if (reinterpret_cast<uintptr_t>(work) % 256) return fail_ad(QDS_ERR_INVALID_ARG, "adjoint work buffer must be 256-byte aligned");
+  const int M = p.n_modes, nx = p.nx, nr = p.nr;
+  const size_t E = state_elems(M, nx, nr);
+  char *b = static_cast<char *>(work);
+  Inst<R> I;
+  std::memset(&I, 0, sizeof I);
+  I.nx = nx; I.nr = nr; I.M = M; I.flags = p.flags;
+  I.h = (R)p.dx; I.dr = (R)p.dr; I.inv_h = (R)(1.0 / p.dx); I.inv_dr = (R)(1.0 / p.dr);
+  I.ma2 = (R)(p.m_a * p.m_a);
+  I.gs = (R)p.g; I.gj = (R)p.g;
+  if (src) {
+    I.jx = (const C<R> *)src->jx;
+    I.jt = (const C<R> *)src->jth;
+    I.sext = (const C<R> *)src->s_ext;
+  }
+  cudaError_t e = cudaMemcpyAsync(b, &I, sizeof I, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint descriptor: ") + cudaGetErrorString(e));
+  C<R> *SB = reinterpret_cast<C<R> *>(b + L.off_scr);
+  C<R> *LN = reinterpret_cast<C<R> *>(b + L.off_ln);
+  const C<R> *F;
+  C<R> *LO;
+  const int cblocks = 1184;
+  if (sizeof(R) == 4) {
+    C<R> *Fw = reinterpret_cast<C<R> *>(b + L.off_f);
+    to_work_kernel<R><<<cblocks, kThr, 0, st>>>((const double2 *)fwd, Fw, E);
+    to_work_kernel<R><<<cblocks, kThr, 0, st>>>((const double2 *)adj, LN, E);
+    F = Fw;
+    LO = reinterpret_cast<C<R> *>(b + L.off_lo);
+  } else {
+    e = cudaMemcpyAsync(LN, adj, E * sizeof(C<R>), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint copy: ") + cudaGetErrorString(e));
+    F = static_cast<const C<R> *>(fwd);
+    LO = static_cast<C<R> *>(adj);
+  }
+  const Inst<R> *d_inst = reinterpret_cast<const Inst<R> *>(b);
+  const int blocks = (int)((size_t(nx) * nr + kThr - 1) / kThr);
+  switch (M) {
+    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
+  if (sizeof(R) == 4) {
+    from_work_kernel<R><<<cblocks, kThr, 0, st>>>(LO, (double2 *)adj, E);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+      return fail_ad(QDS_ERR_CUDA, std::string("adjoint export: ") + cudaGetErrorString(e));
+  }
+  return QDS_OK;
+}
+
+}  // namespace
+
+extern "C" size_t qds_adjoint_work_bytes(const qds_handle *h, int i) {
+  qds_params p;
+  if (qds_internal_params(h, i, &p)) return 0;
+  return (p.flags & QDS_FP32) ? AdjLayout<float>(p).total : AdjLayout<double>(p).total;
+}
+
+extern "C" int qds_adjoint_step(qds_handle *h, int i, const qds_sources *src, const void *fwd_state_dev,
+                                void *adj_state_dev, void *work_dev, size_t work_bytes, double *dLdg_dev,
+                                void *stream) {
+  qds_params p;
+  int rc = qds_internal_params(h, i, &p);
+  if (rc) return rc;
+  if (!fwd_state_dev || !adj_state_dev || !work_dev) return fail_ad(QDS_ERR_INVALID_ARG, "NULL state, adjoint or work pointer");
+  if (p.flags & (QDS_X_PERIODIC | QDS_R_CLOSED))
+    return fail_ad(QDS_ERR_UNSUPPORTED, "the adjoint covers open boundaries only");
+  if (!(p.flags & QDS_AXION)) return fail_ad(QDS_ERR_UNSUPPORTED, "the adjoint step needs QDS_AXION");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.flags & QDS_FP32) return adjoint<float>(p, src, fwd_state_dev, adj_state_dev, work_dev, work_bytes, dLdg_dev, st);
+  return adjoint<double>(p, src, fwd_state_dev, adj_state_dev, work_dev, work_bytes, dLdg_dev, st);
+}

@@ -49,7 +49,7 @@ struct Adj {
   const C<R> *ln;              // adjoint of the state after the step
   C<R> *lo;                    // adjoint of the state before the step (accumulated)
   C<R> *sb;                    // scratch planes
-  double *dg;                  // accumulated dL/dg (may be null)
+  double *dg;                  // accumulated dL/dg (null: not wanted)
   int nx, nr, J;
   size_t P;
   bool mw;
@@ -122,7 +122,7 @@ QDS_HD void conv_T(const C<R> *A, const C<R> *B, const C<R> *Sb, R wgt, C<R> *Ab
 
 // ---------------------------------------------------------------------------
 template <class R, int M>
-QDS_HD void adj_point(const Adj<R, M> &a, int st, int w, int j) {
+QDS_HD void adj_point(const Adj<R, M> &a, int st, int w, int j, double &dg_acc) {
   const int J = a.J;
   const R h = a.h, dr = a.dr, idr = a.idr;
   const R ka = R(0.5) * a.ih, kb = R(0.5) * idr;  // box-scheme weights
@@ -324,11 +324,7 @@ QDS_HD void adj_point(const Adj<R, M> &a, int st, int w, int j) {
         S += t.srcv(t.I->sext, m, f, j);
         acc += (double)Gb[m].re * S.re + (double)Gb[m].im * S.im;
       }
-#if defined(__CUDA_ARCH__)
-      atomicAdd(a.dg, acc);
-#else
-      *a.dg += acc;
-#endif
+      dg_acc += acc;  // the caller reduces and adds to *a.dg
     }
     C<R> eXb[M], bXb[M], rpb[M], rmb[M], qpb[M], qmb[M];
     for (int k = 0; k < M; k++) eXb[k] = bXb[k] = rpb[k] = rmb[k] = qpb[k] = qmb[k] = zero<R>();

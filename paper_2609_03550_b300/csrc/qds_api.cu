@@ -393,6 +393,15 @@ void destroy(qds_handle *h) {
 }  // namespace
 
 // ============================================================================
+// Parameters of instance i, for the adjoint translation unit.
+__attribute__((visibility("hidden"))) int qds_internal_params(const qds_handle *h, int i, qds_params *out) {
+  if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
+  if (i < 0 || i >= h->n_inst) return fail(QDS_ERR_INVALID_ARG, "instance index out of range");
+  *out = h->params[i];
+  out->modes = nullptr;
+  return QDS_OK;
+}
+
 extern "C" {
 
 const char *qds_last_error(void) { return g_err.c_str(); }

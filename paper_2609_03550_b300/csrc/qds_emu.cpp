@@ -223,9 +223,11 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   a.mw = (flags & F_MOVING_WINDOW) != 0;
   a.h = I.h; a.dr = I.dr; a.ih = I.inv_h; a.idr = I.inv_dr;
   a.gs = I.gs; a.ma2 = I.ma2;
+  double acc = 0;
   for (int st = 0; st < N_ADSTAGE; st++)
     for (int w = 0; w < nx; w++)
-      for (int j = 0; j < nr; j++) adj_point<R, M>(a, st, w, j);
+      for (int j = 0; j < nr; j++) adj_point<R, M>(a, st, w, j, acc);
+  if (dg) *dg += acc;
   for (size_t q = 0; q < E; q++) {
     lam_old[2 * q] = (double)LO[q].re;
     lam_old[2 * q + 1] = (double)LO[q].im;

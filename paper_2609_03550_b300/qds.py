@@ -71,6 +71,8 @@ def lib():
             "qds_free": (None, [H]),
             "qds_last_error": (ctypes.c_char_p, []),
             "qds_advance_noalloc": (i, [P, vp, vp, vp, sz, i, vp]),
+            "qds_adjoint_work_bytes": (sz, [H, i]),
+            "qds_adjoint_step": (i, [H, i, ctypes.POINTER(_Sources), vp, vp, vp, sz, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -174,6 +176,37 @@ class QDSSolver:
         src = _Sources(ptr(jx), ptr(jr), ptr(jth), ptr(s_ext))
         self._src_keep = (jx, jr, jth, s_ext)
         _check(lib().qds_step(self.h, ctypes.byref(src), int(nsteps), _stream_ptr(stream)))
+
+    def adjoint_step(self, fwd, lam, i: int = 0, jx=None, jth=None, s_ext=None, dLdg=None, stream=None):
+        """One transposed step (qds_adjoint_step): ``fwd`` is the canonical
+        complex128 state at the start of the step, ``lam`` (complex128, same
+        layout) holds the adjoint of the state after the step and is
+        overwritten with the adjoint of the state before it; dL/dg of the
+        step is added to ``dLdg`` (a float64 device tensor of one element)."""
+        p = self.params[i]
+        for t in (fwd, lam):
+            assert t.dtype == torch.complex128 and t.is_cuda and t.is_contiguous() and t.numel() == p.state_elems()
+
+        def ptr(t):
+            if t is None:
+                return None
+            assert t.is_cuda and t.dtype == self.rdtype and t.is_contiguous()
+            return t.data_ptr()
+        if dLdg is not None:
+            assert dLdg.dtype == torch.float64 and dLdg.is_cuda
+        nbytes = lib().qds_adjoint_work_bytes(self.h, i)
+        if nbytes == 0:
+            _check(1)
+        work = getattr(self, "_adj_work", None)
+        if work is None or work.numel() < nbytes + 256:
+            work = self._adj_work = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        wptr = work.data_ptr() + (-work.data_ptr()) % 256
+        src = _Sources(ptr(jx), None, ptr(jth), ptr(s_ext))
+        self._adj_keep = (fwd, lam, jx, jth, s_ext, dLdg)
+        _check(lib().qds_adjoint_step(self.h, i, ctypes.byref(src), ctypes.c_void_p(fwd.data_ptr()),
+                                      ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(wptr), nbytes,
+                                      None if dLdg is None else ctypes.c_void_p(dLdg.data_ptr()),
+                                      _stream_ptr(stream)))
 
     def diagnostics(self, i: int = 0, profile=False, stream=None):
         out = (ctypes.c_double * 4)()

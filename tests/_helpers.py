@@ -77,3 +77,31 @@ def fp32_tolerance(tol64, field_tol=1e-5, axion_tol=1e-4):
     return {"em": max(field_tol, (tol64["em"] / 10.0) * 10.0 * scale if tol64["em"] > 1e-12 else field_tol),
             "axion": max(axion_tol, tol64["axion"] * scale if tol64["axion"] > 1e-12 else axion_tol),
             "arem": max(axion_tol, tol64["arem"] * scale if tol64["arem"] > 1e-12 else axion_tol)}
+
+
+def oracle_vjp(s, lam, M, nx, nr, dr, flags, g=0.0, m_a=0.0, src=(None, None, None, None), extended=False):
+    """J^T lam of one oracle step at state s, column by column: the step is at
+    most quadratic in the state, so (F(s + e) - F(s - e)) / 2 is exactly the
+    Jacobian column for a basis direction e.  Adjoint convention: the entry
+    for a complex value z is dL/dRe z + i dL/dIm z with L = <lam, F> (real
+    inner product).  Only the EM and axion components (and phi_prev) are
+    probed; the regenerated components of the result are left at zero."""
+    n = M * nx * nr
+    idx = list(range(9 * n)) + list(range(15 * n, 15 * n + M * nx))
+    out = np.zeros_like(s)
+    lr, li = lam.real, lam.imag
+
+    def F(buf):
+        return oracle_run(buf, M, nx, nr, dr, flags, 1, g=g, m_a=m_a, src=src, extended=extended)
+
+    for q in idx:
+        for unit in (1.0, 1j):
+            e = np.zeros_like(s)
+            e[q] = unit
+            col = 0.5 * (F(s + e) - F(s - e))
+            v = float(np.sum(lr * col.real + li * col.imag))
+            if unit == 1.0:
+                out[q] += v
+            else:
+                out[q] += 1j * v
+    return out

@@ -100,3 +100,24 @@ def test_adjoint_coupling_derivative(M):
     fd = rdot(lam * mask, (Fp - Fm) * mask) / (2 * dgs)
     _, dg = emu_adjoint(M, s, lam, nx, nr, dr, 0.0, g, flags)
     assert abs(dg - fd) < 1e-10 * (abs(fd) + 1e-300) + 1e-12, (dg, fd)
+
+
+@pytest.mark.parametrize("M,mw", [(1, False), (2, True), (3, False)])
+def test_adjoint_step_elementwise_vs_oracle_columns(M, mw):
+    """Every entry of J^T lambda against the oracle's Jacobian columns
+    (tiny grid; includes the on-axis entries the regularity rules fix)."""
+    from tests._helpers import oracle_vjp
+    nx, nr = 9, 5
+    m_a, g = 0.1, 0.8
+    dr = stable_dr(M, m_a)
+    flags = oracle.AXION | (oracle.MOVING_WINDOW if mw else 0)
+    rng = np.random.default_rng(40 + M)
+    s = I.random_state(rng, M, nx, nr)
+    jx, jr, jt = I.random_sources(rng, M, nx, nr, 0.3)
+    lam = I.random_state(rng, M, nx, nr, axis_consistent=False) * em_axion_mask(M, nx, nr)
+    ref = oracle_vjp(s, lam, M, nx, nr, dr, flags, g=g, m_a=m_a, src=(jx, jr, jt, None))
+    got, _ = emu_adjoint(M, s, lam, nx, nr, dr, m_a, g, flags, jx, jt)
+    err = np.abs(got - ref)
+    tol = 1e-12 * np.abs(ref).max()
+    bad = np.argwhere(err > tol)
+    assert bad.size == 0, (bad[:10].ravel(), got[bad[:5].ravel()], ref[bad[:5].ravel()])

@@ -1,0 +1,255 @@
+"""GPU transpose of the step (qds_adjoint_step) and the checkpointed gradient
+(run_qds) against the oracle.
+
+Per step: every entry of J^T lambda against the oracle's Jacobian columns on
+a tiny grid, and <lambda, J d> = <J^T lambda, d> with J d from the oracle on
+grids that span several thread blocks with a ragged tail.  Through N steps:
+the gradient of an axion-energy loss with respect to a laser-2 radial
+profile, omega2 and g against central differences of the same loss
+evaluated by the oracle, and dL/dg = 2 L / g for an axion grown from zero.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_03550_b300 import inputs as I
+from tests._helpers import oracle_run, oracle_vjp, stable_dr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+def _Q():
+    from paper_2609_03550_b300 import build as B
+    B.build_cuda()
+    from paper_2609_03550_b300 import qds as Q
+    return Q
+
+
+def em_axion_mask(M, nx, nr):
+    n = M * nx * nr
+    m = np.zeros(15 * n + M * nx, bool)
+    m[:9 * n] = True
+    m[15 * n:] = True
+    return m
+
+
+def rdot(a, b):
+    return float(np.sum(a.real * b.real + a.imag * b.imag))
+
+
+def gpu_vjp(Q, p, s, lam, src=(None, None, None), dg=False):
+    solver = Q.QDSSolver(p, device=DEV)
+    rd = solver.rdtype
+    jx, jr, jt = (None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(rd) for a in src)
+    fwd = torch.from_numpy(s).to(DEV)
+    lt = torch.from_numpy(lam.copy()).to(DEV)
+    acc = torch.zeros(1, dtype=torch.float64, device=DEV) if dg else None
+    solver.adjoint_step(fwd, lt, jx=jx, jth=jt, dLdg=acc)
+    torch.cuda.synchronize()
+    out = lt.cpu().numpy()
+    return (out, float(acc.item())) if dg else out
+
+
+@pytest.mark.parametrize("M,mw,prec", [(1, False, 0), (2, True, 0), (3, False, 0), (4, True, 0), (2, True, 32)])
+def test_adjoint_step_elementwise_vs_oracle_columns(M, mw, prec):
+    Q = _Q()
+    nx, nr = 9, 5
+    m_a, g = 0.1, 0.8
+    dr = stable_dr(M, m_a)
+    flags = oracle.AXION | (oracle.MOVING_WINDOW if mw else 0)
+    rng = np.random.default_rng(60 + M)
+    s = I.random_state(rng, M, nx, nr)
+    jx, jr, jt = I.random_sources(rng, M, nx, nr, 0.3)
+    if prec:  # the sources in the working precision, identical on both sides
+        jx, jt = (a.astype(np.complex64).astype(np.complex128) for a in (jx, jt))
+    lam = I.random_state(rng, M, nx, nr, axis_consistent=False) * em_axion_mask(M, nx, nr)
+    ref = oracle_vjp(s, lam, M, nx, nr, dr, flags, g=g, m_a=m_a, src=(jx, jr, jt, None))
+    p = Q.Params(nx, nr, M, dr, m_a=m_a, g=g, flags=flags | prec)
+    got = gpu_vjp(Q, p, s, lam, (jx, jr, jt))
+    tol = (1e-12 if prec == 0 else 2e-6) * np.abs(ref).max()
+    bad = np.argwhere(np.abs(got - ref) > tol).ravel()
+    assert bad.size == 0, (bad[:10], got[bad[:5]], ref[bad[:5]])
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+@pytest.mark.parametrize("mw", [False, True])
+@pytest.mark.parametrize("prec", [0, 32])
+def test_adjoint_step_dot_product(M, mw, prec):
+    """nx * nr = 4960 points: 19 full blocks of 256 threads and a ragged one."""
+    Q = _Q()
+    nx, nr = 124, 40
+    m_a, g = 0.05, 0.6
+    dr = stable_dr(M, m_a)
+    flags = oracle.AXION | oracle.AREM | (oracle.MOVING_WINDOW if mw else 0)
+    rng = np.random.default_rng(200 + 10 * M + mw)
+    s = I.random_state(rng, M, nx, nr)
+    jx, jr, jt = I.random_sources(rng, M, nx, nr, 0.3)
+    if prec:
+        jx, jt = (a.astype(np.complex64).astype(np.complex128) for a in (jx, jt))
+    mask = em_axion_mask(M, nx, nr)
+    p = Q.Params(nx, nr, M, dr, m_a=m_a, g=g, flags=flags | prec)
+    for trial in range(2):
+        d = I.random_state(rng, M, nx, nr) * mask
+        lam = I.random_state(rng, M, nx, nr, axis_consistent=False) * mask
+        F = lambda b: oracle_run(b, M, nx, nr, dr, flags, 1, g=g, m_a=m_a, src=(jx, jr, jt, None), extended=False)
+        Jd = 0.5 * (F(s + d) - F(s - d))
+        lt = gpu_vjp(Q, p, s, lam, (jx, jr, jt))
+        lhs, rhs = rdot(lam, Jd * mask), rdot(lt, d)
+        scale = np.linalg.norm(lam) * np.linalg.norm(Jd)
+        tol = 1e-12 if prec == 0 else 1e-6
+        assert abs(lhs - rhs) < tol * scale, (trial, lhs, rhs)
+        assert np.all(lt[~mask] == 0)
+
+
+@pytest.mark.parametrize("prec", [0, 32])
+def test_adjoint_step_coupling_derivative(prec):
+    Q = _Q()
+    M, nx, nr = 3, 70, 24
+    dr = stable_dr(M)
+    flags = oracle.AXION | oracle.MOVING_WINDOW
+    rng = np.random.default_rng(31)
+    s = I.random_state(rng, M, nx, nr)
+    lam = I.random_state(rng, M, nx, nr, axis_consistent=False) * em_axion_mask(M, nx, nr)
+    g, dgs = 0.4, 0.1
+    Fp = oracle_run(s, M, nx, nr, dr, flags, 1, g=g + dgs, extended=False)
+    Fm = oracle_run(s, M, nx, nr, dr, flags, 1, g=g - dgs, extended=False)
+    fd = rdot(lam * em_axion_mask(M, nx, nr), Fp - Fm) / (2 * dgs)
+    p = Q.Params(nx, nr, M, dr, g=g, flags=flags | prec)
+    _, dg = gpu_vjp(Q, p, s, lam, dg=True)
+    tol = 1e-11 if prec == 0 else 1e-5
+    assert abs(dg - fd) < tol * abs(fd), (dg, fd)
+
+
+def test_adjoint_rejects_unsupported_boundaries():
+    Q = _Q()
+    p = Q.Params(16, 8, 2, 2.0, g=0.5, flags=oracle.AXION | oracle.X_PERIODIC)
+    s = np.zeros(p.state_elems(), np.complex128)
+    with pytest.raises(Q.QDSError, match="open boundaries"):
+        gpu_vjp(Q, p, s, s.copy())
+
+
+# ---------------------------------------------------------------------------
+# gradients through N steps
+
+
+class Case:
+    """A small two-colour run with a drive: laser 1 fixed, laser 2 given by
+    a complex radial profile and omega2; an m = 0 bunch current and uniform
+    noise on every current redrawn each step; loss = axion energy in the
+    front window cells."""
+
+    def __init__(self, prec, nx=96, nr=16, M=3, nsteps=30, every=7, seed=5):
+        self.M, self.nx, self.nr, self.nsteps, self.every = M, nx, nr, nsteps, every
+        self.dr = stable_dr(M) * 1.6
+        self.flags = oracle.AXION | oracle.AREM | oracle.MOVING_WINDOW
+        self.prec = prec
+        self.g = 0.3
+        self.x0, self.fwhm = 0.6 * nx, 24.0
+        wl = I.Workload("adjoint_case", nx, nr, M, self.dr, nsteps,
+                        [I.Laser(0.5, 16.0, 4 * self.dr, 24.0, self.x0, "y")])
+        self.base = wl.initial_state()
+        rng = np.random.default_rng(seed)
+        r = (np.arange(nr) + 0.5) * self.dr
+        self.profile0 = 0.5 * (2 * np.pi / 20.0) * np.exp(-(r / (4 * self.dr)) ** 2) * (1 + 0.2j * rng.standard_normal(nr))
+        self.omega2 = 2 * np.pi / 20.0
+        self.src = []
+        xf = (np.arange(nx) + 0.5)[:, None]
+        ri = (np.arange(nr) * self.dr)[None, :]
+        for n in range(nsteps):
+            jx = np.zeros((M, nx, nr), np.complex128)
+            jx[0] = -0.05 * np.exp(-((xf - 0.3 * nx) ** 2) / (2 * 8.0 ** 2)) * np.exp(-(ri ** 2) / (2 * (2 * self.dr) ** 2))
+            parts = []
+            for a in (jx, np.zeros_like(jx), np.zeros_like(jx)):
+                noise = 5e-4 * (rng.uniform(-1, 1, a.shape) + 1j * rng.uniform(-1, 1, a.shape))
+                noise[0] = noise[0].real
+                b = a + noise
+                if prec:
+                    b = b.astype(np.complex64).astype(np.complex128)
+                parts.append(np.ascontiguousarray(b))
+            self.src.append(tuple(parts))
+        self.Q = _Q()
+        self.p = self.Q.Params(nx, nr, M, self.dr, g=self.g, flags=self.flags | prec)
+        self._dev_src = None
+
+    def sources(self, n):
+        if self._dev_src is None:
+            rd = torch.complex64 if self.prec else torch.complex128
+            self._dev_src = [tuple(torch.from_numpy(a).to(DEV).to(rd) for a in t) for t in self.src]
+        return self._dev_src[n]
+
+    def state0(self, profile, omega2, device):
+        from paper_2609_03550_b300.adjoint import laser2_state
+        base = torch.from_numpy(self.base).to(device)
+        return laser2_state(base, self.p, profile, omega2, self.x0, self.fwhm)
+
+    def loss(self, state):
+        from paper_2609_03550_b300.adjoint import axion_energy
+        return axion_energy(state, self.p, self.nx - 32, self.nx)
+
+    def oracle_loss(self, profile, omega2, g):
+        s0 = self.state0(torch.as_tensor(profile, dtype=torch.complex128), torch.tensor(float(omega2), dtype=torch.float64),
+                         "cpu").numpy().copy()
+        st = oracle.State(self.M, self.nx, self.nr, s0)
+        pd = dict(nx=self.nx, nr=self.nr, M=self.M, h=1.0, dr=self.dr, g=g, m_a=0.0, flags=self.flags)
+        for n in range(self.nsteps):
+            jx, jr, jt = self.src[n]
+            oracle.step(pd, st, jx, jr, jt)
+        return float(self.loss(torch.from_numpy(st.buf)))
+
+    def gpu_grad(self):
+        from paper_2609_03550_b300.adjoint import RunSpec, run_qds
+        prof = torch.tensor(self.profile0, dtype=torch.complex128, device=DEV, requires_grad=True)
+        om = torch.tensor(self.omega2, dtype=torch.float64, device=DEV, requires_grad=True)
+        g = torch.tensor(self.g, dtype=torch.float64, device=DEV, requires_grad=True)
+        spec = RunSpec(self.p, self.nsteps, every=self.every, sources=self.sources, device=DEV)
+        L = self.loss(run_qds(self.state0(prof, om, DEV), g, spec))
+        L.backward()
+        return float(L), prof.grad.cpu().numpy(), float(om.grad), float(g.grad)
+
+
+def _richardson(f, x0, h):
+    """Central difference with one Richardson step (error O(h^4))."""
+    d1 = (f(x0 + h) - f(x0 - h)) / (2 * h)
+    d2 = (f(x0 + h / 2) - f(x0 - h / 2)) / h
+    return (4 * d2 - d1) / 3
+
+
+@pytest.mark.parametrize("prec", [0, 32])
+def test_run_gradient_vs_oracle_central_differences(prec):
+    c = Case(prec)
+    L, gprof, gom, gg = c.gpu_grad()
+    L0 = c.oracle_loss(c.profile0, c.omega2, c.g)
+    print(f"loss gpu {L!r} oracle {L0!r}")
+    assert abs(L - L0) < (1e-12 if prec == 0 else 1e-4) * abs(L0), (L, L0)
+    tol = 1e-8 if prec == 0 else 1e-4
+    rng = np.random.default_rng(9)
+    # profile: along a random complex direction, step 1e-4 of the profile
+    dirn = rng.standard_normal(c.nr) + 1j * rng.standard_normal(c.nr)
+    dirn *= np.linalg.norm(c.profile0) / np.linalg.norm(dirn)
+    fd = _richardson(lambda t: c.oracle_loss(c.profile0 + t * dirn, c.omega2, c.g), 0.0, 1e-4)
+    ad = rdot(gprof, dirn)
+    print(f"profile adjoint {ad!r} fd {fd!r}")
+    assert abs(ad - fd) < tol * abs(fd), ("profile", ad, fd)
+    fd = _richardson(lambda w: c.oracle_loss(c.profile0, w, c.g), c.omega2, 1e-4 * c.omega2)
+    print(f"omega2 adjoint {gom!r} fd {fd!r}")
+    assert abs(gom - fd) < tol * abs(fd), ("omega2", gom, fd)
+    fd = _richardson(lambda gg_: c.oracle_loss(c.profile0, c.omega2, gg_), c.g, 1e-4 * c.g)
+    print(f"g adjoint {gg!r} fd {fd!r} 2L/g {2 * L / c.g!r}")
+    assert abs(gg - fd) < tol * abs(fd), ("g", gg, fd)
+    # the axion grows from zero and is linear in g, so L is quadratic in g
+    assert abs(gg - 2 * L / c.g) < (1e-10 if prec == 0 else 1e-5) * abs(gg), (gg, 2 * L / c.g)
+
+
+def test_run_rejects_regenerated_cotangent():
+    from paper_2609_03550_b300.adjoint import RunSpec, run_qds
+    Q = _Q()
+    p = Q.Params(32, 8, 2, 2.0, g=0.5, flags=oracle.AXION | oracle.AREM)
+    s0 = torch.zeros(p.state_elems(), dtype=torch.complex128, device=DEV, requires_grad=True)
+    g = torch.tensor(0.5, dtype=torch.float64, device=DEV)
+    out = run_qds(s0, g, RunSpec(p, 3, device=DEV))
+    n = 2 * 32 * 8
+    with pytest.raises(Q.QDSError, match="regenerated"):
+        out[9 * n:10 * n].real.sum().backward()
