@@ -130,11 +130,27 @@ int qds_num_instances(const qds_handle *h);
  * n_inst*4 doubles) in two launches; asynchronous on stream. */
 int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
 
-/* Step implementation: 0 (default) runs one grid-wide pass per stage of the
- * step (leapfrog, axion source, shift, phi, axion current, regenerated
- * leapfrog, regenerated shift), intermediates in the new state and in
- * scratch planes of the caller's buffer; 1 runs every stage of a tile in one
- * kernel with the intermediates and their halos in shared memory. */
+/* Step implementation (all give the same results to rounding):
+ *   QDS_STEP_DEFAULT    the fastest measured of the pass modes below;
+ *   QDS_STEP_FUSED      every stage of a tile in one kernel, intermediates
+ *                       and their halos in shared memory;
+ *   QDS_STEP_STAGES     one grid-wide pass per stage group: leapfrog, axion
+ *                       source, shift + phi, axion current + regenerated
+ *                       leapfrog, regenerated shift (intermediates in the new
+ *                       state and in scratch planes of the caller's buffer);
+ *   QDS_STEP_WARP       warp-column passes: leapfrog + source in one pass,
+ *                       shift + phi + current + regenerated leapfrog in
+ *                       another (radial neighbours through shared memory,
+ *                       the shift of the next cell recomputed), then the
+ *                       regenerated shift;
+ *   QDS_STEP_WARP_LEAP  the first warp-column pass, then the stage passes.
+ * qds_set_fused(h, 1) selects QDS_STEP_FUSED and (h, 0) QDS_STEP_DEFAULT. */
+#define QDS_STEP_DEFAULT 0
+#define QDS_STEP_FUSED 1
+#define QDS_STEP_STAGES 2
+#define QDS_STEP_WARP 3
+#define QDS_STEP_WARP_LEAP 4
+int qds_set_step_mode(qds_handle *h, int mode);
 int qds_set_fused(qds_handle *h, int fused);
 
 /* Tile shape of the fused step kernel (x cells, radial rows); used by the

@@ -94,14 +94,14 @@ cudaError_t launch_all(Adj<R, M> a, int blocks, cudaStream_t st) {
 }
 
 template <class R, int M>
-Adj<R, M> make_adj(const qds_params &p, const Inst<R> *d_inst, const C<R> *F, const C<R> *LN, C<R> *LO,
-                   C<R> *SB, double *dg) {
+Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_inst, const C<R> *F,
+                   const C<R> *LN, C<R> *LO, C<R> *SB, double *dg) {
   Adj<R, M> a;
   std::memset(&a, 0, sizeof a);
   const int nx = p.nx, nr = p.nr;
   const size_t P = plane_elems(M, nx, nr);
   Tile<R, M, false, false> &t = a.f;
-  t.I = d_inst;
+  t.bind(h_inst, d_inst);
   t.nx = nx; t.nr = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
   t.per = false; t.closed = false; t.mw = false;
   t.P = P; t.o = F; t.n = nullptr;
@@ -158,10 +158,10 @@ int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *
   const Inst<R> *d_inst = reinterpret_cast<const Inst<R> *>(b);
   const int blocks = (int)((size_t(nx) * nr + kThr - 1) / kThr);
   switch (M) {
-    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
-    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
-    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
-    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
     default: e = cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));

@@ -303,11 +303,11 @@ QDS_HD void adj_point(const Adj<R, M> &a, int st, int w, int j, double &dg_acc) 
     C<R> eX[M], bX[M], rp[M], rm[M], qp[M], qm[M];
     C<R> exn[M], exn1[M], bxn[M];
     for (int k = 0; k < M; k++) {
-      exn[k] = ex_update(t, 0, k, f, j, t.srcv(t.I->jx, k, f, j));
+      exn[k] = ex_update(t, 0, k, f, j, t.srcv(t.jx, k, f, j));
       bxn[k] = (j < J) ? bx_interior(t, 0, k, f, j)
-                       : bx_outer(t, 0, k, f, R(0.5) * (t.srcv(t.I->jt, k, f, j) + t.srcv(t.I->jt, k, f + 1, j)),
+                       : bx_outer(t, 0, k, f, R(0.5) * (t.srcv(t.jt, k, f, j) + t.srcv(t.jt, k, f + 1, j)),
                                   bx_interior(t, 0, k, f, j - 1));
-      exn1[k] = top ? exn[k] : ex_update(t, 0, k, f, j + 1, t.srcv(t.I->jx, k, f, j + 1));
+      exn1[k] = top ? exn[k] : ex_update(t, 0, k, f, j + 1, t.srcv(t.jx, k, f, j + 1));
       C<R> eo = t.face(EX, k, f, j), eo1 = top ? eo : t.face(EX, k, f, j + 1);
       eX[k] = R(0.25) * (eo + eo1 + exn[k] + exn1[k]);
       bX[k] = R(0.5) * (t.face(BX, k, f, j) + bxn[k]);
@@ -321,7 +321,7 @@ QDS_HD void adj_point(const Adj<R, M> &a, int st, int w, int j, double &dg_acc) 
       double acc = 0;
       for (int m = 0; m < M; m++) {
         C<R> S = conv<R, M>(m, eX, bX) + R(0.5) * (conv<R, M>(m, rp, qp) - conv<R, M>(m, rm, qm));
-        S += t.srcv(t.I->sext, m, f, j);
+        S += t.srcv(t.sext, m, f, j);
         acc += (double)Gb[m].re * S.re + (double)Gb[m].im * S.im;
       }
       dg_acc += acc;  // the caller reduces and adds to *a.dg

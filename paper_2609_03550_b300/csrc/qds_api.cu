@@ -34,6 +34,8 @@ int fail(int code, const std::string &msg) {
   } while (0)
 
 constexpr int kThreads = 256;
+// the step implementation behind QDS_STEP_DEFAULT
+constexpr int kDefaultMode = QDS_STEP_STAGES;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -121,10 +123,13 @@ struct qds_handle {
     int4 *d_tiles = nullptr;  // pass mode: interior tiles first, then edge tiles
     int ntiles = 0;
     int n_interior = 0;       // pass mode: tiles whose halo lies inside the window
+    // warp-column passes P1 (31 output rows per warp) and P2 (30), interior first
+    int4 *d_w[2] = {nullptr, nullptr};
+    int nw[2] = {0, 0}, nw_interior[2] = {0, 0};
   };
   std::vector<Group> groups;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
-  bool fused = false;  // fused shared-memory step (one launch) instead of one pass per stage
+  int mode = QDS_STEP_DEFAULT;  // step implementation (qds_set_step_mode)
   // pass-mode tiles (one thread per point)
   std::vector<Group> pgroups;
   // graph cache: key (jx, jr, jt, sext, nsteps, stream)
@@ -213,16 +218,57 @@ cudaError_t launch_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t 
   return cudaGetLastError();
 }
 
+template <class R, int M, int PASS>
+cudaError_t launch_warp_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  const int q = PASS - 1;
+  const size_t smem = warp_pass_smem<R, M>(PASS);
+  if (G.nw_interior[q] > 0)
+    warp_pass_kernel<R, M, PASS, true><<<G.nw_interior[q], kThreads, smem, st>>>((const Inst<R> *)h->d_inst, G.d_w[q],
+                                                                              h->d_ctrl, G.g);
+  if (G.nw[q] > G.nw_interior[q])
+    warp_pass_kernel<R, M, PASS, false><<<G.nw[q] - G.nw_interior[q], kThreads, smem, st>>>(
+        (const Inst<R> *)h->d_inst, G.d_w[q] + G.nw_interior[q], h->d_ctrl, G.g);
+  return cudaGetLastError();
+}
+
 template <class R, int M>
-cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl, cudaStream_t st) {
+cudaError_t allow_warp_smem_t() {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(warp_pass_kernel<R, M, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(1))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(warp_pass_kernel<R, M, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(1))) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(warp_pass_kernel<R, M, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(2))) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(warp_pass_kernel<R, M, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(2));
+}
+
+cudaError_t allow_warp_smem(bool fp32, int M) {
+  switch (M) {
+    case 1: return fp32 ? allow_warp_smem_t<float, 1>() : allow_warp_smem_t<double, 1>();
+    case 2: return fp32 ? allow_warp_smem_t<float, 2>() : allow_warp_smem_t<double, 2>();
+    case 3: return fp32 ? allow_warp_smem_t<float, 3>() : allow_warp_smem_t<double, 3>();
+    case 4: return fp32 ? allow_warp_smem_t<float, 4>() : allow_warp_smem_t<double, 4>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+// One step of one mode-count group in pass mode: the two warp-column passes,
+// the regenerated shift and (moving window) the zeroing of the rear column.
+template <class R, int M>
+cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl, int mode, cudaStream_t st) {
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
   cudaError_t e;
-  if ((e = launch_pass<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
-  if (ax && (e = launch_pass<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
-  if ((e = launch_pass<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
-  if (ax && (e = launch_pass<R, M, ST_PHI>(h, G, st)) != cudaSuccess) return e;
-  if (ar && (e = launch_pass<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
-  if (ar && (e = launch_pass<R, M, ST_LEAP1>(h, G, st)) != cudaSuccess) return e;
+  if (mode == QDS_STEP_STAGES) {
+    if ((e = launch_pass<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
+    if (ax && (e = launch_pass<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
+  } else if ((e = launch_warp_pass<R, M, 1>(h, G, st)) != cudaSuccess) {
+    return e;
+  }
+  if (mode == QDS_STEP_WARP) {
+    if ((e = launch_warp_pass<R, M, 2>(h, G, st)) != cudaSuccess) return e;
+  } else {
+    // phi is formed in ST_SHIFT0 and the regenerated leapfrog in ST_CURRENT
+    if ((e = launch_pass<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_pass<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
+  }
   if (ar && (e = launch_pass<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
   if (mw && (e = launch_pass<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -230,17 +276,18 @@ cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl
 
 template <class R>
 cudaError_t launch_step(qds_handle *h, cudaStream_t st) {
-  if (!h->fused) {
+  const int mode = h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode;
+  if (mode != QDS_STEP_FUSED) {
     for (const auto &G : h->pgroups) {
       uint32_t fl = 0;
       for (int i = 0; i < h->n_inst; i++)
         if (h->params[i].n_modes == G.M) fl |= h->params[i].flags;
       cudaError_t e = cudaSuccess;
       switch (G.M) {
-        case 1: e = launch_passes<R, 1>(h, G, fl, st); break;
-        case 2: e = launch_passes<R, 2>(h, G, fl, st); break;
-        case 3: e = launch_passes<R, 3>(h, G, fl, st); break;
-        case 4: e = launch_passes<R, 4>(h, G, fl, st); break;
+        case 1: e = launch_passes<R, 1>(h, G, fl, mode, st); break;
+        case 2: e = launch_passes<R, 2>(h, G, fl, mode, st); break;
+        case 3: e = launch_passes<R, 3>(h, G, fl, mode, st); break;
+        case 4: e = launch_passes<R, 4>(h, G, fl, mode, st); break;
         default: e = cudaErrorInvalidValue;
       }
       if (e != cudaSuccess) return e;
@@ -370,6 +417,27 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
       P.ntiles = (int)pt.size();
       CU(cudaMalloc(&P.d_tiles, sizeof(int4) * pt.size()));
       CU(cudaMemcpy(P.d_tiles, pt.data(), sizeof(int4) * pt.size(), cudaMemcpyHostToDevice));
+      // warp-column passes: (instance, x0, row of lane 0, first output row)
+      for (int q = 0; q < 2; q++) {
+        const int stride = q == 0 ? 31 : 30;
+        std::vector<int4> wi, we;
+        for (int i = 0; i < n; i++) {
+          if (params[i].n_modes != M) continue;
+          const bool per = (params[i].flags & QDS_X_PERIODIC) != 0;
+          for (int x0 = 0; x0 < params[i].nx; x0 += P.g.TX)
+            for (int r0 = 0; r0 < params[i].nr; r0 += stride) {
+              const bool inner = per ? (params[i].nx >= P.g.TX + 4) : (x0 >= 2 && x0 + P.g.TX + 2 <= params[i].nx - 1);
+              const int base = q == 0 ? r0 : (r0 > 0 ? r0 - 1 : 0);
+              (inner ? wi : we).push_back(make_int4(i, x0, base, r0));
+            }
+        }
+        P.nw_interior[q] = (int)wi.size();
+        wi.insert(wi.end(), we.begin(), we.end());
+        P.nw[q] = (int)wi.size();
+        CU(cudaMalloc(&P.d_w[q], sizeof(int4) * wi.size()));
+        CU(cudaMemcpy(P.d_w[q], wi.data(), sizeof(int4) * wi.size(), cudaMemcpyHostToDevice));
+      }
+      CU(allow_warp_smem(fp32, M));
       h->pgroups.push_back(P);
     }
   }
@@ -380,7 +448,7 @@ void destroy(qds_handle *h) {
   if (!h) return;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &G : h->groups) cudaFree(G.d_tiles);
-  for (auto &G : h->pgroups) cudaFree(G.d_tiles);
+  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); }
   cudaFree(h->d_inst);
   cudaFree(h->d_ctrl);
   cudaFree(h->d_partial);
@@ -451,7 +519,7 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   for (auto &G : h->groups) cudaFree(G.d_tiles);
   cudaFree(h->d_inst); cudaFree(h->d_ctrl); cudaFree(h->d_partial); cudaFree(h->d_diag);
   cudaFree(h->d_partial_all); cudaFree(h->d_scal);
-  for (auto &G : h->pgroups) cudaFree(G.d_tiles);
+  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); }
   h->groups = nh->groups; h->pgroups = nh->pgroups; h->d_inst = nh->d_inst; h->d_ctrl = nh->d_ctrl;
   h->d_partial_all = nh->d_partial_all; h->d_scal = nh->d_scal;
   h->d_partial = nh->d_partial; h->d_diag = nh->d_diag; h->h_inst = nh->h_inst;
@@ -461,9 +529,12 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   return QDS_OK;
 }
 
-int qds_set_fused(qds_handle *h, int fused) {
+int qds_set_fused(qds_handle *h, int fused) { return qds_set_step_mode(h, fused ? QDS_STEP_FUSED : QDS_STEP_DEFAULT); }
+
+int qds_set_step_mode(qds_handle *h, int mode) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
-  h->fused = fused != 0;
+  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_WARP_LEAP) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
+  h->mode = mode;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   return QDS_OK;

@@ -54,6 +54,24 @@ template <class R> QDS_HD C<R> mul_cj(C<R> a, C<R> b) {
   return mk<R>(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
 }
 
+// FP32 on sm_100 and later: sums, differences and real scalings of complex
+// values as one packed two-lane instruction (same rounding per component).
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+#define QDS_PACKED_F32 1
+#endif
+#if defined(QDS_PACKED_F32)
+__device__ __forceinline__ float2 f2(C<float> a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ C<float> cf(float2 a) { return mk<float>(a.x, a.y); }
+__device__ __forceinline__ C<float> operator+(C<float> a, C<float> b) { return cf(__fadd2_rn(f2(a), f2(b))); }
+__device__ __forceinline__ C<float> operator-(C<float> a, C<float> b) {
+  return cf(__ffma2_rn(make_float2(-1.f, -1.f), f2(b), f2(a)));
+}
+__device__ __forceinline__ C<float> operator*(float s, C<float> a) { return cf(__fmul2_rn(make_float2(s, s), f2(a))); }
+__device__ __forceinline__ C<float> operator*(C<float> a, float s) { return cf(__fmul2_rn(make_float2(s, s), f2(a))); }
+__device__ __forceinline__ C<float> &operator+=(C<float> &a, C<float> b) { a = a + b; return a; }
+__device__ __forceinline__ C<float> &operator-=(C<float> &a, C<float> b) { a = a - b; return a; }
+#endif
+
 // Per-instance descriptor (device resident).
 template <class R>
 struct Inst {

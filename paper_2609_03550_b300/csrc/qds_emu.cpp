@@ -61,8 +61,71 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
   std::vector<C<R>> scratch(4 * P);
   for (int q = 0; q < (int)scratch.size(); q++) scratch[q] = mk<R>((R)1e30, (R)1e30);
   I.scratch = scratch.data();
-  for (int n = 0; n < nsteps && !fused; n++) {
-    // pass mode: every stage over every tile before the next stage
+  auto pass_tile_at = [&](int n, int x0, int r0) {
+    Tile<R, M, false, false> t;
+    t.bind(I, &I);
+    t.nx = nx; t.nr = nr; t.J = nr - 1;
+    t.x0 = x0; t.r0 = r0;
+    t.per = (flags & F_X_PERIODIC) != 0;
+    t.closed = (flags & F_R_CLOSED) != 0;
+    t.mw = (flags & F_MOVING_WINDOW) != 0;
+    t.s = t.mw ? n % nx : 0;
+    t.P = P;
+    t.o = buf[n & 1].data();
+    t.n = buf[(n & 1) ^ 1].data();
+    t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
+    t.g = Geo{};
+    t.g.TX = 8; t.g.TR = 32;
+    t.L = Smem{};
+    t.sm = nullptr;
+    t.scr = scratch.data();
+    t.state_len = E;
+    t.sm_len = 0;
+    return t;
+  };
+  // pass mode (fused == 0): the warp-column passes P1, P2, then the
+  // regenerated shift and the window zeroing as stage passes; warps and
+  // lanes run in order, phase 1 of all 32 lanes before phase 2
+  for (int n = 0; n < nsteps && fused == 0; n++) {
+    const bool ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
+    const bool per_ = (flags & F_X_PERIODIC) != 0;
+    for (int pass = 1; pass <= 2; pass++) {
+      const int stride = pass == 1 ? 31 : 30;
+      for (int x0 = 0; x0 < nx; x0 += 8)
+        for (int r0 = 0; r0 < nr; r0 += stride) {
+          const bool inner = per_ ? (nx >= 8 + 4) : (x0 >= 2 && x0 + 8 + 2 <= nx - 1);
+          const int base = pass == 1 ? r0 : (r0 > 0 ? r0 - 1 : 0);
+          Tile<R, M, false, false> t = pass_tile_at(n, x0, base);
+          Tile<R, M, false, true> tf;
+          std::memcpy((void *)&tf, (const void *)&t, sizeof t);
+          for (int lx = 0; lx < 8 && x0 + lx < nx; lx++) {
+            std::vector<P1Lane<R, M>> L1(32);
+            std::vector<P2Lane<R, M>> L2(32);
+            for (int ph = 0; ph < 2; ph++)
+              for (int lane = 0; lane < 32; lane++) {
+                const int j = base + lane;
+                const bool out = pass == 1 ? (lane < 31 && j < nr) : (j >= r0 && j < r0 + 30 && j < nr);
+                if (pass == 1 && ph == 0) { if (inner) p1_leap(tf, lx, lane, out, L1[lane]); else p1_leap(t, lx, lane, out, L1[lane]); }
+                if (pass == 1 && ph == 1) { if (inner) p1_source(tf, lx, lane, out, L1.data()); else p1_source(t, lx, lane, out, L1.data()); }
+                if (pass == 2 && ph == 0) { if (inner) p2_shift(tf, lx, lane, out, L2[lane]); else p2_shift(t, lx, lane, out, L2[lane]); }
+                if (pass == 2 && ph == 1) { if (inner) p2_current(tf, lx, lane, out, L2.data()); else p2_current(t, lx, lane, out, L2.data()); }
+              }
+          }
+        }
+    }
+    for (int st : {(int)ST_SHIFT1, (int)ST_ZERO}) {
+      if (st == ST_SHIFT1 && !ar) continue;
+      if (st == ST_ZERO && !mw) continue;
+      for (int x0 = 0; x0 < nx; x0 += TX)
+        for (int r0 = 0; r0 < nr; r0 += TR) {
+          Tile<R, M, false, false> t = pass_tile_at(n, x0, r0);
+          t.g.TX = TX; t.g.TR = TR;
+          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false, false>(t, st, tid, nthreads);
+        }
+    }
+  }
+  for (int n = 0; n < nsteps && fused == 2; n++) {
+    // stage passes: every stage over every tile before the next stage
     const int par = n & 1;
     const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
     const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, ST_ZERO};
@@ -75,7 +138,7 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
           const bool per_ = (flags & F_X_PERIODIC) != 0;
           const bool inner = per_ ? (nx >= TX + 4) : (x0 >= 2 && x0 + TX + 2 <= nx - 1);
           Tile<R, M, false, false> t;
-          t.I = &I;
+          t.bind(I, &I);
           t.nx = nx; t.nr = nr; t.J = nr - 1;
           t.x0 = x0; t.r0 = r0;
           t.per = (flags & F_X_PERIODIC) != 0;
@@ -102,12 +165,12 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
         }
     }
   }
-  for (int n = 0; n < nsteps && fused; n++) {
+  for (int n = 0; n < nsteps && fused == 1; n++) {
     const int par = n & 1;
     for (int x0 = 0; x0 < nx; x0 += TX)
       for (int r0 = 0; r0 < nr; r0 += TR) {
         Tile<R, M, true> t;
-        t.I = &I;
+        t.bind(I, &I);
         t.nx = nx; t.nr = nr; t.J = nr - 1;
         t.x0 = x0; t.r0 = r0;
         t.per = (flags & F_X_PERIODIC) != 0;
@@ -210,7 +273,7 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   I.jt = jt ? sjt.data() : nullptr;
   Adj<R, M> a;
   Tile<R, M, false, false> &t = a.f;
-  t.I = &I;
+  t.bind(I, &I);
   t.nx = nx; t.nr = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
   t.per = false; t.closed = false; t.mw = false;
   t.P = P; t.o = F.data(); t.n = nullptr;

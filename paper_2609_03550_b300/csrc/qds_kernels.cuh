@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ i
   const Inst<R> &I = insts[td.x];
   const unsigned long long n = ctrl->step;
   Tile<R, M, true> t;
-  t.I = &I;
+  t.bind(I, &I);
   t.nx = I.nx;
   t.nr = I.nr;
   t.J = I.nr - 1;
@@ -61,15 +61,12 @@ __global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ i
 // FAST: the tile list holds only tiles whose halo lies inside the window
 // (checks skipped).  The heavy stages (axion source and current) keep their
 // registers; the light ones are held to three CTAs per SM.
-template <class R, int M, int ST, bool FAST>
-__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 2 : 3)
-    pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
-                const Ctrl *__restrict__ ctrl, Geo g) {
-  const int4 td = tiles[blockIdx.x];
-  const Inst<R> &I = insts[td.x];
-  const unsigned long long n = ctrl->step;
+// Pass-mode view of one tile (origin x0 = td.y, row r0 = td.z) of
+// instance td.x at step n.
+template <class R, int M, bool FAST>
+__device__ __forceinline__ Tile<R, M, false, FAST> pass_tile(const Inst<R> &I, int4 td, unsigned long long n, Geo g) {
   Tile<R, M, false, FAST> t;
-  t.I = &I;
+  t.bind(I, &I);
   t.nx = I.nx;
   t.nr = I.nr;
   t.J = I.nr - 1;
@@ -90,7 +87,49 @@ __global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 2
   t.g = g;
   t.sm = nullptr;
   t.scr = I.scratch;
+  return t;
+}
+
+template <class R, int M, int ST, bool FAST>
+__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 2 : 4)
+    pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
+                const Ctrl *__restrict__ ctrl, Geo g) {
+  const int4 td = tiles[blockIdx.x];
+  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(insts[td.x], td, ctrl->step, g);
   run_stage<R, M, false, FAST>(t, ST, threadIdx.x, blockDim.x);
+}
+
+// Warp-column passes (P1: leapfrog + Gamma_a; P2: shift + phi + j_a +
+// regenerated leapfrog).  Block = 8 warps = 8 columns x0..x0+7; lane l of a
+// warp holds row td.z + l; P2 outputs rows [td.w, td.w + 30).
+template <class R, int M>
+constexpr size_t warp_pass_smem(int pass) {
+  return 256 * (pass == 1 ? sizeof(P1Lane<R, M>) : sizeof(P2Lane<R, M>));
+}
+
+template <class R, int M, int PASS, bool FAST>
+__global__ void __launch_bounds__(256, 2)
+    warp_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
+                     const Ctrl *__restrict__ ctrl, Geo g) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  const int4 td = tiles[blockIdx.x];
+  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(insts[td.x], td, ctrl->step, g);
+  const int lx = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (t.x0 + lx >= t.nx) return;  // the whole warp: its column lies beyond the window
+  const int j = t.r0 + lane;
+  if (PASS == 1) {
+    P1Lane<R, M> *L = reinterpret_cast<P1Lane<R, M> *>(wsm) + lx * 32;
+    const bool out = lane < 31 && j < t.nr;
+    p1_leap(t, lx, lane, out, L[lane]);
+    __syncwarp();
+    p1_source(t, lx, lane, out, L);
+  } else {
+    P2Lane<R, M> *L = reinterpret_cast<P2Lane<R, M> *>(wsm) + lx * 32;
+    const bool out = j >= td.w && j < td.w + 30 && j < t.nr;
+    p2_shift(t, lx, lane, out, L[lane]);
+    __syncwarp();
+    p2_current(t, lx, lane, out, L);
+  }
 }
 
 static __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {

@@ -77,9 +77,7 @@ cudaError_t run_steps(const Inst<R> *d_inst, const int4 *d_tiles, int ntiles, Ct
     pass_kernel<R, M, ST_LEAP0, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
     if (ax) pass_kernel<R, M, ST_SOURCE, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
     pass_kernel<R, M, ST_SHIFT0, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (ax) pass_kernel<R, M, ST_PHI, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
     if (ar) pass_kernel<R, M, ST_CURRENT, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
-    if (ar) pass_kernel<R, M, ST_LEAP1, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
     if (ar) pass_kernel<R, M, ST_SHIFT1, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
     if (mw) pass_kernel<R, M, ST_ZERO, false><<<ntiles, kThr, 0, st>>>(d_inst, d_tiles, d_ctrl, g);
     advance_kernel<<<1, 32, 0, st>>>(d_ctrl, 1);

@@ -58,6 +58,17 @@ QDS_HD C<R> ldg(const C<R> *p) {
 template <class R, int M, bool SM = true, bool FAST = false>
 struct Tile {
   const Inst<R> *I;
+  // values of the descriptor used per point, held in registers (loads
+  // through I could not be hoisted past the stores of a pass)
+  const C<R> *jx, *jr, *jt, *sext;
+  R gs, gj, ma2;
+  uint32_t flags;
+  QDS_HD void bind(const Inst<R> &d, const Inst<R> *dev) {
+    I = dev;
+    jx = d.jx; jr = d.jr; jt = d.jt; sext = d.sext;
+    gs = d.gs; gj = d.gj; ma2 = d.ma2;
+    flags = d.flags;
+  }
   int nx, nr, J;       // J = nr - 1: last integer row / last half row
   int x0, r0;          // tile origin in window coordinates
   int s;               // ring offset of the window
@@ -317,6 +328,46 @@ QDS_NOINL C<R> bx_outer(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, C<
   return num * (R(1) / (a + b));
 }
 
+// Both longitudinal updates of one mode at face w, with each transverse
+// value loaded once: E_x from B_theta on half rows j-1, j and B_r on row j;
+// B_x from E_theta on rows j, j+1 and E_r on half row j (the same
+// expressions as ex_update and bx_interior; the outer row takes bx_outer).
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL void leap_point(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, int j, C<R> jx, C<R> jt_face,
+                          C<R> &ex, C<R> &bx) {
+  // cell sums over w, w+1 of the reconstructed fields (Eq. reconstruct_fields)
+  const C<R> rp = t.cell(grp + TRP, k, w, j) + t.cell(grp + TRP, k, w + 1, j);
+  const C<R> rm = t.cell(grp + TRM, k, w, j) + t.cell(grp + TRM, k, w + 1, j);
+  const C<R> qp = t.cell(grp + TTP, k, w, j) + t.cell(grp + TTP, k, w + 1, j);
+  const C<R> qm = t.cell(grp + TTM, k, w, j) + t.cell(grp + TTM, k, w + 1, j);
+  const C<R> er = R(0.25) * (rp + rm), bth = R(0.25) * (rp - rm);
+  const C<R> eth = R(0.25) * (qp + qm), brr = R(0.25) * (qp - qm);
+  const C<R> e0 = t.face(grp + EX, k, w, j);
+  if (j == 0) {
+    ex = (k != 0) ? zero<R>() : e0 + t.h * (R(4) * t.idr * bth - jx);
+  } else {
+    const C<R> rpl = t.cell(grp + TRP, k, w, j - 1) + t.cell(grp + TRP, k, w + 1, j - 1);
+    const C<R> rml = t.cell(grp + TRM, k, w, j - 1) + t.cell(grp + TRM, k, w + 1, j - 1);
+    const C<R> blo = R(0.25) * (rpl - rml);
+    const R rj = R(j) * t.dr;
+    const C<R> curl = ((R(j) + R(0.5)) * bth - (R(j) - R(0.5)) * blo) * (R(1) / rj);
+    ex = e0 + t.h * (curl + imul(R(k) / rj, brr) - jx);
+  }
+  if (j == t.J && !t.closed) {
+    bx = bx_outer(t, grp, k, w, jt_face, bx_interior(t, grp, k, w, j - 1));
+    return;
+  }
+  C<R> ehi = zero<R>();
+  if (j + 1 < t.nr) {
+    const C<R> qp1 = t.cell(grp + TTP, k, w, j + 1) + t.cell(grp + TTP, k, w + 1, j + 1);
+    const C<R> qm1 = t.cell(grp + TTM, k, w, j + 1) + t.cell(grp + TTM, k, w + 1, j + 1);
+    ehi = R(0.25) * (qp1 + qm1);
+  }
+  const R rh = (R(j) + R(0.5)) * t.dr;
+  const C<R> curl = (R(j + 1) * ehi - R(j) * eth) * (R(1) / rh);
+  bx = t.face(grp + BX, k, w, j) - t.h * (curl + imul(R(k) / rh, er));
+}
+
 // ---------------------------------------------------------------------------
 // Face quantities consumed by the characteristic shift: group 0 reads them
 // from the tile's shared memory and x-averages the caller's cell currents;
@@ -329,18 +380,18 @@ struct Faces0 {
   QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sA(1, k, lx, lr); }
   QDS_HD C<R> jr(int k, int lx, int lr) const {
     int w = t.x0 + lx, j = t.r0 + lr;
-    if (!t.I->jr || !t.face_ok(w)) return zero<R>();
-    return R(0.5) * (t.srcv(t.I->jr, k, w, j) + t.srcv(t.I->jr, k, w + 1, j));
+    if (!t.jr || !t.face_ok(w)) return zero<R>();
+    return R(0.5) * (t.srcv(t.jr, k, w, j) + t.srcv(t.jr, k, w + 1, j));
   }
   QDS_HD C<R> jt(int k, int lx, int lr) const {
     int w = t.x0 + lx, j = t.r0 + lr;
-    if (!t.I->jt || !t.face_ok(w)) return zero<R>();
-    return R(0.5) * (t.srcv(t.I->jt, k, w, j) + t.srcv(t.I->jt, k, w + 1, j));
+    if (!t.jt || !t.face_ok(w)) return zero<R>();
+    return R(0.5) * (t.srcv(t.jt, k, w, j) + t.srcv(t.jt, k, w + 1, j));
   }
   QDS_HD C<R> jx(int k, int lx, int lr) const {
     int w = t.x0 + lx, j = t.r0 + lr;
     if (!t.face_ok(w)) return zero<R>();
-    return t.srcv(t.I->jx, k, w, j);
+    return t.srcv(t.jx, k, w, j);
   }
 };
 
@@ -439,8 +490,18 @@ QDS_NOINL void tt_update(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, i
 // exterior phi comes from the outgoing condition (d_t + c d_r) phi = 0
 // centred at r_J (Eq. axion_r_ghost) with d_t phi taken half a step back.
 // ---------------------------------------------------------------------------
+// Provider of E_x^(n+1/2), B_x^(n+1/2) at face x0+lx (rows lr, lr+1): the
+// tile's intermediate planes (fused step, pass mode).
 template <class R, int M, bool SM, bool FAST>
-QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
+struct TileLeapVals {
+  const Tile<R, M, SM, FAST> &t;
+  int lx, lr;
+  QDS_HD C<R> exn(int k, int dj) const { return t.sA(0, k, lx, lr + dj); }
+  QDS_HD C<R> bxn(int k) const { return t.sA(1, k, lx, lr); }
+};
+
+template <class R, int M, bool SM, bool FAST, class NV>
+QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, const NV &nv) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) t.sG(k, lx, lr) = zero<R>();
@@ -456,12 +517,12 @@ QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
   C<R> eX[M], bX[M], rp[M], rm[M], qp[M], qm[M];
 #pragma unroll
   for (int k = 0; k < M; k++) {
-    C<R> eo = t.face(EX, k, w, j), en = t.sA(0, k, lx, lr), eo1, en1;
-    if (!top) { eo1 = t.face(EX, k, w, j + 1); en1 = t.sA(0, k, lx, lr + 1); }
+    C<R> eo = t.face(EX, k, w, j), en = nv.exn(k, 0), eo1, en1;
+    if (!top) { eo1 = t.face(EX, k, w, j + 1); en1 = nv.exn(k, 1); }
     else if (t.closed) { eo1 = zero<R>(); en1 = zero<R>(); }
     else { eo1 = eo; en1 = en; }
     eX[k] = R(0.25) * (eo + eo1 + en + en1);
-    bX[k] = R(0.5) * (t.face(BX, k, w, j) + t.sA(1, k, lx, lr));
+    bX[k] = R(0.5) * (t.face(BX, k, w, j) + nv.bxn(k));
     rp[k] = R(0.5) * (t.cell(TRP, k, w, j) + t.cell(TRP, k, w + 1, j));
     rm[k] = R(0.5) * (t.cell(TRM, k, w, j) + t.cell(TRM, k, w + 1, j));
     C<R> p0 = t.cell(TTP, k, w, j) + t.cell(TTP, k, w + 1, j);
@@ -478,7 +539,7 @@ QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
 #pragma unroll
   for (int m = 0; m < M; m++) {
     C<R> S = conv<R, M>(m, eX, bX) + R(0.5) * (conv<R, M>(m, rp, qp) - conv<R, M>(m, rm, qm));
-    S += t.srcv(t.I->sext, m, w, j);
+    S += t.srcv(t.sext, m, w, j);
     C<R> pc = t.face(PHI, m, w, j);
     C<R> pm = (j > 0) ? t.face(PHI, m, w, j - 1) : zero<R>();  // weight j = 0 on the axis
     C<R> pp;
@@ -486,9 +547,14 @@ QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
     else if (t.closed) pp = pc;
     else pp = t.face(PHI, m, w, j - 1) - (R(2) * t.dr * t.ih) * (pc - t.prev(m, w));
     C<R> lap = (R(j + 1) * (pp - pc) - R(j) * (pc - pm)) * (idr2 / (R(j) + R(0.5)));
-    C<R> ga = lap - (R(m * m) / (rh * rh) + t.I->ma2) * pc + t.I->gs * S;
+    C<R> ga = lap - (R(m * m) / (rh * rh) + t.ma2) * pc + t.gs * S;
     t.sG(m, lx, lr) = ga;
   }
+}
+
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
+  source_point(t, lx, lr, TileLeapVals<R, M, SM, FAST>{t, lx, lr});
 }
 
 // ---------------------------------------------------------------------------
@@ -500,16 +566,36 @@ QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
 // Below the axis a scalar on half rows mirrors with parity (-1)^l; E_r and
 // B_theta below the axis follow the T_r ghost of Eq. axis_Tr.
 // ---------------------------------------------------------------------------
+// Provider of the values of the new level that j_a needs around face
+// x0+lx: ns(pl, k, jj) = sum over cells x0+lx, x0+lx+1 of plane pl (0..3:
+// T_r^+, T_r^-, T_th^+, T_th^- at n+1; 4, 5: T_a^+, T_a^- at n+1/2) on row
+// jj, and pn(k, jj) = phi^(n+1) at the face on row jj.
 template <class R, int M, bool SM, bool FAST>
-QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
+struct TileNewVals {
+  const Tile<R, M, SM, FAST> &t;
+  int lx;
+  QDS_HD C<R> ns(int pl, int k, int jj) const {
+    const int l = jj - t.r0;
+    return t.sT(pl, k, lx, l) + t.sT(pl, k, lx + 1, l);
+  }
+  QDS_HD C<R> pn(int k, int jj) const { return t.sP(k, lx, jj - t.r0); }
+};
+
+template <class R, int M, bool SM, bool FAST, class NV>
+QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R> (&jax)[M], C<R> (&jat)[M],
+                             const NV &nv) {
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
-    for (int k = 0; k < M; k++) for (int q = 2; q < 5; q++) t.sJ(q, k, lx, lr) = zero<R>();
+    for (int k = 0; k < M; k++) {
+      for (int q = 2; q < 5; q++)
+        if (SM || q > 2 || j == t.J) t.sJ(q, k, lx, lr) = zero<R>();
+      jax[k] = jat[k] = zero<R>();
+    }
     return;
   }
   const bool top = (j == t.J);
   const int j1 = top ? -1 : j + 1;  // row above, -1: beyond the last row
-  const R gj = t.I->gj;
+  const R gj = t.gj;
   const R ih = t.ih;
   // ---- j_a,x at (w, j, n) ----
   {
@@ -521,11 +607,11 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
       C<R> bx_lo = (j > 0) ? R(0.5) * (t.face(BX, k, w, j - 1) + t.sA(1, k, lx, lr - 1)) : par * bx_hi;
       a1[k] = R(0.5) * (bx_lo + bx_hi);
       C<R> dt_hi = R(0.125) * (t.cell(TAP, k, w, j) + t.cell(TAM, k, w, j) + t.cell(TAP, k, w + 1, j) + t.cell(TAM, k, w + 1, j) +
-                               t.sT(4, k, lx, lr) + t.sT(5, k, lx, lr) + t.sT(4, k, lx + 1, lr) + t.sT(5, k, lx + 1, lr));
+                               nv.ns(4, k, j) + nv.ns(5, k, j));
       C<R> dt_lo;
       if (j > 0)
         dt_lo = R(0.125) * (t.cell(TAP, k, w, j - 1) + t.cell(TAM, k, w, j - 1) + t.cell(TAP, k, w + 1, j - 1) + t.cell(TAM, k, w + 1, j - 1) +
-                            t.sT(4, k, lx, lr - 1) + t.sT(5, k, lx, lr - 1) + t.sT(4, k, lx + 1, lr - 1) + t.sT(5, k, lx + 1, lr - 1));
+                            nv.ns(4, k, j - 1) + nv.ns(5, k, j - 1));
       else dt_lo = par * dt_hi;
       b1[k] = R(0.5) * (dt_lo + dt_hi);
       C<R> er_hi = R(0.5) * (t.Er(0, k, w, j) + t.Er(0, k, w + 1, j)), er_lo;
@@ -541,29 +627,29 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
       b3[k] = t.idr * (ph - pl);
     }
 #pragma unroll
-    for (int m = 0; m < M; m++)
-      t.sJ(2, m, lx, lr) = gj * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2) + conv<R, M>(m, a3, b3));
+    for (int m = 0; m < M; m++) {
+      jax[m] = gj * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2) + conv<R, M>(m, a3, b3));
+      // pass mode: consumed by the caller, and on the outer row by the
+      // box scheme of the regenerated shift
+      if (SM || j == t.J) t.sJ(2, m, lx, lr) = jax[m];
+    }
   }
-  // time-(n+1/2) transverse fields: mean of level n (global) and n+1 (shared)
-  auto ER5 = [&](int k, int dl, int jj) -> C<R> {  // dl: 0 cell w, 1 cell w+1
-    C<R> o = t.Er(0, k, w + dl, jj);
-    C<R> nw = R(0.5) * (t.sT(0, k, lx + dl, jj - t.r0) + t.sT(1, k, lx + dl, jj - t.r0));
-    return R(0.5) * (o + nw);
+  // Transport variables at time n + 1/2 (mean of level n, global, and
+  // level n+1, the new state), summed over cells w and w+1.  With E, B at
+  // n + 1/2 from these means, E_th + B_r = T_th^+ and E_th - B_r = T_th^-,
+  // E_r + B_th = T_r^+ and E_r - B_th = T_r^-, so the sums below are the
+  // cell sums of those combinations.
+  auto QP = [&](int k, int jj) -> C<R> {  // T_th^+ on row jj
+    return R(0.5) * (t.cell(TTP, k, w, jj) + t.cell(TTP, k, w + 1, jj) + nv.ns(2, k, jj));
   };
-  auto BT5 = [&](int k, int dl, int jj) -> C<R> {
-    C<R> o = t.Bt(0, k, w + dl, jj);
-    C<R> nw = R(0.5) * (t.sT(0, k, lx + dl, jj - t.r0) - t.sT(1, k, lx + dl, jj - t.r0));
-    return R(0.5) * (o + nw);
+  auto QM = [&](int k, int jj) -> C<R> {  // T_th^- on row jj
+    return R(0.5) * (t.cell(TTM, k, w, jj) + t.cell(TTM, k, w + 1, jj) + nv.ns(3, k, jj));
   };
-  auto ET5 = [&](int k, int dl, int jj) -> C<R> {
-    C<R> o = t.Et(0, k, w + dl, jj);
-    C<R> nw = R(0.5) * (t.sT(2, k, lx + dl, jj - t.r0) + t.sT(3, k, lx + dl, jj - t.r0));
-    return R(0.5) * (o + nw);
+  auto RP = [&](int k, int jj) -> C<R> {  // T_r^+ on half row jj
+    return R(0.5) * (t.cell(TRP, k, w, jj) + t.cell(TRP, k, w + 1, jj) + nv.ns(0, k, jj));
   };
-  auto BR5 = [&](int k, int dl, int jj) -> C<R> {
-    C<R> o = t.Br(0, k, w + dl, jj);
-    C<R> nw = R(0.5) * (t.sT(2, k, lx + dl, jj - t.r0) - t.sT(3, k, lx + dl, jj - t.r0));
-    return R(0.5) * (o + nw);
+  auto RM = [&](int k, int jj) -> C<R> {  // T_r^- on half row jj
+    return R(0.5) * (t.cell(TRM, k, w, jj) + t.cell(TRM, k, w + 1, jj) + nv.ns(1, k, jj));
   };
 
   // Mean over cells w, w+1 of T_a^+- at n+1/2 on half row jj (the new
@@ -571,8 +657,7 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
   // (1/2)(Ta+ + Ta-) of this mean on every half row (Eq. phi_update), and
   // d_x phi = (1/2)(Ta- - Ta+).
   auto TAX = [&](int pl, int k, int jj) -> C<R> {  // pl 4: Ta+, 5: Ta-
-    int l = jj - t.r0;
-    return R(0.5) * (t.sT(pl, k, lx, l) + t.sT(pl, k, lx + 1, l));
+    return R(0.5) * nv.ns(pl, k, jj);
   };
   // ---- j_a,r at (w, j + 1/2, n + 1/2) ----
   //   C{B_r, d_t phi} - C{E_th, d_x phi} = (1/2)(C{Tth+, Ta+} - C{Tth-, Ta-})
@@ -581,19 +666,19 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
     C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
-      C<R> p = ET5(k, 0, j) + BR5(k, 0, j) + ET5(k, 1, j) + BR5(k, 1, j);   // Tth+ summed over cells w, w+1
-      C<R> m = ET5(k, 0, j) - BR5(k, 0, j) + ET5(k, 1, j) - BR5(k, 1, j);
+      C<R> p = QP(k, j);   // Tth+ summed over cells w, w+1
+      C<R> m = QM(k, j);
       C<R> p1, m1;
       if (j1 >= 0) {
-        p1 = ET5(k, 0, j1) + BR5(k, 0, j1) + ET5(k, 1, j1) + BR5(k, 1, j1);
-        m1 = ET5(k, 0, j1) - BR5(k, 0, j1) + ET5(k, 1, j1) - BR5(k, 1, j1);
+        p1 = QP(k, j1);
+        m1 = QM(k, j1);
       } else if (t.closed) { p1 = zero<R>(); m1 = zero<R>(); }
       else { p1 = p; m1 = m; }
       a1[k] = R(0.25) * (p + p1);
       a2[k] = R(0.25) * (m + m1);
       b1[k] = TAX(4, k, j);
       b2[k] = TAX(5, k, j);
-      C<R> po = t.face(PHI, k, w, j), pn = t.sP(k, lx, lr);
+      C<R> po = t.face(PHI, k, w, j), pn = nv.pn(k, j);
       C<R> ex_lo = t.sA(0, k, lx, lr), ex_hi;
       if (j1 >= 0) ex_hi = t.sA(0, k, lx, lr + 1);
       else ex_hi = t.closed ? zero<R>() : ex_lo;
@@ -616,13 +701,11 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
     for (int k = 0; k < M; k++) {
       const R par = (k & 1) ? R(-1) : R(1);
       if (j > 0) {
-        a1[k] = R(0.25) * (ER5(k, 0, j) + BT5(k, 0, j) + ER5(k, 1, j) + BT5(k, 1, j) +
-                           ER5(k, 0, j - 1) + BT5(k, 0, j - 1) + ER5(k, 1, j - 1) + BT5(k, 1, j - 1));
-        a2[k] = R(0.25) * (ER5(k, 0, j) - BT5(k, 0, j) + ER5(k, 1, j) - BT5(k, 1, j) +
-                           ER5(k, 0, j - 1) - BT5(k, 0, j - 1) + ER5(k, 1, j - 1) - BT5(k, 1, j - 1));
+        a1[k] = R(0.25) * (RP(k, j) + RP(k, j - 1));
+        a2[k] = R(0.25) * (RM(k, j) + RM(k, j - 1));
       } else if (k == 1) {
-        C<R> tm0 = R(0.5) * (ET5(k, 0, 0) - BR5(k, 0, 0) + ET5(k, 1, 0) - BR5(k, 1, 0));  // Tth- at the axis
-        C<R> tp0 = R(0.5) * (ET5(k, 0, 0) + BR5(k, 0, 0) + ET5(k, 1, 0) + BR5(k, 1, 0));  // Tth+
+        C<R> tm0 = R(0.5) * QM(k, 0);  // Tth- at the axis
+        C<R> tp0 = R(0.5) * QP(k, 0);  // Tth+
         a1[k] = imul(R(1), tm0);
         a2[k] = imul(R(1), tp0);
       } else {
@@ -635,13 +718,175 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
       b1[k] = R(0.5) * (am_lo + am_hi);   // Ta- paired with Tr+
       b2[k] = R(0.5) * (ap_lo + ap_hi);   // Ta+ paired with Tr-
       a3[k] = t.sA(0, k, lx, lr);
-      C<R> pbh = R(0.5) * (t.face(PHI, k, w, j) + t.sP(k, lx, lr));
-      C<R> pbl = (j > 0) ? R(0.5) * (t.face(PHI, k, w, j - 1) + t.sP(k, lx, lr - 1)) : par * pbh;
+      C<R> pbh = R(0.5) * (t.face(PHI, k, w, j) + nv.pn(k, j));
+      C<R> pbl = (j > 0) ? R(0.5) * (t.face(PHI, k, w, j - 1) + nv.pn(k, j - 1)) : par * pbh;
       b3[k] = t.idr * (pbh - pbl);
     }
 #pragma unroll
-    for (int m = 0; m < M; m++)
-      t.sJ(4, m, lx, lr) = gj * (R(0.5) * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2)) - conv<R, M>(m, a3, b3));
+    for (int m = 0; m < M; m++) {
+      jat[m] = gj * (R(0.5) * (conv<R, M>(m, a1, b1) - conv<R, M>(m, a2, b2)) - conv<R, M>(m, a3, b3));
+      t.sJ(4, m, lx, lr) = jat[m];
+    }
+  }
+}
+
+template <class R, int M, bool SM, bool FAST>
+QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R> (&jax)[M], C<R> (&jat)[M]) {
+  current_point(t, lx, lr, jax, jat, TileNewVals<R, M, SM, FAST>{t, lx});
+}
+
+// ---------------------------------------------------------------------------
+// Warp-column passes.  A warp owns one window column (face and cell w) and
+// 32 consecutive rows, one row per lane, all modes per lane.  Values that a
+// pass computes and needs again on the neighbouring rows go through the
+// warp's slice of shared memory between the two phases of the pass:
+//   P1  phase 1: E_x, B_x leapfrog (ST_LEAP0);      phase 2: Gamma_a (ST_SOURCE)
+//   P2  phase 1: shift of T, T_a of cells w, w+1, and phi at face w (ST_SHIFT0);
+//       phase 2: j_a and the regenerated leapfrog of face w (ST_CURRENT).
+// The warp recomputes the shift of cell w+1 instead of reading it back, so
+// the two stages of each pass share one read of the state.  P1 outputs
+// lanes 0..30 (lane 31 gives E_x^(n+1/2) on the row above); a P2 warp based
+// at row max(r0-1, 0) outputs rows [r0, r0+30).
+// ---------------------------------------------------------------------------
+template <class R, int M>
+struct P1Lane {
+  C<R> exn[M], bxn[M];
+};
+template <class R, int M>
+struct P2Lane {
+  C<R> ns[6][M];  // cell sums (w, w+1) of T_r^+-, T_th^+- (n+1), T_a^+- (n+1/2)
+  C<R> phn[M];    // phi^(n+1) at face w
+};
+
+template <class R, int M>
+struct P1Vals {
+  const P1Lane<R, M> *L;
+  int lane;
+  QDS_HD C<R> exn(int k, int dj) const { return L[lane + dj].exn[k]; }
+  QDS_HD C<R> bxn(int k) const { return L[lane].bxn[k]; }
+};
+template <class R, int M>
+struct P2Vals {
+  const P2Lane<R, M> *L;
+  int base;  // row of lane 0
+  QDS_HD C<R> ns(int pl, int k, int jj) const {
+#if defined(QDS_EMU)
+    QDS_CHECK(jj - base >= 0 && jj - base < 32, "P2 lane range");
+#endif
+    return L[jj - base].ns[pl][k];
+  }
+  QDS_HD C<R> pn(int k, int jj) const {
+#if defined(QDS_EMU)
+    QDS_CHECK(jj - base >= 0 && jj - base < 32, "P2 lane range");
+#endif
+    return L[jj - base].phn[k];
+  }
+};
+
+// P1 phase 1: E_x^(n+1/2), B_x^(n+1/2) of the lane's row (stored if out).
+template <class R, int M, bool FAST>
+QDS_HD void p1_leap(Tile<R, M, false, FAST> t, int lx, int lane, bool out, P1Lane<R, M> &my) {
+  const int w = t.x0 + lx, j = t.r0 + lane;
+  t.set_point(w);
+  const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+#pragma unroll 1
+  for (int k = 0; k < M; k++) {
+    C<R> ex = zero<R>(), bx = zero<R>();
+    if (live) {
+      C<R> jtf = zero<R>();
+      if (j == t.J && !t.closed) jtf = R(0.5) * (t.srcv(t.jt, k, w, j) + t.srcv(t.jt, k, w + 1, j));
+      leap_point(t, 0, k, w, j, t.srcv(t.jx, k, w, j), jtf, ex, bx);
+    }
+    my.exn[k] = ex;
+    my.bxn[k] = bx;
+    if (out) {
+      t.sA(0, k, lx, lane) = ex;
+      t.sA(1, k, lx, lane) = bx;
+    }
+  }
+}
+
+// P1 phase 2: Gamma_a of the lane's row, E_x^(n+1/2) of the row above from
+// the next lane.
+template <class R, int M, bool FAST>
+QDS_HD void p1_source(Tile<R, M, false, FAST> t, int lx, int lane, bool out, const P1Lane<R, M> *L) {
+  if (!out || !(t.flags & (F_AXION | F_AREM))) return;
+  t.set_point(t.x0 + lx);
+  source_point(t, lx, lane, P1Vals<R, M>{L, lane});
+}
+
+// P2 phase 1: the shift of cells w and w+1 (T^(n+1), T_a^(n+1/2)) and phi^(n+1)
+// at face w; cell w and face w are stored if out.
+template <class R, int M, bool FAST>
+QDS_HD void p2_shift(Tile<R, M, false, FAST> t, int lx, int lane, bool out, P2Lane<R, M> &my) {
+  const int c = t.x0 + lx, j = t.r0 + lane;
+  const bool ax = (t.flags & (F_AXION | F_AREM)) != 0;
+  Faces0<R, M, false, FAST> fs{t};
+#pragma unroll 1
+  for (int k = 0; k < M; k++) {
+    C<R> ns[6], ap[2], am[2];
+    for (int q = 0; q < 6; q++) ns[q] = zero<R>();
+    for (int dc = 0; dc < 2; dc++) {
+      const int cc = c + dc, lxx = lx + dc;
+      t.set_point(cc);
+      const bool live = t.cell_ok(cc) && j >= 0 && j < t.nr;
+      C<R> tp = zero<R>(), tm = zero<R>(), up = zero<R>(), um = zero<R>();
+      ap[dc] = am[dc] = zero<R>();
+      if (live) {
+        if (j < t.J || t.closed) tr_interior(t, fs, 0, k, lxx, lane, tp, tm);
+        else {
+          C<R> ip, im_;
+          tr_interior(t, fs, 0, k, lxx, lane - 1, ip, im_);
+          tr_outer(t, fs, 0, k, lxx, R(0.5) * (ip - im_), lane, tp, tm);
+        }
+        tt_update(t, fs, 0, k, lxx, lane, up, um);
+        if (ax) {
+          ap[dc] = t.cell(TAP, k, cc - 1, j) + t.h * t.sG(k, lxx - 1, lane);
+          am[dc] = t.cell(TAM, k, cc + 1, j) + t.h * t.sG(k, lxx, lane);
+        }
+      }
+      ns[0] += tp; ns[1] += tm; ns[2] += up; ns[3] += um; ns[4] += ap[dc]; ns[5] += am[dc];
+      if (dc == 0 && out) {
+        t.store(TRP, k, c, j, tp); t.store(TRM, k, c, j, tm);
+        t.store(TTP, k, c, j, up); t.store(TTM, k, c, j, um);
+        if (ax) { t.store(TAP, k, c, j, ap[0]); t.store(TAM, k, c, j, am[0]); }
+      }
+    }
+    for (int q = 0; q < 6; q++) my.ns[q][k] = ns[q];
+    my.phn[k] = zero<R>();
+    if (ax) {
+      t.set_point(c);
+      const bool flive = t.face_ok(c) && j >= 0 && j < t.nr;
+      C<R> v = zero<R>(), po = zero<R>();
+      if (flive) {
+        po = t.face(PHI, k, c, j);
+        v = po + (R(0.25) * t.h) * (am[1] + am[0] + ap[1] + ap[0]);
+      }
+      my.phn[k] = v;
+      if (out) {
+        t.sP(k, lx, lane) = v;
+        if (j == t.J) t.store_prev(k, c, po);
+      }
+    }
+  }
+}
+
+// P2 phase 2: j_a at face w (the new-level sums of rows j-1..j+1 from the
+// neighbouring lanes) and the regenerated leapfrog of the face.
+template <class R, int M, bool FAST>
+QDS_HD void p2_current(Tile<R, M, false, FAST> t, int lx, int lane, bool out, const P2Lane<R, M> *L) {
+  if (!out || !(t.flags & F_AREM)) return;
+  const int w = t.x0 + lx, j = t.r0 + lane;
+  t.set_point(w);
+  C<R> jax[M], jat[M];
+  current_point(t, lx, lane, jax, jat, P2Vals<R, M>{L, t.r0});
+  const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+#pragma unroll 1
+  for (int k = 0; k < M; k++) {
+    C<R> ex = zero<R>(), bx = zero<R>();
+    if (live) leap_point(t, 9, k, w, j, jax[k], jat[k], ex, bx);
+    t.sJ(0, k, lx, lane) = ex;
+    t.sJ(1, k, lx, lane) = bx;
   }
 }
 
@@ -654,7 +899,7 @@ enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, S
 template <class R, int M, bool SM, bool FAST = false>
 QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
   const Geo &g = t.g;
-  const uint32_t fl = t.I->flags;
+  const uint32_t fl = t.flags;
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0;
   // region of a stage: its halo region (fused) or the tile itself (pass mode)
   auto region = [&](int x0_, int nx_, int r0_, int nr_, int &xa, int &nxr, int &ra, int &nrr) {
@@ -690,12 +935,9 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
       for (int k = 0; k < M; k++) {
         C<R> ex = zero<R>(), bx = zero<R>();
         if (live) {
-          ex = ex_update(t, 0, k, w, j, t.srcv(t.I->jx, k, w, j));
-          if (j < t.J || t.closed) bx = bx_interior(t, 0, k, w, j);
-          else {
-            C<R> jtf = R(0.5) * (t.srcv(t.I->jt, k, w, j) + t.srcv(t.I->jt, k, w + 1, j));
-            bx = bx_outer(t, 0, k, w, jtf, bx_interior(t, 0, k, w, j - 1));
-          }
+          C<R> jtf = zero<R>();
+          if (j == t.J && !t.closed) jtf = R(0.5) * (t.srcv(t.jt, k, w, j) + t.srcv(t.jt, k, w + 1, j));
+          leap_point(t, 0, k, w, j, t.srcv(t.jx, k, w, j), jtf, ex, bx);
         }
         t.sA(0, k, lx, lr) = ex;
         t.sA(1, k, lx, lr) = bx;
@@ -720,7 +962,7 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
       const int lx = xa + q / nrr, lr = ra + q % nrr;
       if (!SM && !t.owned(lx, lr)) continue;  // pass mode: points of the grid only
       const int c = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(c - 1);  // the shift reads cells c-1 .. c+1
+      t.set_point(c);  // the shift reads cells c-1 .. c+1 (phi: c+2)
       const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
       const bool own = t.owned(lx, lr);
 #pragma unroll 1
@@ -750,10 +992,24 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
           t.store(TTP, k, c, j, up); t.store(TTM, k, c, j, um);
           if (ax) { t.store(TAP, k, c, j, ap); t.store(TAM, k, c, j, am); }
         }
+        if (ax && !SM) {
+          // pass mode: phi at face c (Eq. phi_update) from T_a^(n+1/2) of
+          // cells c (above) and c+1 (formed here from Gamma_a of faces c, c+1)
+          const bool flive = t.face_ok(c) && j >= 0 && j < t.nr;
+          C<R> v = zero<R>(), po = zero<R>();
+          if (flive) {
+            const C<R> ap1 = t.cell(TAP, k, c, j) + t.h * t.sG(k, lx, lr);
+            const C<R> am1 = t.cell(TAM, k, c + 2, j) + t.h * t.sG(k, lx + 1, lr);
+            po = t.face(PHI, k, c, j);
+            v = po + (R(0.25) * t.h) * (am1 + am + ap1 + ap);
+          }
+          t.sP(k, lx, lr) = v;
+          if (j == t.J) t.store_prev(k, c, po);
+        }
       }
     }
   } else if (st == ST_PHI) {
-    if (!ax) return;
+    if (!ax || !SM) return;  // pass mode: part of ST_SHIFT0
     region(g.p_x0(), g.p_nx(), g.p_r0(), g.p_nr(), xa, nxr, ra, nrr);
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
@@ -780,12 +1036,26 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
     region(g.j_x0(), g.j_nx(), g.j_r0(), g.j_nr(), xa, nxr, ra, nrr);
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
-      if (!SM && !t.owned(xa + q / nrr, ra + q % nrr)) continue;
-      t.set_point(t.x0 + xa + q / nrr);
-      current_point(t, xa + q / nrr, ra + q % nrr);
+      const int lx = xa + q / nrr, lr = ra + q % nrr;
+      if (!SM && !t.owned(lx, lr)) continue;
+      const int w = t.x0 + lx, j = t.r0 + lr;
+      t.set_point(w);
+      C<R> jax[M], jat[M];
+      current_point(t, lx, lr, jax, jat);
+      if (SM) continue;
+      // pass mode: the regenerated leapfrog (Sec. 2.2) of this face follows
+      // at once; it needs j_a,x and (outer row) j_a,theta of this point only
+      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+#pragma unroll 1
+      for (int k = 0; k < M; k++) {
+        C<R> ex = zero<R>(), bx = zero<R>();
+        if (live) leap_point(t, 9, k, w, j, jax[k], jat[k], ex, bx);
+        t.sJ(0, k, lx, lr) = ex;
+        t.sJ(1, k, lx, lr) = bx;
+      }
     }
   } else if (st == ST_LEAP1) {
-    if (!ar) return;
+    if (!ar || !SM) return;  // pass mode: part of ST_CURRENT
     region(g.j_x0(), g.j_nx(), g.j_r0(), g.j_nr(), xa, nxr, ra, nrr);
     const int npt = nxr * nrr;
     for (int q = tid; q < npt; q += nth) {
@@ -797,11 +1067,7 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
 #pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> ex = zero<R>(), bx = zero<R>();
-        if (live) {
-          ex = ex_update(t, 9, k, w, j, t.sJ(2, k, lx, lr));
-          if (j < t.J || t.closed) bx = bx_interior(t, 9, k, w, j);
-          else bx = bx_outer(t, 9, k, w, t.sJ(4, k, lx, lr), bx_interior(t, 9, k, w, j - 1));
-        }
+        if (live) leap_point(t, 9, k, w, j, t.sJ(2, k, lx, lr), t.sJ(4, k, lx, lr), ex, bx);
         t.sJ(0, k, lx, lr) = ex;
         t.sJ(1, k, lx, lr) = bx;
         if (SM && t.owned(lx, lr)) { t.store(EX1, k, w, j, ex); t.store(BX1, k, w, j, bx); }
@@ -815,7 +1081,7 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
       const int lx = q / g.TR, lr = q % g.TR;
       if (!t.owned(lx, lr)) continue;
       const int c = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(c - 1);
+      t.set_point(c);
 #pragma unroll 1
       for (int k = 0; k < M; k++) {
         C<R> tp, tm, up, um;

@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqds.so")
 
 AXION, AREM, MOVING_WINDOW, X_PERIODIC, R_CLOSED, FP32, SCALE_G = 1, 2, 4, 8, 16, 32, 64
+STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP, STEP_WARP_LEAP = 0, 1, 2, 3, 4
 FIELDS = ("Trp", "Trm", "Ttp", "Ttm", "Ex", "Bx", "phi", "Tap", "Tam",
           "Trp1", "Trm1", "Ttp1", "Ttm1", "Ex1", "Bx1")
 N_FIELDS = 15
@@ -67,6 +68,7 @@ def lib():
             "qds_diagnostics_all": (i, [H, vp, vp]),
             "qds_set_tile": (i, [H, i, i]),
             "qds_set_fused": (i, [H, i]),
+            "qds_set_step_mode": (i, [H, i]),
             "qds_get_tile": (i, [H, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
             "qds_free": (None, [H]),
             "qds_last_error": (ctypes.c_char_p, []),
@@ -227,6 +229,10 @@ class QDSSolver:
 
     def set_fused(self, fused: bool):
         _check(lib().qds_set_fused(self.h, int(bool(fused))))
+
+    def set_step_mode(self, mode: int):
+        """STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP or STEP_WARP_LEAP."""
+        _check(lib().qds_set_step_mode(self.h, int(mode)))
 
     def set_tile(self, tx, tr):
         _check(lib().qds_set_tile(self.h, int(tx), int(tr)))

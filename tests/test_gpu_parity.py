@@ -17,13 +17,16 @@ from tests._helpers import (fp32_tolerance, group_errors, oracle_run, parity_cas
 DEV = "cuda:0"
 
 
-def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=None, fused=False):
+MODES = [Q.STEP_STAGES, Q.STEP_FUSED, Q.STEP_WARP, Q.STEP_WARP_LEAP]
+
+
+def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=None, mode=Q.STEP_DEFAULT):
     p = Q.Params(nx, nr, M, dr, g=g, m_a=m_a, flags=flags)
     s = Q.QDSSolver(p, device=DEV)
     if tile:
         s.set_tile(*tile)
-    if fused or tile:
-        s.set_fused(True)
+        mode = Q.STEP_FUSED
+    s.set_step_mode(mode)
     s.set_state(torch.from_numpy(buf).to(DEV))
     kw = {}
     if src is not None:
@@ -36,17 +39,31 @@ def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=No
     return s.get_state().cpu().numpy(), s
 
 
-@pytest.mark.parametrize("fused", [False, True])
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("M,flags", parity_cases())
-def test_fp64_parity_random_states(M, flags, fused):
+def test_fp64_parity_random_states(M, flags, mode):
     nx, nr = 37, 21
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 100 + flags, M, nx, nr)
     for nsteps in (3, 20):  # 20 steps replays a captured graph
         ref = oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src)
-        got, _ = gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src, fused=fused)
+        got, _ = gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src, mode=mode)
         for name, e in group_errors(got, ref, M, nx, nr).items():
             assert e < 1e-12, (nsteps, name, e)
+
+
+@pytest.mark.parametrize("mode", [Q.STEP_WARP, Q.STEP_WARP_LEAP])
+@pytest.mark.parametrize("M,flags", [c for c in parity_cases() if c[1] & 2])
+def test_fp64_parity_warp_seams(M, flags, mode):
+    """nr = 70 puts three warps on every column (seams at rows 31/62 for the
+    first warp pass and 30/60 for the second); nx = 45 has interior tiles."""
+    nx, nr = 45, 70
+    dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
+    buf, src = random_case(M * 31 + flags, M, nx, nr)
+    ref = oracle_run(buf, M, nx, nr, dr, flags, 4, g=g, m_a=m_a, src=src)
+    got, _ = gpu_run(buf, M, nx, nr, dr, flags, 4, g=g, m_a=m_a, src=src, mode=mode)
+    for name, e in group_errors(got, ref, M, nx, nr).items():
+        assert e < 1e-12, (name, e)
 
 
 @pytest.mark.parametrize("tile", [(4, 8), (8, 16), (16, 8), (3, 5)])
@@ -60,8 +77,9 @@ def test_fp64_parity_tile_shapes(tile):
         assert e < 1e-12, (name, e)
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("M", [2, 3, 4])
-def test_fp32_scaled_parity(M):
+def test_fp32_scaled_parity(M, mode):
     nx, nr = 64, 24
     dr, g = stable_dr(M), 1e-6
     flags = 1 | 2 | 4
@@ -72,7 +90,7 @@ def test_fp32_scaled_parity(M):
     buf[9 * n:15 * n] *= g * g
     src[3] = None
     ref = oracle_run(buf, M, nx, nr, dr, flags, 10, g=g, src=src)
-    got, _ = gpu_run(buf, M, nx, nr, dr, flags | Q.FP32, 10, g=g, src=src)
+    got, _ = gpu_run(buf, M, nx, nr, dr, flags | Q.FP32, 10, g=g, src=src, mode=mode)
     e = group_errors(got, ref, M, nx, nr)
     assert e["em"] < 1e-5 and e["arem"] < 1e-4 and e["axion"] < 1e-4, e
 
