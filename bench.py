@@ -13,6 +13,7 @@ workload; the FP64 CPU oracle is timed on a bounded sample on the host cores.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -157,6 +158,49 @@ def cpu_baseline(wls, flags, budget_s):
             "sample": f"one FP64 step of each of the first {len(used)} instances ({units} cell-modes, {t_total:.1f} s)"}
 
 
+def adjoint_bench(device, steps, every):
+    """Gradient of the axion energy around the pulses after ``steps`` steps of
+    the two-colour + bunch run (FP32, 4096 x 128, modes 0..2) with respect to
+    the laser-2 radial profile, omega2 and g, by run_qds (checkpoints every
+    ``every`` steps, recompute, transposed steps).  Reports the forward and
+    backward times and the identity dL/dg = 2 L / g (the axion grows from
+    zero and is linear in g)."""
+    import torch
+    from paper_2609_03550_b300 import adjoint as A
+    from paper_2609_03550_b300 import inputs as I
+    from paper_2609_03550_b300 import qds as Q
+    wl = I.adjoint_run(steps=steps)
+    ex = wl.extra
+    p = Q.Params(wl.nx, wl.nr, wl.M, wl.dr, g=wl.g, m_a=wl.m_a,
+                 flags=Q.AXION | Q.AREM | Q.MOVING_WINDOW | Q.FP32)
+    src = I.DeviceBunchSources(wl, device, torch.complex64)
+    spec = A.RunSpec(p, steps, every=every, sources=src, device=str(device))
+    prof = torch.tensor(ex["profile2"], dtype=torch.complex128, device=device, requires_grad=True)
+    om = torch.tensor(ex["omega2"], dtype=torch.float64, device=device, requires_grad=True)
+    g = torch.tensor(wl.g, dtype=torch.float64, device=device, requires_grad=True)
+    base = wl.initial_state(device=device)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    s0 = A.laser2_state(base, p, prof, om, ex["x0"], ex["fwhm"])
+    L = A.axion_energy(A.run_qds(s0, g, spec), p, *ex["window"])
+    ev[1].record()
+    L.backward()
+    ev[2].record()
+    torch.cuda.synchronize()
+    fwd, bwd = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
+    Lv, gg = float(L.detach()), float(g.grad)
+    units = wl.cell_modes() * steps
+    return {"workload": wl.name, "steps": steps, "checkpoint_every": spec.interval(), "dtype": "f32",
+            "params": "laser-2 radial profile (%d complex), omega2, g" % wl.nr,
+            "loss": "axion energy in window cells [%d, %d)" % ex["window"], "L": Lv,
+            "forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
+            "value": units / (fwd + bwd), "unit": "cell-mode updates/s (forward + gradient)",
+            "dLdg_vs_2L_over_g": abs(gg - 2 * Lv / wl.g) / abs(gg),
+            "grad_finite": bool(torch.isfinite(prof.grad).all()) and math.isfinite(float(om.grad)) and math.isfinite(gg),
+            "checks": "gradients vs oracle central differences and oracle Jacobian columns: tests/test_gpu_adjoint.py"}
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -219,7 +263,7 @@ def run_qds(args):
     # ---------------- FP32 batched ----------------
     s = build_solver(wls, flags | Q.FP32, device)
     tile = s.tile()
-    groups_per_step = len({w.M for w in wls}) + 1   # step kernels (one per mode count) + counter advance
+    launches_per_step = s.step_launches()
     s.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
     clocks = Clocks(local)
@@ -265,6 +309,11 @@ def run_qds(args):
         del s64
         torch.cuda.empty_cache()
 
+    adj = None
+    if world == 1 and not args.no_adjoint:
+        adj = adjoint_bench(device, args.adjoint_steps, args.adjoint_every)
+        torch.cuda.empty_cache()
+
     if rank != 0:
         return
     peak, peak_kind = measured_peak()
@@ -286,13 +335,15 @@ def run_qds(args):
                    "tile": tile},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "step_kernel (all mode-count launches of one step)",
+                     "kernel": "the pass kernels of one step, all mode counts (the step reads and writes "
+                               "the state once in algorithmic terms)",
                      "bytes_per_unit": BYTES_PER_UNIT["f32"], "peak_kind": peak_kind},
         "fp64_plain": fp64,
         "e2e": {"value": world * units * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(diag_host.numel() * 8), "finite": e2e_finite,
                 "per_step": "step + diagnostics of all instances + device-to-host read"},
-        "gpu_launches": args.steps * groups_per_step,
+        "gpu_launches": args.steps * launches_per_step,
+        "adjoint": adj,
         "clocks": clk,
         "cpu_baseline": cpu,
     }
@@ -312,6 +363,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--instances", type=int, default=512, help="first N instances (profiling runs only)")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=8000)
+    ap.add_argument("--adjoint-every", type=int, default=90)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "qds":
         args.warmup = 3

@@ -151,6 +151,8 @@ int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
 #define QDS_STEP_WARP 3
 #define QDS_STEP_WARP_LEAP 4
 int qds_set_step_mode(qds_handle *h, int mode);
+/* Kernel launches of one step in the current mode (0 for a NULL handle). */
+int qds_step_launches(const qds_handle *h);
 int qds_set_fused(qds_handle *h, int fused);
 
 /* Tile shape of the fused step kernel (x cells, radial rows); used by the

@@ -529,6 +529,28 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   return QDS_OK;
 }
 
+int qds_step_launches(const qds_handle *h) {
+  if (!h) return 0;
+  const int mode = h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode;
+  if (mode == QDS_STEP_FUSED) return (int)h->groups.size() + 1;
+  int n = 1;  // step counter
+  for (const auto &G : h->pgroups) {
+    uint32_t fl = 0;
+    for (int i = 0; i < h->n_inst; i++)
+      if (h->params[i].n_modes == G.M) fl |= h->params[i].flags;
+    const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
+    const int stage = (G.n_interior > 0) + (G.ntiles > G.n_interior);
+    const int w1 = (G.nw_interior[0] > 0) + (G.nw[0] > G.nw_interior[0]);
+    const int w2 = (G.nw_interior[1] > 0) + (G.nw[1] > G.nw_interior[1]);
+    if (mode == QDS_STEP_STAGES) n += stage * (1 + (ax ? 1 : 0));
+    else n += w1;
+    if (mode == QDS_STEP_WARP) n += w2;
+    else n += stage * (1 + (ar ? 1 : 0));
+    n += stage * ((ar ? 1 : 0) + (mw ? 1 : 0));
+  }
+  return n;
+}
+
 int qds_set_fused(qds_handle *h, int fused) { return qds_set_step_mode(h, fused ? QDS_STEP_FUSED : QDS_STEP_DEFAULT); }
 
 int qds_set_step_mode(qds_handle *h, int mode) {

@@ -237,3 +237,63 @@ def bunch_currents(wl: Workload, step: int):
         im[0] = 0.0
         a += amp * (re + 1j * im)
     return jx, jr, jt
+
+
+def adjoint_run(nx=4096, nr=128, steps=8000):
+    """Gradient workload: the two-colour pair of the two-colour run (pulse 1
+    lambda 16, a0 0.5, y; pulse 2 omega2 = 0.8 omega1, a0 0.5, z; waist
+    32 dr, FWHM 64, x0 = 0.75 nx) with modes {0, 1, 2}, plus the driven-wake
+    electron bunch (rho -0.05, sigma_x 8, sigma_r 6 dr) 256 cells behind the
+    pulses and 1% uniform noise on every current, redrawn each step (seed 1);
+    moving window, dr = 5, g = 1e-6, m_a = 0.  ``lasers`` holds pulse 1
+    only: pulse 2 is the differentiated input (its radial profile and
+    omega2), with its default values in ``extra``."""
+    dr = 5.0
+    x0 = 0.75 * nx
+    lam1, a0, w0, fwhm = 16.0, 0.5, 32 * dr, 64.0
+    omega2 = 0.8 * 2 * math.pi / lam1
+    r_half = (np.arange(nr) + 0.5) * dr
+    profile2 = (a0 * omega2 * np.exp(-(r_half ** 2) / w0 ** 2)).astype(np.complex128)
+    return Workload(f"adjoint_two_colour_bunch_{nx}x{nr}_m3", nx, nr, 3, dr, steps,
+                    [Laser(a0, lam1, w0, fwhm, x0, "y")], axion=True, arem=True, moving_window=True,
+                    g=1e-6, m_a=0.0,
+                    bunch=dict(rho=-0.05, sx=8.0, sr=6 * dr, x0=x0 - 256.0, noise=0.01, seed=1),
+                    extra=dict(x0=x0, fwhm=fwhm, omega2=omega2, profile2=profile2, window=(int(x0) - 256, int(x0) + 256)))
+
+
+class DeviceBunchSources:
+    """Per-step currents of a bunch workload on a CUDA device, written into
+    three fixed buffers (so a solver sees the same source pointers every
+    step): the m = 0 bunch j_x, stationary in a window that moves at c, plus
+    uniform noise of amplitude noise * |rho| on every component, mode and
+    cell (imaginary part zero for m = 0), from torch's device generator
+    seeded by (seed, step).  Calling it with the same step reproduces the
+    same values."""
+
+    def __init__(self, wl, device, dtype):
+        import torch
+        b = wl.bunch
+        self.torch = torch
+        self.M, self.nx, self.nr = wl.M, wl.nx, wl.nr
+        self.seed, self.amp = int(b["seed"]), float(b["noise"] * abs(b["rho"]))
+        self.dtype, self.device = dtype, device
+        x = (torch.arange(wl.nx, dtype=torch.float64, device=device) + 0.5)[:, None]
+        r = (torch.arange(wl.nr, dtype=torch.float64, device=device) * wl.dr)[None, :]
+        self.bunch = (b["rho"] * torch.exp(-((x - b["x0"]) ** 2) / (2 * b["sx"] ** 2))
+                      * torch.exp(-(r ** 2) / (2 * b["sr"] ** 2))).to(dtype)
+        self.buf = [torch.zeros((wl.M, wl.nx, wl.nr), dtype=dtype, device=device) for _ in range(3)]
+        self.gen = torch.Generator(device=device)
+        rdt = torch.float32 if dtype == torch.complex64 else torch.float64
+        self.noise = torch.empty((3, 2, wl.M, wl.nx, wl.nr), dtype=rdt, device=device)
+
+    def __call__(self, step):
+        self.gen.manual_seed(self.seed * 1_000_003 + int(step))
+        self.noise.uniform_(-1.0, 1.0, generator=self.gen)
+        self.noise[:, 1, 0] = 0.0
+        for c in range(3):
+            v = self.buf[c].view(self.torch.float32 if self.dtype == self.torch.complex64 else self.torch.float64)
+            v = v.view(self.M, self.nx, self.nr, 2)
+            v[..., 0] = self.amp * self.noise[c, 0]
+            v[..., 1] = self.amp * self.noise[c, 1]
+        self.buf[0][0] += self.bunch
+        return tuple(self.buf)

@@ -69,6 +69,7 @@ def lib():
             "qds_set_tile": (i, [H, i, i]),
             "qds_set_fused": (i, [H, i]),
             "qds_set_step_mode": (i, [H, i]),
+            "qds_step_launches": (i, [H]),
             "qds_get_tile": (i, [H, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
             "qds_free": (None, [H]),
             "qds_last_error": (ctypes.c_char_p, []),
@@ -229,6 +230,10 @@ class QDSSolver:
 
     def set_fused(self, fused: bool):
         _check(lib().qds_set_fused(self.h, int(bool(fused))))
+
+    def step_launches(self) -> int:
+        """Kernel launches of one step in the current step mode."""
+        return int(lib().qds_step_launches(self.h))
 
     def set_step_mode(self, mode: int):
         """STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP or STEP_WARP_LEAP."""
