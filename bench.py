@@ -33,8 +33,7 @@ WORDS = 15
 BYTES_PER_UNIT = {"f32": 2 * WORDS * 8, "f64": 2 * WORDS * 16}
 
 
-def env_rank():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+from paper_2609_03550_b300.ranks import env_rank  # noqa: E402
 
 
 def measured_peak():
@@ -115,11 +114,13 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_solver(wls, flags, device):
+def build_solver(wls, flags, device, autotune=False):
     import torch
     from paper_2609_03550_b300 import qds as Q
     params = [Q.Params(w.nx, w.nr, w.M, w.dr, g=w.g, m_a=w.m_a, flags=flags) for w in wls]
     s = Q.QDSSolver(params, device=device)
+    if autotune:
+        s.autotune()  # before the initial state is set: the trial steps advance the state
     for i, w in enumerate(wls):
         s.set_state(w.initial_state(device=device), i=i)
     torch.cuda.synchronize()
@@ -234,24 +235,12 @@ def run_reference(args):
 
 def run_qds(args):
     import torch
+    from paper_2609_03550_b300.ranks import Ranks, job_throughput
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=device)
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl", device)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     from paper_2609_03550_b300 import inputs as I
     from paper_2609_03550_b300 import qds as Q
@@ -261,8 +250,9 @@ def run_qds(args):
     stream = torch.cuda.current_stream(device)
 
     # ---------------- FP32 batched ----------------
-    s = build_solver(wls, flags | Q.FP32, device)
+    s = build_solver(wls, flags | Q.FP32, device, autotune=True)
     tile = s.tile()
+    tile["step_mode"] = s.step_mode_name()
     launches_per_step = s.step_launches()
     s.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
@@ -315,6 +305,7 @@ def run_qds(args):
         torch.cuda.empty_cache()
 
     if rank != 0:
+        ranks.close()
         return
     peak, peak_kind = measured_peak()
     achieved = units * BYTES_PER_UNIT["f32"] / step32 / 1e9
@@ -323,7 +314,7 @@ def run_qds(args):
     if world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wls, flags, args.cpu_seconds)
     out = {
-        "metric": METRIC, "value": world * units / step32, "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(units, world, step32), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step32,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -348,8 +339,7 @@ def run_qds(args):
         "cpu_baseline": cpu,
     }
     print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def main():

@@ -230,6 +230,36 @@ class QDSSolver:
 
     def set_fused(self, fused: bool):
         _check(lib().qds_set_fused(self.h, int(bool(fused))))
+        self._mode = STEP_FUSED if fused else STEP_DEFAULT
+
+    def autotune(self, steps: int = 6, modes=None, stream=None) -> int:
+        """Time the pass-mode step implementations on this batch and keep
+        the fastest (the fused tile kernel is far slower and is not tried).
+        The trial steps advance the state: call before set_state."""
+        modes = modes or (STEP_STAGES, STEP_WARP_LEAP, STEP_WARP)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        best, best_t = None, None
+        self.timings = {}
+        for m in modes:
+            self.set_step_mode(m)
+            self.step(2, stream=s)  # first launches of this mode
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            self.step(steps, stream=s)
+            e1.record(s)
+            e1.synchronize()
+            t = e0.elapsed_time(e1) / steps
+            self.timings[m] = t
+            if best_t is None or t < best_t:
+                best, best_t = m, t
+        self.set_step_mode(best)
+        self._mode = best
+        return best
+
+    def step_mode_name(self) -> str:
+        names = {STEP_DEFAULT: "default", STEP_FUSED: "fused", STEP_STAGES: "stage passes",
+                 STEP_WARP: "warp-column passes", STEP_WARP_LEAP: "warp-column leapfrog + stage passes"}
+        return names[getattr(self, "_mode", STEP_DEFAULT)]
 
     def step_launches(self) -> int:
         """Kernel launches of one step in the current step mode."""
@@ -238,6 +268,7 @@ class QDSSolver:
     def set_step_mode(self, mode: int):
         """STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP or STEP_WARP_LEAP."""
         _check(lib().qds_set_step_mode(self.h, int(mode)))
+        self._mode = int(mode)
 
     def set_tile(self, tx, tr):
         _check(lib().qds_set_tile(self.h, int(tx), int(tr)))

@@ -209,3 +209,23 @@ def test_batched_uneven_instances_match_single_runs():
         got = s.get_state(i).cpu().numpy()
         e = group_errors(got, ref, w.M, w.nx, w.nr)
         assert all(e[k] < tol[k] for k in e), (i, e, tol)
+
+
+def test_autotune_then_parity():
+    """The autotuner times the pass-mode implementations and keeps one; the
+    solve that follows still matches the oracle."""
+    M, nx, nr, flags = 3, 48, 40, 1 | 2 | 4
+    dr, g = stable_dr(M), 0.2
+    buf, src = random_case(5, M, nx, nr)
+    p = Q.Params(nx, nr, M, dr, g=g, flags=flags)
+    s = Q.QDSSolver([p, p], device=DEV)
+    best = s.autotune(steps=2)
+    assert best in (Q.STEP_STAGES, Q.STEP_WARP, Q.STEP_WARP_LEAP) and len(s.timings) == 3
+    for i in range(2):
+        s.set_state(torch.from_numpy(buf).to(DEV), i)
+    s.step(5)
+    ref = oracle_run(buf, M, nx, nr, dr, flags, 5, g=g)
+    for i in range(2):
+        got = s.get_state(i).cpu().numpy()
+        for name, e in group_errors(got, ref, M, nx, nr).items():
+            assert e < 1e-12, (i, name, e)
