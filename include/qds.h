@@ -143,13 +143,17 @@ int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
  *                       another (radial neighbours through shared memory,
  *                       the shift of the next cell recomputed), then the
  *                       regenerated shift;
- *   QDS_STEP_WARP_LEAP  the first warp-column pass, then the stage passes.
+ *   QDS_STEP_WARP_LEAP  the first warp-column pass, then the stage passes;
+ *   QDS_STEP_FLAT       the stage passes over flat ranges of 256 points of
+ *                       an instance (x, r order) instead of 8 x 32 tiles, so
+ *                       that no thread idles on rows beyond nr.
  * qds_set_fused(h, 1) selects QDS_STEP_FUSED and (h, 0) QDS_STEP_DEFAULT. */
 #define QDS_STEP_DEFAULT 0
 #define QDS_STEP_FUSED 1
 #define QDS_STEP_STAGES 2
 #define QDS_STEP_WARP 3
 #define QDS_STEP_WARP_LEAP 4
+#define QDS_STEP_FLAT 5
 int qds_set_step_mode(qds_handle *h, int mode);
 /* Kernel launches of one step in the current mode (0 for a NULL handle). */
 int qds_step_launches(const qds_handle *h);

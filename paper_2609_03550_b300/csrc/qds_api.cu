@@ -5,6 +5,7 @@
 // step counter, a small diagnostics scratch and any captured CUDA graphs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -35,7 +36,7 @@ int fail(int code, const std::string &msg) {
 
 constexpr int kThreads = 256;
 // the step implementation behind QDS_STEP_DEFAULT
-constexpr int kDefaultMode = QDS_STEP_STAGES;
+constexpr int kDefaultMode = QDS_STEP_FLAT;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -126,6 +127,9 @@ struct qds_handle {
     // warp-column passes P1 (31 output rows per warp) and P2 (30), interior first
     int4 *d_w[2] = {nullptr, nullptr};
     int nw[2] = {0, 0}, nw_interior[2] = {0, 0};
+    // flat stage passes: (instance, first point, points, 0), interior first
+    int4 *d_flat = nullptr;
+    int nflat = 0, nflat_interior = 0;
   };
   std::vector<Group> groups;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
@@ -218,6 +222,17 @@ cudaError_t launch_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t 
   return cudaGetLastError();
 }
 
+template <class R, int M, int ST>
+cudaError_t launch_flat(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  if (G.nflat_interior > 0)
+    flat_pass_kernel<R, M, ST, true><<<G.nflat_interior, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_flat,
+                                                                            h->d_ctrl);
+  if (G.nflat > G.nflat_interior)
+    flat_pass_kernel<R, M, ST, false><<<G.nflat - G.nflat_interior, kThreads, 0, st>>>(
+        (const Inst<R> *)h->d_inst, G.d_flat + G.nflat_interior, h->d_ctrl);
+  return cudaGetLastError();
+}
+
 template <class R, int M, int PASS>
 cudaError_t launch_warp_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
   const int q = PASS - 1;
@@ -256,6 +271,15 @@ template <class R, int M>
 cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl, int mode, cudaStream_t st) {
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
   cudaError_t e;
+  if (mode == QDS_STEP_FLAT) {
+    if ((e = launch_flat<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
+    if (ax && (e = launch_flat<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
+    if ((e = launch_flat<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_flat<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_flat<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
+    if (mw && (e = launch_flat<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
   if (mode == QDS_STEP_STAGES) {
     if ((e = launch_pass<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
     if (ax && (e = launch_pass<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
@@ -438,6 +462,27 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
         CU(cudaMemcpy(P.d_w[q], wi.data(), sizeof(int4) * wi.size(), cudaMemcpyHostToDevice));
       }
       CU(allow_warp_smem(fp32, M));
+      {
+        std::vector<int4> fi, fe;
+        for (int i = 0; i < n; i++) {
+          if (params[i].n_modes != M) continue;
+          const int nx_ = params[i].nx, nr_ = params[i].nr;
+          const bool per = (params[i].flags & QDS_X_PERIODIC) != 0;
+          const int total = nx_ * nr_;
+          for (int q0 = 0; q0 < total; q0 += kThreads) {
+            const int cnt = std::min(kThreads, total - q0);
+            const int w0 = q0 / nr_, w1 = (q0 + cnt - 1) / nr_;
+            // interior: columns w0-2 .. w1+2 are cells and w1+2 is a real face
+            const bool inner = per ? (nx_ >= (w1 - w0 + 1) + 4) : (w0 >= 2 && w1 + 3 <= nx_ - 1);
+            (inner ? fi : fe).push_back(make_int4(i, q0, cnt, 0));
+          }
+        }
+        P.nflat_interior = (int)fi.size();
+        fi.insert(fi.end(), fe.begin(), fe.end());
+        P.nflat = (int)fi.size();
+        CU(cudaMalloc(&P.d_flat, sizeof(int4) * fi.size()));
+        CU(cudaMemcpy(P.d_flat, fi.data(), sizeof(int4) * fi.size(), cudaMemcpyHostToDevice));
+      }
       h->pgroups.push_back(P);
     }
   }
@@ -448,7 +493,7 @@ void destroy(qds_handle *h) {
   if (!h) return;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &G : h->groups) cudaFree(G.d_tiles);
-  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); }
+  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); }
   cudaFree(h->d_inst);
   cudaFree(h->d_ctrl);
   cudaFree(h->d_partial);
@@ -519,7 +564,7 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   for (auto &G : h->groups) cudaFree(G.d_tiles);
   cudaFree(h->d_inst); cudaFree(h->d_ctrl); cudaFree(h->d_partial); cudaFree(h->d_diag);
   cudaFree(h->d_partial_all); cudaFree(h->d_scal);
-  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); }
+  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); }
   h->groups = nh->groups; h->pgroups = nh->pgroups; h->d_inst = nh->d_inst; h->d_ctrl = nh->d_ctrl;
   h->d_partial_all = nh->d_partial_all; h->d_scal = nh->d_scal;
   h->d_partial = nh->d_partial; h->d_diag = nh->d_diag; h->h_inst = nh->h_inst;
@@ -542,6 +587,11 @@ int qds_step_launches(const qds_handle *h) {
     const int stage = (G.n_interior > 0) + (G.ntiles > G.n_interior);
     const int w1 = (G.nw_interior[0] > 0) + (G.nw[0] > G.nw_interior[0]);
     const int w2 = (G.nw_interior[1] > 0) + (G.nw[1] > G.nw_interior[1]);
+    if (mode == QDS_STEP_FLAT) {
+      const int f = (G.nflat_interior > 0) + (G.nflat > G.nflat_interior);
+      n += f * (2 + (ax ? 1 : 0) + (ar ? 2 : 0) + (mw ? 1 : 0));
+      continue;
+    }
     if (mode == QDS_STEP_STAGES) n += stage * (1 + (ax ? 1 : 0));
     else n += w1;
     if (mode == QDS_STEP_WARP) n += w2;
@@ -555,7 +605,7 @@ int qds_set_fused(qds_handle *h, int fused) { return qds_set_step_mode(h, fused 
 
 int qds_set_step_mode(qds_handle *h, int mode) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
-  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_WARP_LEAP) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
+  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_FLAT) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
   h->mode = mode;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();

@@ -29,8 +29,10 @@ enum Flag : uint32_t {
   F_R_CLOSED = 16u, F_FP32 = 32u, F_SCALE_G = 64u
 };
 
+// Aligned to its size, so that one complex value moves as one 8-byte (FP32)
+// or 16-byte (FP64) access.
 template <class R>
-struct C {
+struct alignas(2 * sizeof(R)) C {
   R re, im;
 };
 

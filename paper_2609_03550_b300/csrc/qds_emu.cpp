@@ -1,3 +1,4 @@
+#include <algorithm>
 // qds_emu.cpp -- host emulation of the fused step kernel, for CPU tests only.
 //
 // Compiles the same stage code as the CUDA kernel (qds_stages.cuh) for the
@@ -122,6 +123,34 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
           t.g.TX = TX; t.g.TR = TR;
           for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false, false>(t, st, tid, nthreads);
         }
+    }
+  }
+  // flat stage passes (fused == 3): blocks of 256 consecutive points in
+  // (x, r) order, each point a 1 x 1 tile
+  for (int n = 0; n < nsteps && fused == 3; n++) {
+    const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
+    const bool per_ = (flags & F_X_PERIODIC) != 0;
+    const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_CURRENT, ST_SHIFT1, ST_ZERO};
+    for (int st : order) {
+      if (st == ST_SOURCE && !ax) continue;
+      if ((st == ST_CURRENT || st == ST_SHIFT1) && !ar) continue;
+      if (st == ST_ZERO && !mw) continue;
+      for (int q0 = 0; q0 < nx * nr; q0 += 256) {
+        const int cnt = std::min(256, nx * nr - q0);
+        const int w0 = q0 / nr, w1 = (q0 + cnt - 1) / nr;
+        const bool inner = per_ ? (nx >= (w1 - w0 + 1) + 4) : (w0 >= 2 && w1 + 3 <= nx - 1);
+        for (int q = q0; q < q0 + cnt; q++) {
+          Tile<R, M, false, false> t = pass_tile_at(n, q / nr, q % nr);
+          t.g.TX = 1; t.g.TR = 1;
+          if (inner) {
+            Tile<R, M, false, true> tf;
+            std::memcpy((void *)&tf, (const void *)&t, sizeof t);
+            run_stage<R, M, false, true>(tf, st, 0, 1);
+          } else {
+            run_stage<R, M, false, false>(t, st, 0, 1);
+          }
+        }
+      }
     }
   }
   for (int n = 0; n < nsteps && fused == 2; n++) {

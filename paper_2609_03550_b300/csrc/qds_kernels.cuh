@@ -91,12 +91,32 @@ __device__ __forceinline__ Tile<R, M, false, FAST> pass_tile(const Inst<R> &I, i
 }
 
 template <class R, int M, int ST, bool FAST>
-__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 2 : 4)
+__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 3 : 4)
     pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
                 const Ctrl *__restrict__ ctrl, Geo g) {
   const int4 td = tiles[blockIdx.x];
   Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(insts[td.x], td, ctrl->step, g);
   run_stage<R, M, false, FAST>(t, ST, threadIdx.x, blockDim.x);
+}
+
+// Stage pass over a flat range of points: block td covers points
+// td.y .. td.y + td.z - 1 of instance td.x in (x, r) order (r fastest), one
+// point per thread, so no lane idles on rows beyond nr.  Each thread views
+// its point as a 1 x 1 tile.
+template <class R, int M, int ST, bool FAST>
+__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 3 : 4)
+    flat_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
+                     const Ctrl *__restrict__ ctrl) {
+  const int4 td = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= td.z) return;
+  const Inst<R> &I = insts[td.x];
+  const int q = td.y + (int)threadIdx.x;
+  const int w = q / I.nr, j = q - w * I.nr;
+  Geo g{};
+  g.TX = 1;
+  g.TR = 1;
+  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl->step, g);
+  run_stage<R, M, false, FAST>(t, ST, 0, 1);
 }
 
 // Warp-column passes (P1: leapfrog + Gamma_a; P2: shift + phi + j_a +

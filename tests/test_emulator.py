@@ -37,11 +37,11 @@ def run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, nsteps, TX, TR, nth=64, fuse
     return out
 
 
-# fused: 1 = fused tile kernel, 0 = warp-column passes (the default pass
-# mode), 2 = one pass per stage (the no-allocation entry point)
+# fused: 1 = fused tile kernel, 0 = warp-column passes, 2 = one pass per
+# stage over 8 x 32 tiles, 3 = the stage passes over flat point ranges
 @pytest.mark.parametrize("M,flags", parity_cases())
 @pytest.mark.parametrize("tile,fused", [((8, 32), 1), ((5, 3), 1), ((8, 32), 0), ((3, 4), 0), ((8, 32), 2),
-                                        ((3, 4), 2)])
+                                        ((3, 4), 2), ((8, 32), 3)])
 def test_emulated_kernel_matches_oracle_fp64(M, flags, tile, fused):
     nx, nr = 21, 11
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
@@ -53,21 +53,23 @@ def test_emulated_kernel_matches_oracle_fp64(M, flags, tile, fused):
         assert e < 1e-13, (name, e)
 
 
+@pytest.mark.parametrize("fused", [0, 3])
 @pytest.mark.parametrize("M,flags", [c for c in parity_cases() if c[1] & 2])
-def test_warp_passes_span_several_row_tiles(M, flags):
+def test_warp_passes_span_several_row_tiles(M, flags, fused):
     """nr = 70: P1 warps at rows 0, 31, 62 and P2 warps based at 0, 29, 59
     (outputs from 0, 30, 60), so every seam between warps is crossed; nx = 30
-    gives interior (unchecked) and edge tiles."""
+    gives interior (unchecked) and edge tiles; the flat passes (fused = 3)
+    cover 256 points per block across column boundaries."""
     nx, nr = 30, 70
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 17 + flags, M, nx, nr)
     ref = oracle_run(buf, M, nx, nr, dr, flags, 2, g=g, m_a=m_a, src=src)
-    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 2, 8, 32, nth=256, fused=0)
+    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 2, 8, 32, nth=256, fused=fused)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 1e-13, (name, e)
 
 
-@pytest.mark.parametrize("fused", [1, 0, 2])
+@pytest.mark.parametrize("fused", [1, 0, 2, 3])
 @pytest.mark.parametrize("M", [2, 3])
 def test_emulated_kernel_fp32_scaled(M, fused):
     nx, nr = 24, 12
