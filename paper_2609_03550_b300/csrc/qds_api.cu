@@ -130,6 +130,9 @@ struct qds_handle {
     // flat stage passes: (instance, first point, points, 0), interior first
     int4 *d_flat = nullptr;
     int nflat = 0, nflat_interior = 0;
+    // the same per mode: (instance, first point, points, mode)
+    int4 *d_flatk = nullptr;
+    int nflatk = 0, nflatk_interior = 0;
   };
   std::vector<Group> groups;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
@@ -233,6 +236,17 @@ cudaError_t launch_flat(qds_handle *h, const qds_handle::Group &G, cudaStream_t 
   return cudaGetLastError();
 }
 
+template <class R, int M, int ST>
+cudaError_t launch_flatk(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  if (G.nflatk_interior > 0)
+    flatk_pass_kernel<R, M, ST, true><<<G.nflatk_interior, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_flatk,
+                                                                              h->d_ctrl);
+  if (G.nflatk > G.nflatk_interior)
+    flatk_pass_kernel<R, M, ST, false><<<G.nflatk - G.nflatk_interior, kThreads, 0, st>>>(
+        (const Inst<R> *)h->d_inst, G.d_flatk + G.nflatk_interior, h->d_ctrl);
+  return cudaGetLastError();
+}
+
 template <class R, int M, int PASS>
 cudaError_t launch_warp_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
   const int q = PASS - 1;
@@ -271,6 +285,15 @@ template <class R, int M>
 cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl, int mode, cudaStream_t st) {
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
   cudaError_t e;
+  if (mode == QDS_STEP_FLAT_MODES) {
+    if ((e = launch_flatk<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
+    if (ax && (e = launch_flat<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
+    if ((e = launch_flatk<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_flat<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_flatk<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
+    if (mw && (e = launch_flatk<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
   if (mode == QDS_STEP_FLAT) {
     if ((e = launch_flat<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
     if (ax && (e = launch_flat<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
@@ -482,6 +505,19 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
         P.nflat = (int)fi.size();
         CU(cudaMalloc(&P.d_flat, sizeof(int4) * fi.size()));
         CU(cudaMemcpy(P.d_flat, fi.data(), sizeof(int4) * fi.size(), cudaMemcpyHostToDevice));
+        // per mode: every block of the point list once per mode
+        std::vector<int4> ki, ke;
+        for (int k = 0; k < M; k++)
+          for (int b = 0; b < P.nflat; b++) {
+            int4 v = fi[b];
+            v.w = k;
+            (b < P.nflat_interior ? ki : ke).push_back(v);
+          }
+        P.nflatk_interior = (int)ki.size();
+        ki.insert(ki.end(), ke.begin(), ke.end());
+        P.nflatk = (int)ki.size();
+        CU(cudaMalloc(&P.d_flatk, sizeof(int4) * ki.size()));
+        CU(cudaMemcpy(P.d_flatk, ki.data(), sizeof(int4) * ki.size(), cudaMemcpyHostToDevice));
       }
       h->pgroups.push_back(P);
     }
@@ -493,7 +529,7 @@ void destroy(qds_handle *h) {
   if (!h) return;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &G : h->groups) cudaFree(G.d_tiles);
-  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); }
+  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); cudaFree(G.d_flatk); }
   cudaFree(h->d_inst);
   cudaFree(h->d_ctrl);
   cudaFree(h->d_partial);
@@ -564,7 +600,7 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   for (auto &G : h->groups) cudaFree(G.d_tiles);
   cudaFree(h->d_inst); cudaFree(h->d_ctrl); cudaFree(h->d_partial); cudaFree(h->d_diag);
   cudaFree(h->d_partial_all); cudaFree(h->d_scal);
-  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); }
+  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); cudaFree(G.d_flatk); }
   h->groups = nh->groups; h->pgroups = nh->pgroups; h->d_inst = nh->d_inst; h->d_ctrl = nh->d_ctrl;
   h->d_partial_all = nh->d_partial_all; h->d_scal = nh->d_scal;
   h->d_partial = nh->d_partial; h->d_diag = nh->d_diag; h->h_inst = nh->h_inst;
@@ -587,7 +623,7 @@ int qds_step_launches(const qds_handle *h) {
     const int stage = (G.n_interior > 0) + (G.ntiles > G.n_interior);
     const int w1 = (G.nw_interior[0] > 0) + (G.nw[0] > G.nw_interior[0]);
     const int w2 = (G.nw_interior[1] > 0) + (G.nw[1] > G.nw_interior[1]);
-    if (mode == QDS_STEP_FLAT) {
+    if (mode == QDS_STEP_FLAT || mode == QDS_STEP_FLAT_MODES) {
       const int f = (G.nflat_interior > 0) + (G.nflat > G.nflat_interior);
       n += f * (2 + (ax ? 1 : 0) + (ar ? 2 : 0) + (mw ? 1 : 0));
       continue;
@@ -605,7 +641,7 @@ int qds_set_fused(qds_handle *h, int fused) { return qds_set_step_mode(h, fused 
 
 int qds_set_step_mode(qds_handle *h, int mode) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
-  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_FLAT) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
+  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_FLAT_MODES) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
   h->mode = mode;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();

@@ -127,7 +127,9 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
   }
   // flat stage passes (fused == 3): blocks of 256 consecutive points in
   // (x, r) order, each point a 1 x 1 tile
-  for (int n = 0; n < nsteps && fused == 3; n++) {
+  // (fused == 4: the same, one (point, mode) per thread in the
+  // mode-independent passes)
+  for (int n = 0; n < nsteps && (fused == 3 || fused == 4); n++) {
     const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
     const bool per_ = (flags & F_X_PERIODIC) != 0;
     const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_CURRENT, ST_SHIFT1, ST_ZERO};
@@ -135,6 +137,8 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
       if (st == ST_SOURCE && !ax) continue;
       if ((st == ST_CURRENT || st == ST_SHIFT1) && !ar) continue;
       if (st == ST_ZERO && !mw) continue;
+      const bool per_mode = fused == 4 && st != ST_SOURCE && st != ST_CURRENT;
+      for (int kk = 0; kk < (per_mode ? M : 1); kk++)
       for (int q0 = 0; q0 < nx * nr; q0 += 256) {
         const int cnt = std::min(256, nx * nr - q0);
         const int w0 = q0 / nr, w1 = (q0 + cnt - 1) / nr;
@@ -142,6 +146,7 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
         for (int q = q0; q < q0 + cnt; q++) {
           Tile<R, M, false, false> t = pass_tile_at(n, q / nr, q % nr);
           t.g.TX = 1; t.g.TR = 1;
+          if (per_mode) { t.k_lo = kk; t.k_hi = kk + 1; }
           if (inner) {
             Tile<R, M, false, true> tf;
             std::memcpy((void *)&tf, (const void *)&t, sizeof t);

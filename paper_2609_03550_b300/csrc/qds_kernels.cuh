@@ -119,6 +119,28 @@ __global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 3
   run_stage<R, M, false, FAST>(t, ST, 0, 1);
 }
 
+// Mode-independent stage pass (leapfrog, shift, regenerated shift, window
+// zeroing) over a flat range of points of one mode: block td covers points
+// td.y .. td.y + td.z - 1 of mode td.w of instance td.x, one (point, mode)
+// per thread.
+template <class R, int M, int ST, bool FAST>
+__global__ void __launch_bounds__(256, 4)
+    flatk_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
+                      const Ctrl *__restrict__ ctrl) {
+  const int4 td = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= td.z) return;
+  const Inst<R> &I = insts[td.x];
+  const int q = td.y + (int)threadIdx.x;
+  const int w = q / I.nr, j = q - w * I.nr;
+  Geo g{};
+  g.TX = 1;
+  g.TR = 1;
+  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl->step, g);
+  t.k_lo = td.w;
+  t.k_hi = td.w + 1;
+  run_stage<R, M, false, FAST>(t, ST, 0, 1);
+}
+
 // Warp-column passes (P1: leapfrog + Gamma_a; P2: shift + phi + j_a +
 // regenerated leapfrog).  Block = 8 warps = 8 columns x0..x0+7; lane l of a
 // warp holds row td.z + l; P2 outputs rows [td.w, td.w + 30).

@@ -63,6 +63,9 @@ struct Tile {
   const C<R> *jx, *jr, *jt, *sext;
   R gs, gj, ma2;
   uint32_t flags;
+  // modes k_lo .. k_hi-1 of the mode-independent stages (leapfrog, shift,
+  // window zeroing); a pass over single modes narrows the range
+  int k_lo = 0, k_hi = M;
   QDS_HD void bind(const Inst<R> &d, const Inst<R> *dev) {
     I = dev;
     jx = d.jx; jr = d.jr; jt = d.jt; sext = d.sext;
@@ -916,9 +919,9 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
       const int j = t.r0 + q;
       if (j >= t.nr) continue;
       for (int f = 0; f < NFIELD; f++)
-        for (int k = 0; k < M; k++) t.n[t.gidx(f, k, 0, j)] = zero<R>();
+        for (int k = t.k_lo; k < t.k_hi; k++) t.n[t.gidx(f, k, 0, j)] = zero<R>();
       if (j == t.J)
-        for (int k = 0; k < M; k++) t.n[(size_t)NFIELD * t.P + (size_t)k * t.nx + t.slot(0)] = zero<R>();
+        for (int k = t.k_lo; k < t.k_hi; k++) t.n[(size_t)NFIELD * t.P + (size_t)k * t.nx + t.slot(0)] = zero<R>();
     }
     return;
   }
@@ -932,7 +935,7 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
       t.set_point(w);
       const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
-      for (int k = 0; k < M; k++) {
+      for (int k = t.k_lo; k < t.k_hi; k++) {
         C<R> ex = zero<R>(), bx = zero<R>();
         if (live) {
           C<R> jtf = zero<R>();
@@ -966,7 +969,7 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
       const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
       const bool own = t.owned(lx, lr);
 #pragma unroll 1
-      for (int k = 0; k < M; k++) {
+      for (int k = t.k_lo; k < t.k_hi; k++) {
         C<R> tp = zero<R>(), tm = zero<R>(), up = zero<R>(), um = zero<R>();
         C<R> ap = zero<R>(), am = zero<R>();
         if (live) {
@@ -1083,7 +1086,7 @@ QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
       const int c = t.x0 + lx, j = t.r0 + lr;
       t.set_point(c);
 #pragma unroll 1
-      for (int k = 0; k < M; k++) {
+      for (int k = t.k_lo; k < t.k_hi; k++) {
         C<R> tp, tm, up, um;
         if (j < t.J || t.closed) tr_interior(t, fs, 9, k, lx, lr, tp, tm);
         else {

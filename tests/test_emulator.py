@@ -38,10 +38,11 @@ def run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, nsteps, TX, TR, nth=64, fuse
 
 
 # fused: 1 = fused tile kernel, 0 = warp-column passes, 2 = one pass per
-# stage over 8 x 32 tiles, 3 = the stage passes over flat point ranges
+# stage over 8 x 32 tiles, 3 = the stage passes over flat point ranges,
+# 4 = as 3 with one (point, mode) per thread in the mode-independent passes
 @pytest.mark.parametrize("M,flags", parity_cases())
 @pytest.mark.parametrize("tile,fused", [((8, 32), 1), ((5, 3), 1), ((8, 32), 0), ((3, 4), 0), ((8, 32), 2),
-                                        ((3, 4), 2), ((8, 32), 3)])
+                                        ((3, 4), 2), ((8, 32), 3), ((8, 32), 4)])
 def test_emulated_kernel_matches_oracle_fp64(M, flags, tile, fused):
     nx, nr = 21, 11
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
@@ -53,7 +54,7 @@ def test_emulated_kernel_matches_oracle_fp64(M, flags, tile, fused):
         assert e < 1e-13, (name, e)
 
 
-@pytest.mark.parametrize("fused", [0, 3])
+@pytest.mark.parametrize("fused", [0, 3, 4])
 @pytest.mark.parametrize("M,flags", [c for c in parity_cases() if c[1] & 2])
 def test_warp_passes_span_several_row_tiles(M, flags, fused):
     """nr = 70: P1 warps at rows 0, 31, 62 and P2 warps based at 0, 29, 59
@@ -69,7 +70,7 @@ def test_warp_passes_span_several_row_tiles(M, flags, fused):
         assert e < 1e-13, (name, e)
 
 
-@pytest.mark.parametrize("fused", [1, 0, 2, 3])
+@pytest.mark.parametrize("fused", [1, 0, 2, 3, 4])
 @pytest.mark.parametrize("M", [2, 3])
 def test_emulated_kernel_fp32_scaled(M, fused):
     nx, nr = 24, 12
