@@ -280,20 +280,22 @@ class DeviceBunchSources:
         x = (torch.arange(wl.nx, dtype=torch.float64, device=device) + 0.5)[:, None]
         r = (torch.arange(wl.nr, dtype=torch.float64, device=device) * wl.dr)[None, :]
         self.bunch = (b["rho"] * torch.exp(-((x - b["x0"]) ** 2) / (2 * b["sx"] ** 2))
-                      * torch.exp(-(r ** 2) / (2 * b["sr"] ** 2))).to(dtype)
+                      * torch.exp(-(r ** 2) / (2 * b["sr"] ** 2)))[None].expand(wl.M, -1, -1)
         self.buf = [torch.zeros((wl.M, wl.nx, wl.nr), dtype=dtype, device=device) for _ in range(3)]
         self.gen = torch.Generator(device=device)
-        rdt = torch.float32 if dtype == torch.complex64 else torch.float64
-        self.noise = torch.empty((3, 2, wl.M, wl.nx, wl.nr), dtype=rdt, device=device)
+        # drawn in float64 whatever the working precision, so that an FP32
+        # run sees the FP64 run's values rounded
+        self.noise = torch.empty((3, 2, wl.M, wl.nx, wl.nr), dtype=torch.float64, device=device)
+        self.bunch64 = self.bunch.to(torch.complex128)
 
     def __call__(self, step):
+        torch = self.torch
         self.gen.manual_seed(self.seed * 1_000_003 + int(step))
         self.noise.uniform_(-1.0, 1.0, generator=self.gen)
         self.noise[:, 1, 0] = 0.0
         for c in range(3):
-            v = self.buf[c].view(self.torch.float32 if self.dtype == self.torch.complex64 else self.torch.float64)
-            v = v.view(self.M, self.nx, self.nr, 2)
-            v[..., 0] = self.amp * self.noise[c, 0]
-            v[..., 1] = self.amp * self.noise[c, 1]
-        self.buf[0][0] += self.bunch
+            z = torch.complex(self.amp * self.noise[c, 0], self.amp * self.noise[c, 1])
+            if c == 0:
+                z[0] += self.bunch64[0]
+            self.buf[c].copy_(z)
         return tuple(self.buf)

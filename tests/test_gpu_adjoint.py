@@ -253,3 +253,80 @@ def test_run_rejects_regenerated_cotangent():
     n = 2 * 32 * 8
     with pytest.raises(Q.QDSError, match="regenerated"):
         out[9 * n:10 * n].real.sum().backward()
+
+
+# ---------------------------------------------------------------------------
+# the gradient workload itself (4096 x 128, modes 0..2, bunch + noise)
+
+
+def _gradient_case(steps):
+    import math
+    from paper_2609_03550_b300 import adjoint as A
+    Q = _Q()
+    wl = I.adjoint_run(steps=steps)
+    ex = wl.extra
+    base = wl.initial_state(device=DEV)
+
+    def params(prec):
+        return Q.Params(wl.nx, wl.nr, wl.M, wl.dr, g=wl.g, m_a=wl.m_a, flags=Q.AXION | Q.AREM | Q.MOVING_WINDOW | prec)
+
+    def state0(p, prof, om):
+        return A.laser2_state(base, p, prof, om, ex["x0"], ex["fwhm"])
+
+    def gradient(prec):
+        p = params(prec)
+        src = I.DeviceBunchSources(wl, DEV, torch.complex64 if prec else torch.complex128)
+        spec = A.RunSpec(p, steps, every=max(1, int(round(math.sqrt(steps)))), sources=src, device=DEV)
+        prof = torch.tensor(ex["profile2"], dtype=torch.complex128, device=DEV, requires_grad=True)
+        om = torch.tensor(ex["omega2"], dtype=torch.float64, device=DEV, requires_grad=True)
+        g = torch.tensor(wl.g, dtype=torch.float64, device=DEV, requires_grad=True)
+        L = A.axion_energy(A.run_qds(state0(p, prof, om), g, spec), p, *ex["window"])
+        L.backward()
+        return float(L.detach()), prof.grad.cpu().numpy(), float(om.grad), float(g.grad)
+
+    def loss64(prof, om, g):
+        """Forward only, FP64."""
+        p = params(0)
+        p.g = g
+        src = I.DeviceBunchSources(wl, DEV, torch.complex128)
+        s = Q.QDSSolver(p, device=DEV)
+        with torch.no_grad():
+            s.set_state(state0(p, torch.as_tensor(prof, device=DEV), torch.tensor(om, dtype=torch.float64, device=DEV)))
+        for n in range(steps):
+            jx, jr, jt = src(n)
+            s.step(1, jx=jx, jr=jr, jth=jt)
+        return float(A.axion_energy(s.get_state(), p, *ex["window"]))
+
+    return wl, gradient, loss64
+
+
+def test_gradient_workload_fp64_and_fp32_against_fp64_central_differences():
+    """The gradient workload at full grid size (steps from QDS_FD_STEPS,
+    default 1000; 8000 is the benchmark's length): the FP64 and FP32
+    gradients with respect to the laser-2 profile (a random complex
+    direction), omega2 and g against FP64 central differences (step 1e-4
+    relative) of the same loss on the GPU's FP64 path, itself pinned to the
+    oracle at 1e-12 on reduced sizes."""
+    import os
+    steps = int(os.environ.get("QDS_FD_STEPS", "1000"))
+    wl, gradient, loss64 = _gradient_case(steps)
+    ex = wl.extra
+    L64, gp64, go64, gg64 = gradient(0)
+    L32, gp32, go32, gg32 = gradient(32)
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal(wl.nr) + 1j * rng.standard_normal(wl.nr)
+    d *= np.linalg.norm(ex["profile2"]) / np.linalg.norm(d)
+    h = 1e-4
+    fd_p = (loss64(ex["profile2"] + h * d, ex["omega2"], wl.g) - loss64(ex["profile2"] - h * d, ex["omega2"], wl.g)) / (2 * h)
+    ho = h * ex["omega2"]
+    fd_o = (loss64(ex["profile2"], ex["omega2"] + ho, wl.g) - loss64(ex["profile2"], ex["omega2"] - ho, wl.g)) / (2 * ho)
+    hg = h * wl.g
+    fd_g = (loss64(ex["profile2"], ex["omega2"], wl.g + hg) - loss64(ex["profile2"], ex["omega2"], wl.g - hg)) / (2 * hg)
+    rows = [("profile", rdot(gp64, d), rdot(gp32, d), fd_p), ("omega2", go64, go32, fd_o), ("g", gg64, gg32, fd_g)]
+    for name, a64, a32, fd in rows:
+        print(f"steps {steps} {name}: fd {fd!r} adjoint fp64 {a64!r} ({abs(a64 - fd) / abs(fd):.2e}) "
+              f"fp32 {a32!r} ({abs(a32 - fd) / abs(fd):.2e})")
+    print(f"L fp64 {L64!r} fp32 {L32!r} ({abs(L32 - L64) / L64:.2e})")
+    for name, a64, a32, fd in rows:
+        assert abs(a64 - fd) < 1e-5 * abs(fd), (name, a64, fd)
+        assert abs(a32 - fd) < 1e-4 * abs(fd), (name, a32, fd)
