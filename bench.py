@@ -250,7 +250,7 @@ def run_qds(args):
     stream = torch.cuda.current_stream(device)
 
     # ---------------- FP32 batched ----------------
-    s = build_solver(wls, flags | Q.FP32, device, autotune=True)
+    s = build_solver(wls, flags | Q.FP32, device, autotune=not args.no_autotune)
     tile = s.tile()
     tile["step_mode"] = s.step_mode_name()
     launches_per_step = s.step_launches()
@@ -354,6 +354,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--instances", type=int, default=512, help="first N instances (profiling runs only)")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default step mode (profiling runs)")
     ap.add_argument("--adjoint-steps", type=int, default=8000)
     ap.add_argument("--adjoint-every", type=int, default=90)
     args = ap.parse_args()
