@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 3
 // point per thread, so no lane idles on rows beyond nr.  Each thread views
 // its point as a 1 x 1 tile.
 template <class R, int M, int ST, bool FAST>
-__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 3 : 6)
+__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? (M <= 3 ? 4 : 3) : 6)
     flat_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
                      const Ctrl *__restrict__ ctrl) {
   const int4 td = tiles[blockIdx.x];
