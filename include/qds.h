@@ -148,7 +148,10 @@ int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
  *                       an instance (x, r order) instead of 8 x 32 tiles, so
  *                       that no thread idles on rows beyond nr;
  *   QDS_STEP_FLAT_MODES as QDS_STEP_FLAT, with one (point, mode) per thread
- *                       in the mode-independent passes (leapfrog, shifts).
+ *                       in the mode-independent passes (leapfrog, shifts);
+ *   QDS_STEP_QUEUE      as QDS_STEP_FLAT, each pass one persistent launch of
+ *                       (SMs x resident CTAs) blocks that take the point
+ *                       blocks of every instance from a work counter.
  * qds_set_fused(h, 1) selects QDS_STEP_FUSED and (h, 0) QDS_STEP_DEFAULT. */
 #define QDS_STEP_DEFAULT 0
 #define QDS_STEP_FUSED 1
@@ -157,6 +160,7 @@ int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
 #define QDS_STEP_WARP_LEAP 4
 #define QDS_STEP_FLAT 5
 #define QDS_STEP_FLAT_MODES 6
+#define QDS_STEP_QUEUE 7
 int qds_set_step_mode(qds_handle *h, int mode);
 /* Kernel launches of one step in the current mode (0 for a NULL handle). */
 int qds_step_launches(const qds_handle *h);

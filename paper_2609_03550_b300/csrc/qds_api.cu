@@ -133,7 +133,11 @@ struct qds_handle {
     // the same per mode: (instance, first point, points, mode)
     int4 *d_flatk = nullptr;
     int nflatk = 0, nflatk_interior = 0;
+    int q_base = 0;  // first of this group's work counters (interior, edge per stage)
   };
+  int *d_queue = nullptr;  // work counters of the persistent passes
+  int n_queue = 0;
+  int n_sm = 0;
   std::vector<Group> groups;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
   int mode = QDS_STEP_DEFAULT;  // step implementation (qds_set_step_mode)
@@ -236,6 +240,28 @@ cudaError_t launch_flat(qds_handle *h, const qds_handle::Group &G, cudaStream_t 
   return cudaGetLastError();
 }
 
+template <class R, int M, int ST, bool FAST>
+int queue_grid(qds_handle *h, int nblocks) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_pass_kernel<R, M, ST, FAST>, kThreads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return std::max(1, std::min(nblocks, per_sm * h->n_sm));
+}
+
+template <class R, int M, int ST>
+cudaError_t launch_queue(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  int *c = h->d_queue + G.q_base + 2 * ST;
+  const int ni = G.nflat_interior, ne = G.nflat - G.nflat_interior;
+  if (ni > 0)
+    queue_pass_kernel<R, M, ST, true><<<queue_grid<R, M, ST, true>(h, ni), kThreads, 0, st>>>(
+        (const Inst<R> *)h->d_inst, G.d_flat, ni, c, h->d_ctrl);
+  if (ne > 0)
+    queue_pass_kernel<R, M, ST, false><<<queue_grid<R, M, ST, false>(h, ne), kThreads, 0, st>>>(
+        (const Inst<R> *)h->d_inst, G.d_flat + ni, ne, c + 1, h->d_ctrl);
+  return cudaGetLastError();
+}
+
 template <class R, int M, int ST>
 cudaError_t launch_flatk(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
   if (G.nflatk_interior > 0)
@@ -294,6 +320,15 @@ cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl
     if (mw && (e = launch_flatk<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
     return cudaSuccess;
   }
+  if (mode == QDS_STEP_QUEUE) {
+    if ((e = launch_queue<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
+    if (ax && (e = launch_queue<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
+    if ((e = launch_queue<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_queue<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_queue<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
+    if (mw && (e = launch_queue<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
   if (mode == QDS_STEP_FLAT) {
     if ((e = launch_flat<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
     if (ax && (e = launch_flat<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
@@ -325,6 +360,7 @@ template <class R>
 cudaError_t launch_step(qds_handle *h, cudaStream_t st) {
   const int mode = h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode;
   if (mode != QDS_STEP_FUSED) {
+    if (mode == QDS_STEP_QUEUE) zero_counters_kernel<<<1, 256, 0, st>>>(h->d_queue, h->n_queue);
     for (const auto &G : h->pgroups) {
       uint32_t fl = 0;
       for (int i = 0; i < h->n_inst; i++)
@@ -519,8 +555,17 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
         CU(cudaMalloc(&P.d_flatk, sizeof(int4) * ki.size()));
         CU(cudaMemcpy(P.d_flatk, ki.data(), sizeof(int4) * ki.size(), cudaMemcpyHostToDevice));
       }
+      P.q_base = 2 * (N_STAGE + 1) * (int)h->pgroups.size();  // stages 0 .. ST_ZERO
       h->pgroups.push_back(P);
     }
+  }
+  h->n_queue = 2 * (N_STAGE + 1) * (int)h->pgroups.size();
+  CU(cudaMalloc(&h->d_queue, sizeof(int) * std::max(1, h->n_queue)));
+  CU(cudaMemset(h->d_queue, 0, sizeof(int) * std::max(1, h->n_queue)));
+  {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
   }
   return upload_inst(h, 0);
 }
@@ -530,6 +575,7 @@ void destroy(qds_handle *h) {
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   for (auto &G : h->groups) cudaFree(G.d_tiles);
   for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); cudaFree(G.d_flatk); }
+  cudaFree(h->d_queue);
   cudaFree(h->d_inst);
   cudaFree(h->d_ctrl);
   cudaFree(h->d_partial);
@@ -604,6 +650,9 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   h->groups = nh->groups; h->pgroups = nh->pgroups; h->d_inst = nh->d_inst; h->d_ctrl = nh->d_ctrl;
   h->d_partial_all = nh->d_partial_all; h->d_scal = nh->d_scal;
   h->d_partial = nh->d_partial; h->d_diag = nh->d_diag; h->h_inst = nh->h_inst;
+  cudaFree(h->d_queue);
+  h->d_queue = nh->d_queue; h->n_queue = nh->n_queue; h->n_sm = nh->n_sm;
+  nh->d_queue = nullptr;
   nh->groups.clear(); nh->pgroups.clear(); nh->d_inst = nullptr; nh->d_ctrl = nullptr; nh->d_partial = nullptr;
   nh->d_diag = nullptr; nh->d_partial_all = nullptr; nh->d_scal = nullptr;
   delete nh;
@@ -614,7 +663,7 @@ int qds_step_launches(const qds_handle *h) {
   if (!h) return 0;
   const int mode = h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode;
   if (mode == QDS_STEP_FUSED) return (int)h->groups.size() + 1;
-  int n = 1;  // step counter
+  int n = mode == QDS_STEP_QUEUE ? 2 : 1;  // step counter (+ work counters)
   for (const auto &G : h->pgroups) {
     uint32_t fl = 0;
     for (int i = 0; i < h->n_inst; i++)
@@ -623,7 +672,7 @@ int qds_step_launches(const qds_handle *h) {
     const int stage = (G.n_interior > 0) + (G.ntiles > G.n_interior);
     const int w1 = (G.nw_interior[0] > 0) + (G.nw[0] > G.nw_interior[0]);
     const int w2 = (G.nw_interior[1] > 0) + (G.nw[1] > G.nw_interior[1]);
-    if (mode == QDS_STEP_FLAT || mode == QDS_STEP_FLAT_MODES) {
+    if (mode == QDS_STEP_FLAT || mode == QDS_STEP_FLAT_MODES || mode == QDS_STEP_QUEUE) {
       const int f = (G.nflat_interior > 0) + (G.nflat > G.nflat_interior);
       n += f * (2 + (ax ? 1 : 0) + (ar ? 2 : 0) + (mw ? 1 : 0));
       continue;
@@ -641,7 +690,7 @@ int qds_set_fused(qds_handle *h, int fused) { return qds_set_step_mode(h, fused 
 
 int qds_set_step_mode(qds_handle *h, int mode) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
-  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_FLAT_MODES) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
+  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_QUEUE) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
   h->mode = mode;
   for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();

@@ -104,10 +104,7 @@ __global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 3
 // point per thread, so no lane idles on rows beyond nr.  Each thread views
 // its point as a 1 x 1 tile.
 template <class R, int M, int ST, bool FAST>
-__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? (M <= 3 ? 4 : 3) : 6)
-    flat_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
-                     const Ctrl *__restrict__ ctrl) {
-  const int4 td = tiles[blockIdx.x];
+__device__ __forceinline__ void flat_point(const Inst<R> *__restrict__ insts, int4 td, const Ctrl *__restrict__ ctrl) {
   if ((int)threadIdx.x >= td.z) return;
   const Inst<R> &I = insts[td.x];
   const int q = td.y + (int)threadIdx.x;
@@ -117,6 +114,40 @@ __global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? (
   g.TR = 1;
   Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl->step, g);
   run_stage<R, M, false, FAST>(t, ST, 0, 1);
+}
+
+template <int M, int ST>
+constexpr int flat_ctas_per_sm() {
+  return (ST == ST_SOURCE || ST == ST_CURRENT) ? (M <= 3 ? 4 : 3) : 6;
+}
+
+template <class R, int M, int ST, bool FAST>
+__global__ void __launch_bounds__(256, flat_ctas_per_sm<M, ST>())
+    flat_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
+                     const Ctrl *__restrict__ ctrl) {
+  flat_point<R, M, ST, FAST>(insts, tiles[blockIdx.x], ctrl);
+}
+
+// Persistent form of the same pass: a grid of (SMs x resident CTAs) blocks
+// takes the blocks of the point list from a work counter (zeroed at the
+// start of each step) until the list is exhausted.
+template <class R, int M, int ST, bool FAST>
+__global__ void __launch_bounds__(256, flat_ctas_per_sm<M, ST>())
+    queue_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles, int ntiles,
+                      int *__restrict__ counter, const Ctrl *__restrict__ ctrl) {
+  __shared__ int next;
+  for (;;) {
+    __syncthreads();  // every thread has read the previous value of next
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int b = next;
+    if (b >= ntiles) return;
+    flat_point<R, M, ST, FAST>(insts, tiles[b], ctrl);
+  }
+}
+
+static __global__ void zero_counters_kernel(int *c, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) c[i] = 0;
 }
 
 // Mode-independent stage pass (leapfrog, shift, regenerated shift, window

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqds.so")
 
 AXION, AREM, MOVING_WINDOW, X_PERIODIC, R_CLOSED, FP32, SCALE_G = 1, 2, 4, 8, 16, 32, 64
-STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP, STEP_WARP_LEAP, STEP_FLAT, STEP_FLAT_MODES = 0, 1, 2, 3, 4, 5, 6
+STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP, STEP_WARP_LEAP, STEP_FLAT, STEP_FLAT_MODES, STEP_QUEUE = range(8)
 FIELDS = ("Trp", "Trm", "Ttp", "Ttm", "Ex", "Bx", "phi", "Tap", "Tam",
           "Trp1", "Trm1", "Ttp1", "Ttm1", "Ex1", "Bx1")
 N_FIELDS = 15
@@ -236,7 +236,7 @@ class QDSSolver:
         """Time the pass-mode step implementations on this batch and keep
         the fastest (the fused tile kernel is far slower and is not tried).
         The trial steps advance the state: call before set_state."""
-        modes = modes or (STEP_FLAT, STEP_FLAT_MODES, STEP_STAGES, STEP_WARP_LEAP, STEP_WARP)
+        modes = modes or (STEP_FLAT, STEP_QUEUE, STEP_FLAT_MODES, STEP_STAGES, STEP_WARP_LEAP, STEP_WARP)
         s = stream if stream is not None else torch.cuda.current_stream()
         best, best_t = None, None
         self.timings = {}
@@ -260,7 +260,8 @@ class QDSSolver:
         names = {STEP_DEFAULT: "default", STEP_FUSED: "fused", STEP_STAGES: "stage passes",
                  STEP_WARP: "warp-column passes", STEP_WARP_LEAP: "warp-column leapfrog + stage passes",
                  STEP_FLAT: "stage passes over flat point ranges",
-                 STEP_FLAT_MODES: "flat stage passes, one (point, mode) per thread where modes decouple"}
+                 STEP_FLAT_MODES: "flat stage passes, one (point, mode) per thread where modes decouple",
+                 STEP_QUEUE: "flat stage passes as persistent work-queue launches"}
         return names[getattr(self, "_mode", STEP_DEFAULT)]
 
     def step_launches(self) -> int:
@@ -268,7 +269,8 @@ class QDSSolver:
         return int(lib().qds_step_launches(self.h))
 
     def set_step_mode(self, mode: int):
-        """STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP, STEP_WARP_LEAP, STEP_FLAT or STEP_FLAT_MODES."""
+        """STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP, STEP_WARP_LEAP, STEP_FLAT, STEP_FLAT_MODES
+        or STEP_QUEUE."""
         _check(lib().qds_set_step_mode(self.h, int(mode)))
         self._mode = int(mode)
 

@@ -17,7 +17,7 @@ from tests._helpers import (fp32_tolerance, group_errors, oracle_run, parity_cas
 DEV = "cuda:0"
 
 
-MODES = [Q.STEP_STAGES, Q.STEP_FUSED, Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_FLAT, Q.STEP_FLAT_MODES]
+MODES = [Q.STEP_STAGES, Q.STEP_FUSED, Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_FLAT, Q.STEP_FLAT_MODES, Q.STEP_QUEUE]
 
 
 def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=None, mode=Q.STEP_DEFAULT):
@@ -52,7 +52,7 @@ def test_fp64_parity_random_states(M, flags, mode):
             assert e < 1e-12, (nsteps, name, e)
 
 
-@pytest.mark.parametrize("mode", [Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_FLAT, Q.STEP_FLAT_MODES])
+@pytest.mark.parametrize("mode", [Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_FLAT, Q.STEP_FLAT_MODES, Q.STEP_QUEUE])
 @pytest.mark.parametrize("M,flags", [c for c in parity_cases() if c[1] & 2])
 def test_fp64_parity_warp_seams(M, flags, mode):
     """nr = 70 puts three warps on every column (seams at rows 31/62 for the
@@ -220,8 +220,8 @@ def test_autotune_then_parity():
     p = Q.Params(nx, nr, M, dr, g=g, flags=flags)
     s = Q.QDSSolver([p, p], device=DEV)
     best = s.autotune(steps=2)
-    assert best in (Q.STEP_STAGES, Q.STEP_FLAT, Q.STEP_FLAT_MODES, Q.STEP_WARP, Q.STEP_WARP_LEAP)
-    assert len(s.timings) == 5
+    assert best in (Q.STEP_STAGES, Q.STEP_FLAT, Q.STEP_FLAT_MODES, Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_QUEUE)
+    assert len(s.timings) == 6
     for i in range(2):
         s.set_state(torch.from_numpy(buf).to(DEV), i)
     s.step(5)
