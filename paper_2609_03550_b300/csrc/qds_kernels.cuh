@@ -118,7 +118,7 @@ __device__ __forceinline__ void flat_point(const Inst<R> *__restrict__ insts, in
 
 template <int M, int ST>
 constexpr int flat_ctas_per_sm() {
-  return (ST == ST_SOURCE || ST == ST_CURRENT) ? (M <= 3 ? 4 : 3) : 6;
+  return (ST == ST_SOURCE || ST == ST_CURRENT) ? (M <= 3 ? 4 : 3) : ST == ST_LEAP0 ? 5 : 6;
 }
 
 template <class R, int M, int ST, bool FAST>
