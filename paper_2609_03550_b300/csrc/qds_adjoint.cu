@@ -67,19 +67,27 @@ __global__ void __launch_bounds__(kThr) adjoint_kernel(Adj<R, M> a) {
   }
 }
 
+// Conversions between complex128 and the working precision over the part of
+// a state that the transpose uses: the EM and axion fields (the first
+// n_lo elements) and phi_prev (after the regenerated fields, skip elements
+// further on); n counts the elements converted.
+__device__ __forceinline__ size_t used_index(size_t q, size_t n_lo, size_t skip) { return q < n_lo ? q : q + skip; }
+
 template <class R>
-__global__ void to_work_kernel(const double2 *__restrict__ src, C<R> *dst, size_t n) {
+__global__ void to_work_kernel(const double2 *__restrict__ src, C<R> *dst, size_t n, size_t n_lo, size_t skip) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    double2 v = src[q];
-    dst[q] = mk<R>((R)v.x, (R)v.y);
+    const size_t i = used_index(q, n_lo, skip);
+    double2 v = src[i];
+    dst[i] = mk<R>((R)v.x, (R)v.y);
   }
 }
 
 template <class R>
-__global__ void from_work_kernel(const C<R> *__restrict__ src, double2 *dst, size_t n) {
+__global__ void from_work_kernel(const C<R> *__restrict__ src, double2 *dst, size_t n, size_t n_lo, size_t skip) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-    C<R> v = src[q];
-    dst[q] = make_double2((double)v.re, (double)v.im);
+    const size_t i = used_index(q, n_lo, skip);
+    C<R> v = src[i];
+    dst[i] = make_double2((double)v.re, (double)v.im);
   }
 }
 
@@ -143,15 +151,20 @@ int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *
   const C<R> *F;
   C<R> *LO;
   const int cblocks = 1184;
+  // the regenerated fields (TRP1 .. BX1) are neither read nor needed
+  const size_t P = plane_elems(M, nx, nr), n_lo = (size_t)TRP1 * P, skip = (size_t)(NFIELD - TRP1) * P;
+  const size_t n_used = E - skip;
   if (sizeof(R) == 4) {
     C<R> *Fw = reinterpret_cast<C<R> *>(b + L.off_f);
-    to_work_kernel<R><<<cblocks, kThr, 0, st>>>((const double2 *)fwd, Fw, E);
-    to_work_kernel<R><<<cblocks, kThr, 0, st>>>((const double2 *)adj, LN, E);
+    to_work_kernel<R><<<cblocks, kThr, 0, st>>>((const double2 *)fwd, Fw, n_used, n_lo, skip);
+    to_work_kernel<R><<<cblocks, kThr, 0, st>>>((const double2 *)adj, LN, n_used, n_lo, skip);
     F = Fw;
     LO = reinterpret_cast<C<R> *>(b + L.off_lo);
   } else {
-    e = cudaMemcpyAsync(LN, adj, E * sizeof(C<R>), cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint copy: ") + cudaGetErrorString(e));
+    if ((e = cudaMemcpyAsync(LN, adj, n_lo * sizeof(C<R>), cudaMemcpyDeviceToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(LN + n_lo + skip, static_cast<const C<R> *>(adj) + n_lo + skip,
+                             (E - n_lo - skip) * sizeof(C<R>), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+      return fail_ad(QDS_ERR_CUDA, std::string("adjoint copy: ") + cudaGetErrorString(e));
     F = static_cast<const C<R> *>(fwd);
     LO = static_cast<C<R> *>(adj);
   }
@@ -166,8 +179,9 @@ int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *
   }
   if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
   if (sizeof(R) == 4) {
-    from_work_kernel<R><<<cblocks, kThr, 0, st>>>(LO, (double2 *)adj, E);
-    if ((e = cudaGetLastError()) != cudaSuccess)
+    from_work_kernel<R><<<cblocks, kThr, 0, st>>>(LO, (double2 *)adj, n_used, n_lo, skip);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemsetAsync(static_cast<double2 *>(adj) + n_lo, 0, skip * sizeof(double2), st)) != cudaSuccess)
       return fail_ad(QDS_ERR_CUDA, std::string("adjoint export: ") + cudaGetErrorString(e));
   }
   return QDS_OK;
