@@ -154,9 +154,23 @@ def cpu_baseline(wls, flags, budget_s):
         used.append(w.name)
         if t_total >= budget_s:
             break
-    cores = int(os.environ.get("OMP_NUM_THREADS", len(os.sched_getaffinity(0))))
+    cores = oracle.set_threads(0)
+    # the same on one thread, over a quarter of the time budget
+    oracle.set_threads(1)
+    u1, t1 = 0, 0.0
+    for w in wls:
+        st = oracle.State(w.M, w.nx, w.nr, w.initial_state())
+        p = dict(nx=w.nx, nr=w.nr, M=w.M, h=1.0, dr=w.dr, g=w.g, m_a=w.m_a, flags=flags & 31)
+        t0 = time.perf_counter()
+        oracle.step(p, st)
+        t1 += time.perf_counter() - t0
+        u1 += w.cell_modes()
+        if t1 >= budget_s / 4:
+            break
+    oracle.set_threads(cores)
     return {"value": units / t_total, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one FP64 step of each of the first {len(used)} instances ({units} cell-modes, {t_total:.1f} s)"}
+            "sample": f"one FP64 step of each of the first {len(used)} instances ({units} cell-modes, {t_total:.1f} s)",
+            "value_1_thread": u1 / t1, "sample_1_thread": f"{u1} cell-modes, {t1:.1f} s"}
 
 
 def adjoint_bench(device, steps, every):

@@ -43,6 +43,8 @@ def lib(extended=False):
         L.ora_diagnostics.restype = ctypes.c_int
         L.ora_mode_conv.argtypes = [ctypes.c_int, dp, dp, dp]
         L.ora_mode_conv.restype = None
+        L.ora_set_threads.argtypes = [ctypes.c_int]
+        L.ora_set_threads.restype = ctypes.c_int
         _libs[extended] = L
     return _libs[extended]
 
@@ -116,3 +118,9 @@ def mode_conv(A, B):
     out = np.zeros(A.size, np.complex128)
     lib().ora_mode_conv(A.size, _ptr(A), _ptr(B), _ptr(out))
     return out
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops (n <= 0: the default); returns
+    the count in force."""
+    return int(lib().ora_set_threads(int(n)))

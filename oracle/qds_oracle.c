@@ -39,6 +39,9 @@
  */
 #define _USE_MATH_DEFINES
 #include <complex.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -127,6 +130,18 @@ static cplx mode_conv(int M, int m, const cplx *A, const cplx *B) {
 }
 
 /* exported for the quadrature pin */
+/* Threads of the OpenMP loops (for timing the oracle on 1 thread and on all
+ * cores); n <= 0 leaves the runtime's default.  Returns the count in force. */
+int ora_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 void ora_mode_conv(int M, const double *A, const double *B, double *out) {
   cplx a[8], b[8];
   for (int k = 0; k < M && k < 8; k++) {
