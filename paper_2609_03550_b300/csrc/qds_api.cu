@@ -135,6 +135,11 @@ struct qds_handle {
     int nflatk = 0, nflatk_interior = 0;
     int q_base = 0;  // first of this group's work counters (interior, edge per stage)
   };
+  // pass modes: the mode-count groups of a batch run on streams of their own
+  // between a fork and a join event (independent instances)
+  std::vector<cudaStream_t> gstream;
+  std::vector<cudaEvent_t> gjoin;
+  cudaEvent_t fork = nullptr;
   int *d_queue = nullptr;  // work counters of the persistent passes
   int n_queue = 0;
   int n_sm = 0;
@@ -361,19 +366,31 @@ cudaError_t launch_step(qds_handle *h, cudaStream_t st) {
   const int mode = h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode;
   if (mode != QDS_STEP_FUSED) {
     if (mode == QDS_STEP_QUEUE) zero_counters_kernel<<<1, 256, 0, st>>>(h->d_queue, h->n_queue);
-    for (const auto &G : h->pgroups) {
+    const bool fork = h->pgroups.size() > 1;
+    cudaError_t e = cudaSuccess;
+    if (fork && (e = cudaEventRecord(h->fork, st)) != cudaSuccess) return e;
+    for (size_t gi = 0; gi < h->pgroups.size(); gi++) {
+      const auto &G = h->pgroups[gi];
+      cudaStream_t gs = st;
+      if (fork) {
+        gs = h->gstream[gi];
+        if ((e = cudaStreamWaitEvent(gs, h->fork, 0)) != cudaSuccess) return e;
+      }
       uint32_t fl = 0;
       for (int i = 0; i < h->n_inst; i++)
         if (h->params[i].n_modes == G.M) fl |= h->params[i].flags;
-      cudaError_t e = cudaSuccess;
       switch (G.M) {
-        case 1: e = launch_passes<R, 1>(h, G, fl, mode, st); break;
-        case 2: e = launch_passes<R, 2>(h, G, fl, mode, st); break;
-        case 3: e = launch_passes<R, 3>(h, G, fl, mode, st); break;
-        case 4: e = launch_passes<R, 4>(h, G, fl, mode, st); break;
+        case 1: e = launch_passes<R, 1>(h, G, fl, mode, gs); break;
+        case 2: e = launch_passes<R, 2>(h, G, fl, mode, gs); break;
+        case 3: e = launch_passes<R, 3>(h, G, fl, mode, gs); break;
+        case 4: e = launch_passes<R, 4>(h, G, fl, mode, gs); break;
         default: e = cudaErrorInvalidValue;
       }
       if (e != cudaSuccess) return e;
+      if (fork) {
+        if ((e = cudaEventRecord(h->gjoin[gi], gs)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, h->gjoin[gi], 0)) != cudaSuccess) return e;
+      }
     }
     advance_kernel<<<1, 32, 0, st>>>(h->d_ctrl, 1);
     return cudaGetLastError();
@@ -559,6 +576,15 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
       h->pgroups.push_back(P);
     }
   }
+  CU(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+  for (size_t gi = 0; gi < h->pgroups.size(); gi++) {
+    cudaStream_t gs;
+    cudaEvent_t ev;
+    CU(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
+    h->gstream.push_back(gs);
+    CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    h->gjoin.push_back(ev);
+  }
   h->n_queue = 2 * (N_STAGE + 1) * (int)h->pgroups.size();
   CU(cudaMalloc(&h->d_queue, sizeof(int) * std::max(1, h->n_queue)));
   CU(cudaMemset(h->d_queue, 0, sizeof(int) * std::max(1, h->n_queue)));
@@ -576,6 +602,9 @@ void destroy(qds_handle *h) {
   for (auto &G : h->groups) cudaFree(G.d_tiles);
   for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); cudaFree(G.d_flatk); }
   cudaFree(h->d_queue);
+  for (auto gs : h->gstream) cudaStreamDestroy(gs);
+  for (auto ev : h->gjoin) cudaEventDestroy(ev);
+  if (h->fork) cudaEventDestroy(h->fork);
   cudaFree(h->d_inst);
   cudaFree(h->d_ctrl);
   cudaFree(h->d_partial);
@@ -653,6 +682,11 @@ int qds_set_tile(qds_handle *h, int tx, int tr) {
   cudaFree(h->d_queue);
   h->d_queue = nh->d_queue; h->n_queue = nh->n_queue; h->n_sm = nh->n_sm;
   nh->d_queue = nullptr;
+  for (auto gs : h->gstream) cudaStreamDestroy(gs);
+  for (auto ev : h->gjoin) cudaEventDestroy(ev);
+  if (h->fork) cudaEventDestroy(h->fork);
+  h->gstream = nh->gstream; h->gjoin = nh->gjoin; h->fork = nh->fork;
+  nh->gstream.clear(); nh->gjoin.clear(); nh->fork = nullptr;
   nh->groups.clear(); nh->pgroups.clear(); nh->d_inst = nullptr; nh->d_ctrl = nullptr; nh->d_partial = nullptr;
   nh->d_diag = nullptr; nh->d_partial_all = nullptr; nh->d_scal = nullptr;
   delete nh;
