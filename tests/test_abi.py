@@ -60,9 +60,19 @@ def test_state_bytes_of_valid_statements():
     dict(flags=Q.MOVING_WINDOW | Q.X_PERIODIC),
     dict(flags=Q.AREM),                   # needs the axion
     dict(flags=1 << 12),
+    dict(nx=7),                           # below the smallest window
+    dict(nx=65536, nr=1024, n_modes=4, dr=3.25),  # 2^31 state elements or more per instance
+    dict(dx=1.0, dr=2.0, m_a=1.5),        # dx m_a > 1
 ])
 def test_invalid_or_unstable_statements_are_rejected(bad):
     assert _bytes(**bad) == 0
+
+
+def test_largest_instance_below_the_element_limit_is_accepted():
+    """15 M nx nr + M nx < 2^31: with 4 modes and nx = 4096, nr = 8738 is
+    the largest grid that fits and 8739 the smallest that does not."""
+    assert _bytes(nx=4096, nr=8738, n_modes=4, dr=3.25) > 0
+    assert _bytes(nx=4096, nr=8739, n_modes=4, dr=3.25) == 0
 
 
 def test_stability_rule_matches_limits():
