@@ -108,7 +108,10 @@ int qds_set_state(qds_handle *h, const void *src_dev, void *stream);
 int qds_get_state(qds_handle *h, void *dst_dev, void *stream);
 
 /* Advance nsteps steps with constant sources (src may be NULL); calls of
- * >= 16 steps replay a captured CUDA graph.  Asynchronous on stream. */
+ * >= 16 steps replay a captured CUDA graph.  Asynchronous on stream: a batch
+ * with several mode counts runs each mode count's kernels on a stream of the
+ * handle, forked from and joined back to `stream` by events, so the call is
+ * ordered on `stream` like a single launch. */
 int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream);
 
 /* Energies into out_host[4] = {EM energy, axion energy, regenerated EM
