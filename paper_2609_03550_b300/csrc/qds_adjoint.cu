@@ -59,7 +59,9 @@ __global__ void __launch_bounds__(kThr) adjoint_kernel(Adj<R, M> a) {
   double acc = 0;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     const int w = q / a.nr, j = q - w * a.nr;
-    adj_point<R, M>(a, ST, w, j, acc);
+    Adj<R, M> ap = a;
+    ap.f.set_point(w);  // ring slots of columns w-1 .. w+2
+    adj_point<R, M>(ap, ST, w, j, acc);
   }
   if (ST == AD_UNSRC && a.dg) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -115,7 +117,7 @@ Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_
   t.P = P; t.o = F; t.n = nullptr;
   t.h = (R)p.dx; t.dr = (R)p.dr; t.ih = (R)(1.0 / p.dx); t.idr = (R)(1.0 / p.dr);
   t.sm = nullptr; t.scr = nullptr;
-  t.cw = -(1 << 28);  // no cached columns: every access takes the general path
+  t.cw = -(1 << 28);  // each point sets the column cache (adjoint_kernel)
   a.ln = LN; a.lo = LO; a.sb = SB; a.dg = dg;
   a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
   a.mw = (p.flags & QDS_MOVING_WINDOW) != 0;

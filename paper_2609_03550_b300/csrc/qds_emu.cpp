@@ -313,7 +313,7 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   t.P = P; t.o = F.data(); t.n = nullptr;
   t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
   t.sm = nullptr; t.scr = nullptr;
-  t.cw = -(1 << 28);  // no cached columns: every access takes the general path
+  t.cw = -(1 << 28);  // set per column below
   t.state_len = E; t.sm_len = 0;
   a.ln = LN.data(); a.lo = LO.data(); a.sb = SB.data(); a.dg = dg;
   a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
@@ -322,8 +322,10 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   a.gs = I.gs; a.ma2 = I.ma2;
   double acc = 0;
   for (int st = 0; st < N_ADSTAGE; st++)
-    for (int w = 0; w < nx; w++)
+    for (int w = 0; w < nx; w++) {
+      a.f.set_point(w);
       for (int j = 0; j < nr; j++) adj_point<R, M>(a, st, w, j, acc);
+    }
   if (dg) *dg += acc;
   for (size_t q = 0; q < E; q++) {
     lam_old[2 * q] = (double)LO[q].re;
