@@ -49,7 +49,7 @@ def kernel_hash():
     define them); launch code on the host does not change their counters."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2609_03550_b300", "csrc")
-    for f in ("qds_common.cuh", "qds_stages.cuh", "qds_kernels.cuh"):
+    for f in ("qds_common.cuh", "qds_stages.cuh", "qds_kernels.cuh", "qds_march.cuh"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -19,6 +19,9 @@
  * Layouts: a "complex plane set" [M][nx][nr] stores mode m, x index i and
  * radial index j at ((m*nx + i)*nr + j), each element an interleaved
  * (re, im) pair of the working precision (float for QDS_FP32, else double).
+ * Inside the library's state buffer the row stride is nr rounded up to even
+ * in FP32 (every column starts on a 16-byte boundary for the bulk copies);
+ * callers never see that layout (qds_set_state / qds_get_state convert).
  * Staggering: T_r at (x_i, r_{j+1/2}), T_theta at (x_i, r_j), E_x at
  * (x_{i+1/2}, r_j), B_x and phi at (x_{i+1/2}, r_{j+1/2}), T_a at
  * (x_i, r_{j+1/2}); r_j = j dr.  Faces i = 0..nx-2 are real (nx-1 is held
@@ -48,8 +51,8 @@ extern "C" {
 #define QDS_OK 0
 #define QDS_ERR_INVALID_ARG 1
 #define QDS_ERR_CUDA 2
-#define QDS_ERR_NONFINITE 3
-#define QDS_ERR_TIMEOUT 4
+#define QDS_ERR_NONFINITE 3   /* a NaN or Inf reached the state (step kernels, energies) */
+#define QDS_ERR_TIMEOUT 4     /* a bounded device wait (bulk copy of a step kernel) ran out */
 #define QDS_ERR_UNSUPPORTED 5
 
 /* flags */
@@ -133,46 +136,42 @@ int qds_num_instances(const qds_handle *h);
  * n_inst*4 doubles) in two launches; asynchronous on stream. */
 int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
 
-/* Step implementation (all give the same results to rounding):
- *   QDS_STEP_DEFAULT    the fastest measured of the pass modes below;
- *   QDS_STEP_FUSED      every stage of a tile in one kernel, intermediates
- *                       and their halos in shared memory;
- *   QDS_STEP_STAGES     one grid-wide pass per stage group: leapfrog, axion
- *                       source, shift + phi, axion current + regenerated
- *                       leapfrog, regenerated shift (intermediates in the new
- *                       state and in scratch planes of the caller's buffer);
- *   QDS_STEP_WARP       warp-column passes: leapfrog + source in one pass,
- *                       shift + phi + current + regenerated leapfrog in
- *                       another (radial neighbours through shared memory,
- *                       the shift of the next cell recomputed), then the
- *                       regenerated shift;
- *   QDS_STEP_WARP_LEAP  the first warp-column pass, then the stage passes;
- *   QDS_STEP_FLAT       the stage passes over flat ranges of 256 points of
- *                       an instance (x, r order) instead of 8 x 32 tiles, so
- *                       that no thread idles on rows beyond nr;
- *   QDS_STEP_FLAT_MODES as QDS_STEP_FLAT, with one (point, mode) per thread
- *                       in the mode-independent passes (leapfrog, shifts);
- *   QDS_STEP_QUEUE      as QDS_STEP_FLAT, each pass one persistent launch of
- *                       (SMs x resident CTAs) blocks that take the point
- *                       blocks of every instance from a work counter.
- * qds_set_fused(h, 1) selects QDS_STEP_FUSED and (h, 0) QDS_STEP_DEFAULT. */
+/* Step implementation (both give the same results to rounding):
+ *   QDS_STEP_DEFAULT  QDS_STEP_FLAT (the faster of the two measured on the
+ *                     batched scan);
+ *   QDS_STEP_FLAT     one grid-wide pass per stage group (leapfrog, axion
+ *                     source, shift + phi, axion current + regenerated
+ *                     leapfrog, regenerated shift, window zeroing), one
+ *                     point per thread over flat ranges of 256 points,
+ *                     intermediates in the new state and scratch planes;
+ *   QDS_STEP_MARCH    two x-marching kernels per mode count: each CTA walks
+ *                     a band of rows (all modes) along x, the old state
+ *                     arriving column by column in a shared-memory ring by
+ *                     bulk tensor copies; the first kernel advances the EM
+ *                     field and the axion and writes j_a, the second the
+ *                     axion-regenerated field.
+ * Changing the mode drops the captured graphs. */
 #define QDS_STEP_DEFAULT 0
-#define QDS_STEP_FUSED 1
-#define QDS_STEP_STAGES 2
-#define QDS_STEP_WARP 3
-#define QDS_STEP_WARP_LEAP 4
-#define QDS_STEP_FLAT 5
-#define QDS_STEP_FLAT_MODES 6
-#define QDS_STEP_QUEUE 7
+#define QDS_STEP_FLAT 1
+#define QDS_STEP_MARCH 2
 int qds_set_step_mode(qds_handle *h, int mode);
 /* Kernel launches of one step in the current mode (0 for a NULL handle). */
 int qds_step_launches(const qds_handle *h);
-int qds_set_fused(qds_handle *h, int fused);
 
-/* Tile shape of the fused step kernel (x cells, radial rows); used by the
- * autotuner.  qds_get_tile also reports the tile count and shared memory. */
-int qds_set_tile(qds_handle *h, int tx, int tr);
-int qds_get_tile(qds_handle *h, int *tx, int *tr, int *ntiles, int *smem_bytes);
+/* Work split of QDS_STEP_MARCH (the autotuner's knobs): rows = radial rows
+ * per CTA including the halo (24..256, rounded down to a multiple of 8, at
+ * most 256 / n_modes; 0 = the default that fits two CTAs per SM), cols =
+ * window columns per CTA (>= 4; 0 = 128).  qds_get_tile reports the rows of
+ * the first kernel of the first mode count, the columns, the CTAs of one
+ * step and that kernel's shared memory in bytes. */
+int qds_set_tile(qds_handle *h, int rows, int cols);
+int qds_get_tile(qds_handle *h, int *rows, int *cols, int *ntiles, int *smem_bytes);
+
+/* Device error state since the last qds_set_state: QDS_OK, QDS_ERR_TIMEOUT
+ * or QDS_ERR_NONFINITE (the step kernels flag a non-finite T_r^+ or T_a^+
+ * they store; the energy reductions flag a non-finite energy).  Synchronises
+ * stream.  qds_diagnostics returns the same codes. */
+int qds_status(qds_handle *h, void *stream);
 
 void qds_free(qds_handle *h);
 const char *qds_last_error(void);

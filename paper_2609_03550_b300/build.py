@@ -1,5 +1,5 @@
 """Build the CUDA library (libqds.so, sm_103a) and the host emulator of its
-tile stages (libqds_emu.so, CPU tests only) in the package directory."""
+step kernels (libqds_emu.so, CPU tests only) in the package directory."""
 import os
 import subprocess
 
@@ -10,7 +10,7 @@ EMU = os.path.join(HERE, "libqds_emu.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["qds_api.cu", "qds_noalloc.cu", "qds_adjoint.cu"]
-HEADERS = ["qds_common.cuh", "qds_stages.cuh", "qds_kernels.cuh", "qds_adjoint.cuh"]
+HEADERS = ["qds_common.cuh", "qds_stages.cuh", "qds_kernels.cuh", "qds_march.cuh", "qds_adjoint.cuh"]
 
 
 def _stale(target, deps):
@@ -34,7 +34,8 @@ def build_cuda(force=False, verbose=False):
 
 
 def build_emu(force=False):
-    deps = [os.path.join(CSRC, f) for f in ("qds_emu.cpp", "qds_common.cuh", "qds_stages.cuh", "qds_adjoint.cuh")]
+    deps = [os.path.join(CSRC, f) for f in ("qds_emu.cpp", "qds_common.cuh", "qds_stages.cuh", "qds_march.cuh",
+                                            "qds_adjoint.cuh")]
     if not force and not _stale(EMU, deps):
         return EMU
     cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-Wno-unknown-pragmas",

@@ -110,13 +110,13 @@ Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_
   std::memset(&a, 0, sizeof a);
   const int nx = p.nx, nr = p.nr;
   const size_t P = plane_elems(M, nx, nr);
-  Tile<R, M, false, false> &t = a.f;
+  Tile<R, M, false> &t = a.f;
   t.bind(h_inst, d_inst);
-  t.nx = nx; t.nr = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
+  t.nx = nx; t.nr = nr; t.ld = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
   t.per = false; t.closed = false; t.mw = false;
   t.P = P; t.o = F; t.n = nullptr;
   t.h = (R)p.dx; t.dr = (R)p.dr; t.ih = (R)(1.0 / p.dx); t.idr = (R)(1.0 / p.dr);
-  t.sm = nullptr; t.scr = nullptr;
+  t.scr = nullptr;
   t.cw = -(1 << 28);  // each point sets the column cache (adjoint_kernel)
   a.ln = LN; a.lo = LO; a.sb = SB; a.dg = dg;
   a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
@@ -137,7 +137,7 @@ int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *
   char *b = static_cast<char *>(work);
   Inst<R> I;
   std::memset(&I, 0, sizeof I);
-  I.nx = nx; I.nr = nr; I.M = M; I.flags = p.flags;
+  I.nx = nx; I.nr = nr; I.ld = nr; I.M = M; I.flags = p.flags;
   I.h = (R)p.dx; I.dr = (R)p.dr; I.inv_h = (R)(1.0 / p.dx); I.inv_dr = (R)(1.0 / p.dr);
   I.ma2 = (R)(p.m_a * p.m_a);
   I.gs = (R)p.g; I.gj = (R)p.g;

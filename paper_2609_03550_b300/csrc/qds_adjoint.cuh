@@ -45,7 +45,7 @@ QDS_HD void cadd(C<R> *p, C<R> v) {
 
 template <class R, int M>
 struct Adj {
-  Tile<R, M, false, false> f;  // forward state at time n (s = 0)
+  Tile<R, M, false> f;  // forward state at time n (s = 0)
   const C<R> *ln;              // adjoint of the state after the step
   C<R> *lo;                    // adjoint of the state before the step (accumulated)
   C<R> *sb;                    // scratch planes
@@ -126,7 +126,7 @@ QDS_HD void adj_point(const Adj<R, M> &a, int st, int w, int j, double &dg_acc) 
   const int J = a.J;
   const R h = a.h, dr = a.dr, idr = a.idr;
   const R ka = R(0.5) * a.ih, kb = R(0.5) * idr;  // box-scheme weights
-  const Tile<R, M, false, false> &t = a.f;
+  const Tile<R, M, false> &t = a.f;
 
   if (st == AD_UNPHI) {
     // phi^(n+1) = phi^n + (h/4) sum T_a^(n+1/2) over the cells around face w;

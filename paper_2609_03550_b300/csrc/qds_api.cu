@@ -1,21 +1,25 @@
 // qds_api.cu -- the C-ABI of the QDS field-step library (include/qds.h).
 //
 // The caller (PyTorch in the Python binding) owns all device memory of the
-// field state and the sources; a handle owns only its descriptor tables, a
-// step counter, a small diagnostics scratch and any captured CUDA graphs.
+// field state and the sources; a handle owns only its descriptor tables, the
+// tensor maps of the bulk copies, a step counter, a small diagnostics
+// scratch and any captured CUDA graphs.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
 
 #include "../../include/qds.h"
-#include "qds_kernels.cuh"
+#include "qds_march.cuh"
 
 using namespace qds;
 
@@ -35,8 +39,6 @@ int fail(int code, const std::string &msg) {
   } while (0)
 
 constexpr int kThreads = 256;
-// the step implementation behind QDS_STEP_DEFAULT
-constexpr int kDefaultMode = QDS_STEP_FLAT;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -49,7 +51,9 @@ bool is_scaled(const qds_params &p) { return (p.flags & (QDS_FP32 | QDS_SCALE_G)
 // ghost needs dr >= 1.5 dx, and a mass widens both by (1 + dx m_a)).
 int validate(const qds_params &p) {
   if (p.nx < 8 || p.nr < 4) return fail(QDS_ERR_INVALID_ARG, "nx must be >= 8 and nr >= 4");
-  if ((double)15 * p.n_modes * p.nx * p.nr + (double)p.n_modes * p.nx > 2147483647.0)
+  if (p.nx > (1 << 24) || p.nr > 32768) return fail(QDS_ERR_INVALID_ARG, "nx must be <= 2^24 and nr <= 32768");
+  const double ld = (p.flags & QDS_FP32) ? p.nr + (p.nr & 1) : p.nr;  // row stride of the working layout
+  if ((double)15 * p.n_modes * p.nx * ld + (double)p.n_modes * p.nx > 2147483647.0)
     return fail(QDS_ERR_INVALID_ARG, "one instance must hold fewer than 2^31 state elements");
   if (p.n_modes < 1 || p.n_modes > 4) return fail(QDS_ERR_INVALID_ARG, "n_modes must be 1..4");
   if (p.modes)
@@ -73,38 +77,100 @@ int validate(const qds_params &p) {
 }
 
 size_t elem_bytes(const qds_params &p) { return is_fp32(p) ? 8 : 16; }
+int row_ld(const qds_params &p) { return is_fp32(p) ? row_stride<float>(p.nr) : row_stride<double>(p.nr); }
 
-size_t half_bytes(const qds_params &p) { return align_up(state_elems(p.n_modes, p.nx, p.nr) * elem_bytes(p)); }
+size_t half_bytes(const qds_params &p) { return align_up(state_elems(p.n_modes, p.nx, row_ld(p)) * elem_bytes(p)); }
 
 // two ping-pong copies of the state, then four scratch planes (Gamma_a and
-// the three components of j_a) used by the pass-mode step
+// the three components of j_a)
 size_t instance_bytes(const qds_params &p) {
-  return 2 * half_bytes(p) + align_up(4 * plane_elems(p.n_modes, p.nx, p.nr) * elem_bytes(p));
+  return 2 * half_bytes(p) + align_up(4 * plane_elems(p.n_modes, p.nx, row_ld(p)) * elem_bytes(p));
 }
 
-Geo pick_geo(const qds_params &p, int override_tx, int override_tr) {
-  Geo g;
-  g.TX = override_tx > 0 ? override_tx : 8;
-  g.TR = override_tr > 0 ? override_tr : 32;
-  if (override_tr <= 0) {
-    size_t eb = elem_bytes(p);
-    while (g.TR > 8 && (size_t)smem_layout(g, p.n_modes, p.flags).total * eb > 200 * 1024) g.TR /= 2;
+// ---------------------------------------------------------------------------
+// x-marching launch plan
+// ---------------------------------------------------------------------------
+// Shared memory of one CTA, in bytes, for band rows RB.
+int march_smem(bool fp32, int kind, int M, int RB) {
+  return fp32 ? march_geo<float>(kind, M, RB).bytes : march_geo<double>(kind, M, RB).bytes;
+}
+
+// Default rows per CTA: the largest multiple of 8 (at most 256/M threads,
+// 128 rows in FP64 for the copy box) whose shared memory lets two CTAs share
+// an SM.
+int default_rows(bool fp32, int kind, int M) {
+  const int cap_thr = 256 / M;
+  const int cap = std::min(cap_thr, fp32 ? 256 : 128);
+  int best = 8;
+  for (int RB = 8; RB <= cap; RB += 8)
+    if (march_smem(fp32, kind, M, RB) <= 110 * 1024) best = RB;
+  return best;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map over planes [nplanes][M][nx][ld] of complex elements at base:
+// dims (row, column, mode, plane), box (RB rows, one column, all modes,
+// box_planes planes).  8-byte integer elements: one per FP32 complex, two
+// per FP64 complex.  Coordinates outside the tensor read as zero.
+int encode_map(CUtensorMap *out, void *base, bool fp32, int M, int nx, int nr, int ld, int nplanes, int RB,
+               int box_planes) {
+  auto fn = encode_fn();
+  if (!fn) return fail(QDS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t w = fp32 ? 1 : 2;  // 8-byte words per complex
+  cuuint64_t dims[4] = {w * (cuuint64_t)nr, (cuuint64_t)nx, (cuuint64_t)M, (cuuint64_t)nplanes};
+  const cuuint64_t eb = 8 * w;
+  cuuint64_t strides[3] = {eb * ld, eb * ld * nx, eb * ld * nx * M};
+  cuuint32_t box[4] = {(cuuint32_t)(w * RB), 1, (cuuint32_t)M, (cuuint32_t)box_planes};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = fn(out, CU_TENSOR_MAP_DATA_TYPE_INT64, 4, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char b[200];
+    std::snprintf(b, sizeof b, "cuTensorMapEncodeTiled failed (%d) for nx=%d nr=%d M=%d rows=%d", (int)r, nx, nr, M, RB);
+    return fail(QDS_ERR_CUDA, b);
   }
-  return g;
+  return QDS_OK;
+}
+
+// Work items of one kernel kind for one instance: bands of rows (the first
+// band starts at row 0 with no halo below) times segments of columns.
+void march_items(std::vector<MarchItem> &out, int inst, int nx, int nr, int RB, int halo, int seg) {
+  const int first = RB - halo;
+  const int tr = RB - 2 * halo;
+  for (int r0 = 0; r0 < nr;) {
+    const int r1 = std::min(nr, r0 == 0 ? first : r0 + tr);
+    const int rb0 = r0 == 0 ? 0 : r0 - halo;
+    for (int xa = 0; xa < nx; xa += seg) {
+      MarchItem it{};
+      it.inst = inst; it.r0 = r0; it.r1 = r1; it.rb0 = rb0; it.xa = xa; it.xb = std::min(nx, xa + seg);
+      out.push_back(it);
+    }
+    r0 = r1;
+  }
 }
 
 }  // namespace
 
-// Internal (not part of the C ABI): lets the other translation unit of the
+// Internal (not part of the C ABI): lets the other translation units of the
 // library report through qds_last_error().
 __attribute__((visibility("hidden"))) void qds_internal_set_error(const std::string &m) { g_err = m; }
 
 struct qds_handle {
   int n_inst = 0;
   std::vector<qds_params> params;
-  std::vector<std::vector<int32_t>> modes;
   bool fp32 = false;
-  uint32_t flags = 0;  // common flags (all instances share precision)
   char *state = nullptr;
   std::vector<size_t> inst_off;  // byte offset of each instance in the state arena
   // device tables
@@ -114,40 +180,32 @@ struct qds_handle {
   double *d_diag = nullptr;
   int diag_blocks = 0;
   double *d_partial_all = nullptr;  // [n_inst][diag_all_blocks][4]
-  double4 *d_scal = nullptr;        // per-instance diagnostic prefactors
+  Scal4 *d_scal = nullptr;        // per-instance diagnostic prefactors
   int diag_all_blocks = 0;
-  // per-M launch groups
+  MarchMaps *d_maps = nullptr;      // per instance
+  // per mode count
   struct Group {
-    int M;
-    Geo g;
-    Smem L;
-    int4 *d_tiles = nullptr;  // pass mode: interior tiles first, then edge tiles
-    int ntiles = 0;
-    int n_interior = 0;       // pass mode: tiles whose halo lies inside the window
-    // warp-column passes P1 (31 output rows per warp) and P2 (30), interior first
-    int4 *d_w[2] = {nullptr, nullptr};
-    int nw[2] = {0, 0}, nw_interior[2] = {0, 0};
+    int M = 0;
+    uint32_t flags = 0;  // union of the flags of its instances
     // flat stage passes: (instance, first point, points, 0), interior first
     int4 *d_flat = nullptr;
     int nflat = 0, nflat_interior = 0;
-    // the same per mode: (instance, first point, points, mode)
-    int4 *d_flatk = nullptr;
-    int nflatk = 0, nflatk_interior = 0;
-    int q_base = 0;  // first of this group's work counters (interior, edge per stage)
+    // x-marching: K1 and K2 work items and shared-memory plans
+    MarchItem *d_items[2] = {nullptr, nullptr};
+    int nitems[2] = {0, 0};
+    int rows[2] = {0, 0};
+    MarchGeo geo[2];
   };
-  // pass modes: the mode-count groups of a batch run on streams of their own
-  // between a fork and a join event (independent instances)
+  std::vector<Group> groups;
+  // the mode-count groups of a batch run on streams of their own between a
+  // fork and a join event (independent instances)
   std::vector<cudaStream_t> gstream;
   std::vector<cudaEvent_t> gjoin;
   cudaEvent_t fork = nullptr;
-  int *d_queue = nullptr;  // work counters of the persistent passes
-  int n_queue = 0;
-  int n_sm = 0;
-  std::vector<Group> groups;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
   int mode = QDS_STEP_DEFAULT;  // step implementation (qds_set_step_mode)
-  // pass-mode tiles (one thread per point)
-  std::vector<Group> pgroups;
+  int seg = 0;                  // march: columns per CTA (0: default)
+  int rows_override = 0;        // march: rows per CTA (0: default)
   // graph cache: key (jx, jr, jt, sext, nsteps, stream)
   std::map<std::tuple<const void *, const void *, const void *, const void *, int, void *>, cudaGraphExec_t> graphs;
   const void *cur_src[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -155,12 +213,16 @@ struct qds_handle {
 
 namespace {
 
+constexpr int kDefaultMode = QDS_STEP_FLAT;  // measured faster on the batched scan
+constexpr int kDefaultSeg = 128;
+
 template <class R>
 void fill_inst(qds_handle *h, int i, const qds_params &p, void *base) {
   Inst<R> I;
   std::memset(&I, 0, sizeof I);
   I.nx = p.nx;
   I.nr = p.nr;
+  I.ld = row_ld(p);
   I.M = p.n_modes;
   I.flags = p.flags;
   I.h = (R)p.dx;
@@ -171,7 +233,7 @@ void fill_inst(qds_handle *h, int i, const qds_params &p, void *base) {
   const bool sc = is_scaled(p);
   I.gs = sc ? (R)1 : (R)p.g;
   I.gj = sc ? (R)1 : (R)p.g;
-  size_t half = align_up(state_elems(p.n_modes, p.nx, p.nr) * sizeof(C<R>));
+  size_t half = half_bytes(p);
   I.state[0] = reinterpret_cast<C<R> *>((char *)base);
   I.state[1] = reinterpret_cast<C<R> *>((char *)base + half);
   I.scratch = reinterpret_cast<C<R> *>((char *)base + 2 * half);
@@ -201,39 +263,6 @@ int upload_inst(qds_handle *h, cudaStream_t st) {
   return QDS_OK;
 }
 
-template <class R, int M>
-cudaError_t launch_group(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
-  const size_t smem = (size_t)G.L.total * sizeof(C<R>);
-  step_kernel<R, M><<<G.ntiles, kThreads, smem, st>>>((const Inst<R> *)h->d_inst, G.d_tiles, h->d_ctrl, G.g, G.L);
-  return cudaGetLastError();
-}
-
-template <class R, int M>
-cudaError_t allow_smem(size_t bytes) {
-  return cudaFuncSetAttribute(step_kernel<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-cudaError_t allow_smem_for(bool fp32, int M, size_t bytes) {
-  if (fp32) {
-    switch (M) { case 1: return allow_smem<float, 1>(bytes); case 2: return allow_smem<float, 2>(bytes);
-                 case 3: return allow_smem<float, 3>(bytes); case 4: return allow_smem<float, 4>(bytes); }
-  } else {
-    switch (M) { case 1: return allow_smem<double, 1>(bytes); case 2: return allow_smem<double, 2>(bytes);
-                 case 3: return allow_smem<double, 3>(bytes); case 4: return allow_smem<double, 4>(bytes); }
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <class R, int M, int ST>
-cudaError_t launch_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
-  if (G.n_interior > 0)
-    pass_kernel<R, M, ST, true><<<G.n_interior, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_tiles, h->d_ctrl, G.g);
-  if (G.ntiles > G.n_interior)
-    pass_kernel<R, M, ST, false><<<G.ntiles - G.n_interior, kThreads, 0, st>>>(
-        (const Inst<R> *)h->d_inst, G.d_tiles + G.n_interior, h->d_ctrl, G.g);
-  return cudaGetLastError();
-}
-
 template <class R, int M, int ST>
 cudaError_t launch_flat(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
   if (G.nflat_interior > 0)
@@ -245,166 +274,79 @@ cudaError_t launch_flat(qds_handle *h, const qds_handle::Group &G, cudaStream_t 
   return cudaGetLastError();
 }
 
-template <class R, int M, int ST, bool FAST>
-int queue_grid(qds_handle *h, int nblocks) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, queue_pass_kernel<R, M, ST, FAST>, kThreads, 0) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  return std::max(1, std::min(nblocks, per_sm * h->n_sm));
-}
-
-template <class R, int M, int ST>
-cudaError_t launch_queue(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
-  int *c = h->d_queue + G.q_base + 2 * ST;
-  const int ni = G.nflat_interior, ne = G.nflat - G.nflat_interior;
-  if (ni > 0)
-    queue_pass_kernel<R, M, ST, true><<<queue_grid<R, M, ST, true>(h, ni), kThreads, 0, st>>>(
-        (const Inst<R> *)h->d_inst, G.d_flat, ni, c, h->d_ctrl);
-  if (ne > 0)
-    queue_pass_kernel<R, M, ST, false><<<queue_grid<R, M, ST, false>(h, ne), kThreads, 0, st>>>(
-        (const Inst<R> *)h->d_inst, G.d_flat + ni, ne, c + 1, h->d_ctrl);
-  return cudaGetLastError();
-}
-
-template <class R, int M, int ST>
-cudaError_t launch_flatk(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
-  if (G.nflatk_interior > 0)
-    flatk_pass_kernel<R, M, ST, true><<<G.nflatk_interior, kThreads, 0, st>>>((const Inst<R> *)h->d_inst, G.d_flatk,
-                                                                              h->d_ctrl);
-  if (G.nflatk > G.nflatk_interior)
-    flatk_pass_kernel<R, M, ST, false><<<G.nflatk - G.nflatk_interior, kThreads, 0, st>>>(
-        (const Inst<R> *)h->d_inst, G.d_flatk + G.nflatk_interior, h->d_ctrl);
-  return cudaGetLastError();
-}
-
-template <class R, int M, int PASS>
-cudaError_t launch_warp_pass(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
-  const int q = PASS - 1;
-  const size_t smem = warp_pass_smem<R, M>(PASS);
-  if (G.nw_interior[q] > 0)
-    warp_pass_kernel<R, M, PASS, true><<<G.nw_interior[q], kThreads, smem, st>>>((const Inst<R> *)h->d_inst, G.d_w[q],
-                                                                              h->d_ctrl, G.g);
-  if (G.nw[q] > G.nw_interior[q])
-    warp_pass_kernel<R, M, PASS, false><<<G.nw[q] - G.nw_interior[q], kThreads, smem, st>>>(
-        (const Inst<R> *)h->d_inst, G.d_w[q] + G.nw_interior[q], h->d_ctrl, G.g);
+template <class R, int M, int KIND>
+cudaError_t launch_march(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  const MarchGeo &g = G.geo[KIND];
+  march_kernel<R, M, KIND><<<G.nitems[KIND], M * g.RB, g.bytes, st>>>((const Inst<R> *)h->d_inst, h->d_maps,
+                                                                     G.d_items[KIND], h->d_ctrl, g);
   return cudaGetLastError();
 }
 
 template <class R, int M>
-cudaError_t allow_warp_smem_t() {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(warp_pass_kernel<R, M, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(1))) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(warp_pass_kernel<R, M, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(1))) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(warp_pass_kernel<R, M, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(2))) != cudaSuccess) return e;
-  return cudaFuncSetAttribute(warp_pass_kernel<R, M, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_pass_smem<R, M>(2));
+cudaError_t allow_march_smem_t(int b0, int b1) {
+  cudaError_t e = cudaFuncSetAttribute(march_kernel<R, M, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(march_kernel<R, M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b1);
 }
 
-cudaError_t allow_warp_smem(bool fp32, int M) {
+cudaError_t allow_march_smem(bool fp32, int M, int b0, int b1) {
   switch (M) {
-    case 1: return fp32 ? allow_warp_smem_t<float, 1>() : allow_warp_smem_t<double, 1>();
-    case 2: return fp32 ? allow_warp_smem_t<float, 2>() : allow_warp_smem_t<double, 2>();
-    case 3: return fp32 ? allow_warp_smem_t<float, 3>() : allow_warp_smem_t<double, 3>();
-    case 4: return fp32 ? allow_warp_smem_t<float, 4>() : allow_warp_smem_t<double, 4>();
+    case 1: return fp32 ? allow_march_smem_t<float, 1>(b0, b1) : allow_march_smem_t<double, 1>(b0, b1);
+    case 2: return fp32 ? allow_march_smem_t<float, 2>(b0, b1) : allow_march_smem_t<double, 2>(b0, b1);
+    case 3: return fp32 ? allow_march_smem_t<float, 3>(b0, b1) : allow_march_smem_t<double, 3>(b0, b1);
+    case 4: return fp32 ? allow_march_smem_t<float, 4>(b0, b1) : allow_march_smem_t<double, 4>(b0, b1);
   }
   return cudaErrorInvalidValue;
 }
 
-// One step of one mode-count group in pass mode: the two warp-column passes,
-// the regenerated shift and (moving window) the zeroing of the rear column.
+// One step of one mode-count group: the flat stage passes (six launches
+// over interior and edge blocks) or the two x-marching kernels.
 template <class R, int M>
-cudaError_t launch_passes(qds_handle *h, const qds_handle::Group &G, uint32_t fl, int mode, cudaStream_t st) {
+cudaError_t launch_group(qds_handle *h, const qds_handle::Group &G, int mode, cudaStream_t st) {
+  const uint32_t fl = G.flags;
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
   cudaError_t e;
-  if (mode == QDS_STEP_FLAT_MODES) {
-    if ((e = launch_flatk<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
-    if (ax && (e = launch_flat<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
-    if ((e = launch_flatk<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
-    if (ar && (e = launch_flat<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
-    if (ar && (e = launch_flatk<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
-    if (mw && (e = launch_flatk<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
+  if (mode == QDS_STEP_MARCH) {
+    if ((e = launch_march<R, M, 0>(h, G, st)) != cudaSuccess) return e;
+    if (ar && (e = launch_march<R, M, 1>(h, G, st)) != cudaSuccess) return e;
     return cudaSuccess;
   }
-  if (mode == QDS_STEP_QUEUE) {
-    if ((e = launch_queue<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
-    if (ax && (e = launch_queue<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
-    if ((e = launch_queue<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
-    if (ar && (e = launch_queue<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
-    if (ar && (e = launch_queue<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
-    if (mw && (e = launch_queue<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
-    return cudaSuccess;
-  }
-  if (mode == QDS_STEP_FLAT) {
-    if ((e = launch_flat<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
-    if (ax && (e = launch_flat<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
-    if ((e = launch_flat<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
-    if (ar && (e = launch_flat<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
-    if (ar && (e = launch_flat<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
-    if (mw && (e = launch_flat<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
-    return cudaSuccess;
-  }
-  if (mode == QDS_STEP_STAGES) {
-    if ((e = launch_pass<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
-    if (ax && (e = launch_pass<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
-  } else if ((e = launch_warp_pass<R, M, 1>(h, G, st)) != cudaSuccess) {
-    return e;
-  }
-  if (mode == QDS_STEP_WARP) {
-    if ((e = launch_warp_pass<R, M, 2>(h, G, st)) != cudaSuccess) return e;
-  } else {
-    // phi is formed in ST_SHIFT0 and the regenerated leapfrog in ST_CURRENT
-    if ((e = launch_pass<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
-    if (ar && (e = launch_pass<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
-  }
-  if (ar && (e = launch_pass<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
-  if (mw && (e = launch_pass<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
+  if ((e = launch_flat<R, M, ST_LEAP0>(h, G, st)) != cudaSuccess) return e;
+  if (ax && (e = launch_flat<R, M, ST_SOURCE>(h, G, st)) != cudaSuccess) return e;
+  if ((e = launch_flat<R, M, ST_SHIFT0>(h, G, st)) != cudaSuccess) return e;
+  if (ar && (e = launch_flat<R, M, ST_CURRENT>(h, G, st)) != cudaSuccess) return e;
+  if (ar && (e = launch_flat<R, M, ST_SHIFT1>(h, G, st)) != cudaSuccess) return e;
+  if (mw && (e = launch_flat<R, M, ST_ZERO>(h, G, st)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
+int effective_mode(const qds_handle *h) { return h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode; }
+
 template <class R>
 cudaError_t launch_step(qds_handle *h, cudaStream_t st) {
-  const int mode = h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode;
-  if (mode != QDS_STEP_FUSED) {
-    if (mode == QDS_STEP_QUEUE) zero_counters_kernel<<<1, 256, 0, st>>>(h->d_queue, h->n_queue);
-    const bool fork = h->pgroups.size() > 1;
-    cudaError_t e = cudaSuccess;
-    if (fork && (e = cudaEventRecord(h->fork, st)) != cudaSuccess) return e;
-    for (size_t gi = 0; gi < h->pgroups.size(); gi++) {
-      const auto &G = h->pgroups[gi];
-      cudaStream_t gs = st;
-      if (fork) {
-        gs = h->gstream[gi];
-        if ((e = cudaStreamWaitEvent(gs, h->fork, 0)) != cudaSuccess) return e;
-      }
-      uint32_t fl = 0;
-      for (int i = 0; i < h->n_inst; i++)
-        if (h->params[i].n_modes == G.M) fl |= h->params[i].flags;
-      switch (G.M) {
-        case 1: e = launch_passes<R, 1>(h, G, fl, mode, gs); break;
-        case 2: e = launch_passes<R, 2>(h, G, fl, mode, gs); break;
-        case 3: e = launch_passes<R, 3>(h, G, fl, mode, gs); break;
-        case 4: e = launch_passes<R, 4>(h, G, fl, mode, gs); break;
-        default: e = cudaErrorInvalidValue;
-      }
-      if (e != cudaSuccess) return e;
-      if (fork) {
-        if ((e = cudaEventRecord(h->gjoin[gi], gs)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(st, h->gjoin[gi], 0)) != cudaSuccess) return e;
-      }
+  const int mode = effective_mode(h);
+  const bool fork = h->groups.size() > 1;
+  cudaError_t e = cudaSuccess;
+  if (fork && (e = cudaEventRecord(h->fork, st)) != cudaSuccess) return e;
+  for (size_t gi = 0; gi < h->groups.size(); gi++) {
+    const auto &G = h->groups[gi];
+    cudaStream_t gs = st;
+    if (fork) {
+      gs = h->gstream[gi];
+      if ((e = cudaStreamWaitEvent(gs, h->fork, 0)) != cudaSuccess) return e;
     }
-    advance_kernel<<<1, 32, 0, st>>>(h->d_ctrl, 1);
-    return cudaGetLastError();
-  }
-  for (const auto &G : h->groups) {
-    cudaError_t e = cudaSuccess;
     switch (G.M) {
-      case 1: e = launch_group<R, 1>(h, G, st); break;
-      case 2: e = launch_group<R, 2>(h, G, st); break;
-      case 3: e = launch_group<R, 3>(h, G, st); break;
-      case 4: e = launch_group<R, 4>(h, G, st); break;
+      case 1: e = launch_group<R, 1>(h, G, mode, gs); break;
+      case 2: e = launch_group<R, 2>(h, G, mode, gs); break;
+      case 3: e = launch_group<R, 3>(h, G, mode, gs); break;
+      case 4: e = launch_group<R, 4>(h, G, mode, gs); break;
       default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
+    if (fork) {
+      if ((e = cudaEventRecord(h->gjoin[gi], gs)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(st, h->gjoin[gi], 0)) != cudaSuccess) return e;
+    }
   }
   advance_kernel<<<1, 32, 0, st>>>(h->d_ctrl, 1);
   return cudaGetLastError();
@@ -418,7 +360,60 @@ cudaError_t launch_steps(qds_handle *h, int n, cudaStream_t st) {
   return cudaSuccess;
 }
 
-int build(qds_handle *h, int n, const qds_params *params, void *state, size_t bytes, int tx, int tr) {
+void drop_graphs(qds_handle *h) {
+  for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+}
+
+// (Re)build the x-marching work items and tensor maps of every group.
+int build_march(qds_handle *h) {
+  for (auto &G : h->groups) {
+    for (int kind = 0; kind < 2; kind++) {
+      cudaFree(G.d_items[kind]);
+      G.d_items[kind] = nullptr;
+      int RB = h->rows_override > 0 ? h->rows_override : default_rows(h->fp32, kind, G.M);
+      RB = std::min(RB, std::min(256 / G.M, h->fp32 ? 256 : 128)) / 8 * 8;
+      const int halo = kind == 0 ? kHalo1 : kHalo2;
+      if (RB < 2 * halo + 8) return fail(QDS_ERR_INVALID_ARG, "march rows per CTA too small");
+      G.rows[kind] = RB;
+      G.geo[kind] = h->fp32 ? march_geo<float>(kind, G.M, RB) : march_geo<double>(kind, G.M, RB);
+      if (G.geo[kind].bytes > 227 * 1024) return fail(QDS_ERR_UNSUPPORTED, "march tile does not fit in shared memory");
+      std::vector<MarchItem> items;
+      const int seg = h->seg > 0 ? h->seg : kDefaultSeg;
+      for (int i = 0; i < h->n_inst; i++)
+        if (h->params[i].n_modes == G.M) march_items(items, i, h->params[i].nx, h->params[i].nr, RB, halo, seg);
+      G.nitems[kind] = (int)items.size();
+      CU(cudaMalloc(&G.d_items[kind], sizeof(MarchItem) * std::max<size_t>(1, items.size())));
+      CU(cudaMemcpy(G.d_items[kind], items.data(), sizeof(MarchItem) * items.size(), cudaMemcpyHostToDevice));
+    }
+    CU(allow_march_smem(h->fp32, G.M, G.geo[0].bytes, G.geo[1].bytes));
+  }
+  // tensor maps of every instance (box rows of its group)
+  std::vector<MarchMaps> maps(h->n_inst);
+  std::memset(maps.data(), 0, sizeof(MarchMaps) * maps.size());
+  for (int i = 0; i < h->n_inst; i++) {
+    const qds_params &p = h->params[i];
+    const qds_handle::Group *G = nullptr;
+    for (auto &g : h->groups)
+      if (g.M == p.n_modes) G = &g;
+    const int ld = row_ld(p);
+    char *base = h->state + h->inst_off[i];
+    const size_t half = half_bytes(p);
+    for (int par = 0; par < 2; par++) {
+      int rc = encode_map(&maps[i].k1[par], base + par * half, h->fp32, p.n_modes, p.nx, p.nr, ld, NFIELD, G->rows[0], 9);
+      if (rc) return rc;
+      rc = encode_map(&maps[i].k2[par], base + par * half, h->fp32, p.n_modes, p.nx, p.nr, ld, NFIELD, G->rows[1], 6);
+      if (rc) return rc;
+    }
+    int rc = encode_map(&maps[i].ja, base + 2 * half, h->fp32, p.n_modes, p.nx, p.nr, ld, 4, G->rows[1], 3);
+    if (rc) return rc;
+  }
+  if (!h->d_maps) CU(cudaMalloc(&h->d_maps, sizeof(MarchMaps) * h->n_inst));
+  CU(cudaMemcpy(h->d_maps, maps.data(), sizeof(MarchMaps) * h->n_inst, cudaMemcpyHostToDevice));
+  return QDS_OK;
+}
+
+int build(qds_handle *h, int n, const qds_params *params, void *state, size_t bytes) {
   if (n < 1) return fail(QDS_ERR_INVALID_ARG, "need at least one instance");
   const bool fp32 = is_fp32(params[0]);
   size_t need = 0;
@@ -435,9 +430,8 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
   h->fp32 = fp32;
   h->state = (char *)state;
   h->params.assign(params, params + n);
-  h->modes.resize(n);
+  for (auto &p : h->params) p.modes = nullptr;
   h->h_inst.resize(n);
-  h->flags = params[0].flags;
   size_t off = 0;
   for (int i = 0; i < n; i++) {
     h->inst_off.push_back(off);
@@ -454,130 +448,48 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
   h->diag_all_blocks = n >= 64 ? 8 : 64;
   CU(cudaMalloc(&h->d_partial_all, sizeof(double) * 4 * h->diag_all_blocks * n));
   {
-    std::vector<double4> sc(n);
+    std::vector<Scal4> sc(n);
     for (int i = 0; i < n; i++) {
       const bool s_ = is_scaled(params[i]);
       const double g2 = s_ ? params[i].g * params[i].g : 1.0;
-      sc[i] = make_double4(3.14159265358979323846 * params[i].dr * params[i].dx, g2, g2 * g2, g2);
+      sc[i] = Scal4{3.14159265358979323846 * params[i].dr * params[i].dx, g2, g2 * g2, g2};
     }
-    CU(cudaMalloc(&h->d_scal, sizeof(double4) * n));
-    CU(cudaMemcpy(h->d_scal, sc.data(), sizeof(double4) * n, cudaMemcpyHostToDevice));
+    CU(cudaMalloc(&h->d_scal, sizeof(Scal4) * n));
+    CU(cudaMemcpy(h->d_scal, sc.data(), sizeof(Scal4) * n, cudaMemcpyHostToDevice));
   }
-  // tiles grouped by mode count
   for (int M = 1; M <= 4; M++) {
-    std::vector<int4> tl;
-    Geo g{};
-    Smem L{};
-    uint32_t fl_union = 0;
-    bool any = false;
-    for (int i = 0; i < n; i++)
-      if (params[i].n_modes == M) { fl_union |= params[i].flags; any = true; }
-    if (!any) continue;
-    qds_params pg = params[0];
-    pg.n_modes = M;
-    pg.flags = fl_union;
-    g = pick_geo(pg, tx, tr);
-    L = smem_layout(g, M, fl_union);
-    for (int i = 0; i < n; i++) {
-      if (params[i].n_modes != M) continue;
-      for (int x0 = 0; x0 < params[i].nx; x0 += g.TX)
-        for (int r0 = 0; r0 < params[i].nr; r0 += g.TR) tl.push_back(make_int4(i, x0, r0, 0));
-    }
     qds_handle::Group G;
     G.M = M;
-    G.g = g;
-    G.L = L;
-    G.ntiles = (int)tl.size();
-    CU(cudaMalloc(&G.d_tiles, sizeof(int4) * tl.size()));
-    CU(cudaMemcpy(G.d_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice));
-    const size_t smem = (size_t)L.total * elem_bytes(pg);
-    if (smem > 227 * 1024) return fail(QDS_ERR_UNSUPPORTED, "tile does not fit in shared memory");
-    CU(allow_smem_for(fp32, M, smem));
-    h->groups.push_back(G);
-    // pass mode: 8 x 32 points per CTA, one point per thread
-    {
-      qds_handle::Group P;
-      P.M = M;
-      P.g.TX = kThreads / 32;
-      P.g.TR = 32;
-      P.L = Smem{};
-      std::vector<int4> pt, edge;
-      for (int i = 0; i < n; i++) {
-        if (params[i].n_modes != M) continue;
-        const bool per = (params[i].flags & QDS_X_PERIODIC) != 0;
-        for (int x0 = 0; x0 < params[i].nx; x0 += P.g.TX)
-          for (int r0 = 0; r0 < params[i].nr; r0 += P.g.TR) {
-            // interior: columns x0-2 .. x0+TX+1 are cells and x0+TX is a real face
-            const bool inner = per ? (params[i].nx >= P.g.TX + 4) : (x0 >= 2 && x0 + P.g.TX + 2 <= params[i].nx - 1);
-            (inner ? pt : edge).push_back(make_int4(i, x0, r0, 0));
-          }
+    bool any = false;
+    for (int i = 0; i < n; i++)
+      if (params[i].n_modes == M) { G.flags |= params[i].flags; any = true; }
+    if (!any) continue;
+    // flat passes: blocks of 256 consecutive points of one instance
+    std::vector<int4> fi, fe;
+    for (int i = 0; i < n; i++) {
+      if (params[i].n_modes != M) continue;
+      const int nx_ = params[i].nx, nr_ = params[i].nr;
+      const bool per = (params[i].flags & QDS_X_PERIODIC) != 0;
+      const int total = nx_ * nr_;
+      for (int q0 = 0; q0 < total; q0 += kThreads) {
+        const int cnt = std::min(kThreads, total - q0);
+        const int w0 = q0 / nr_, w1 = (q0 + cnt - 1) / nr_;
+        // interior: columns w0-2 .. w1+2 are cells and w1+2 is a real face
+        const bool inner = per ? (nx_ >= (w1 - w0 + 1) + 4) : (w0 >= 2 && w1 + 3 <= nx_ - 1);
+        (inner ? fi : fe).push_back(make_int4(i, q0, cnt, 0));
       }
-      P.n_interior = (int)pt.size();
-      pt.insert(pt.end(), edge.begin(), edge.end());
-      P.ntiles = (int)pt.size();
-      CU(cudaMalloc(&P.d_tiles, sizeof(int4) * pt.size()));
-      CU(cudaMemcpy(P.d_tiles, pt.data(), sizeof(int4) * pt.size(), cudaMemcpyHostToDevice));
-      // warp-column passes: (instance, x0, row of lane 0, first output row)
-      for (int q = 0; q < 2; q++) {
-        const int stride = q == 0 ? 31 : 30;
-        std::vector<int4> wi, we;
-        for (int i = 0; i < n; i++) {
-          if (params[i].n_modes != M) continue;
-          const bool per = (params[i].flags & QDS_X_PERIODIC) != 0;
-          for (int x0 = 0; x0 < params[i].nx; x0 += P.g.TX)
-            for (int r0 = 0; r0 < params[i].nr; r0 += stride) {
-              const bool inner = per ? (params[i].nx >= P.g.TX + 4) : (x0 >= 2 && x0 + P.g.TX + 2 <= params[i].nx - 1);
-              const int base = q == 0 ? r0 : (r0 > 0 ? r0 - 1 : 0);
-              (inner ? wi : we).push_back(make_int4(i, x0, base, r0));
-            }
-        }
-        P.nw_interior[q] = (int)wi.size();
-        wi.insert(wi.end(), we.begin(), we.end());
-        P.nw[q] = (int)wi.size();
-        CU(cudaMalloc(&P.d_w[q], sizeof(int4) * wi.size()));
-        CU(cudaMemcpy(P.d_w[q], wi.data(), sizeof(int4) * wi.size(), cudaMemcpyHostToDevice));
-      }
-      CU(allow_warp_smem(fp32, M));
-      {
-        std::vector<int4> fi, fe;
-        for (int i = 0; i < n; i++) {
-          if (params[i].n_modes != M) continue;
-          const int nx_ = params[i].nx, nr_ = params[i].nr;
-          const bool per = (params[i].flags & QDS_X_PERIODIC) != 0;
-          const int total = nx_ * nr_;
-          for (int q0 = 0; q0 < total; q0 += kThreads) {
-            const int cnt = std::min(kThreads, total - q0);
-            const int w0 = q0 / nr_, w1 = (q0 + cnt - 1) / nr_;
-            // interior: columns w0-2 .. w1+2 are cells and w1+2 is a real face
-            const bool inner = per ? (nx_ >= (w1 - w0 + 1) + 4) : (w0 >= 2 && w1 + 3 <= nx_ - 1);
-            (inner ? fi : fe).push_back(make_int4(i, q0, cnt, 0));
-          }
-        }
-        P.nflat_interior = (int)fi.size();
-        fi.insert(fi.end(), fe.begin(), fe.end());
-        P.nflat = (int)fi.size();
-        CU(cudaMalloc(&P.d_flat, sizeof(int4) * fi.size()));
-        CU(cudaMemcpy(P.d_flat, fi.data(), sizeof(int4) * fi.size(), cudaMemcpyHostToDevice));
-        // per mode: every block of the point list once per mode
-        std::vector<int4> ki, ke;
-        for (int k = 0; k < M; k++)
-          for (int b = 0; b < P.nflat; b++) {
-            int4 v = fi[b];
-            v.w = k;
-            (b < P.nflat_interior ? ki : ke).push_back(v);
-          }
-        P.nflatk_interior = (int)ki.size();
-        ki.insert(ki.end(), ke.begin(), ke.end());
-        P.nflatk = (int)ki.size();
-        CU(cudaMalloc(&P.d_flatk, sizeof(int4) * ki.size()));
-        CU(cudaMemcpy(P.d_flatk, ki.data(), sizeof(int4) * ki.size(), cudaMemcpyHostToDevice));
-      }
-      P.q_base = 2 * (N_STAGE + 1) * (int)h->pgroups.size();  // stages 0 .. ST_ZERO
-      h->pgroups.push_back(P);
     }
+    G.nflat_interior = (int)fi.size();
+    fi.insert(fi.end(), fe.begin(), fe.end());
+    G.nflat = (int)fi.size();
+    CU(cudaMalloc(&G.d_flat, sizeof(int4) * fi.size()));
+    CU(cudaMemcpy(G.d_flat, fi.data(), sizeof(int4) * fi.size(), cudaMemcpyHostToDevice));
+    h->groups.push_back(G);
   }
+  int rc = build_march(h);
+  if (rc) return rc;
   CU(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
-  for (size_t gi = 0; gi < h->pgroups.size(); gi++) {
+  for (size_t gi = 0; gi < h->groups.size(); gi++) {
     cudaStream_t gs;
     cudaEvent_t ev;
     CU(cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking));
@@ -585,23 +497,17 @@ int build(qds_handle *h, int n, const qds_params *params, void *state, size_t by
     CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     h->gjoin.push_back(ev);
   }
-  h->n_queue = 2 * (N_STAGE + 1) * (int)h->pgroups.size();
-  CU(cudaMalloc(&h->d_queue, sizeof(int) * std::max(1, h->n_queue)));
-  CU(cudaMemset(h->d_queue, 0, sizeof(int) * std::max(1, h->n_queue)));
-  {
-    int dev = 0;
-    CU(cudaGetDevice(&dev));
-    CU(cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev));
-  }
   return upload_inst(h, 0);
 }
 
 void destroy(qds_handle *h) {
   if (!h) return;
-  for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  for (auto &G : h->groups) cudaFree(G.d_tiles);
-  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); cudaFree(G.d_flatk); }
-  cudaFree(h->d_queue);
+  drop_graphs(h);
+  for (auto &G : h->groups) {
+    cudaFree(G.d_flat);
+    cudaFree(G.d_items[0]);
+    cudaFree(G.d_items[1]);
+  }
   for (auto gs : h->gstream) cudaStreamDestroy(gs);
   for (auto ev : h->gjoin) cudaEventDestroy(ev);
   if (h->fork) cudaEventDestroy(h->fork);
@@ -611,7 +517,18 @@ void destroy(qds_handle *h) {
   cudaFree(h->d_diag);
   cudaFree(h->d_partial_all);
   cudaFree(h->d_scal);
+  cudaFree(h->d_maps);
   delete h;
+}
+
+// Device error bits -> status (synchronises the stream).
+int read_status(qds_handle *h, cudaStream_t st) {
+  Ctrl c;
+  CU(cudaMemcpyAsync(&c, h->d_ctrl, sizeof c, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (c.err & kErrTimeout) return fail(QDS_ERR_TIMEOUT, "a bulk copy of the step kernel did not complete in time");
+  if (c.err & kErrNonfinite) return fail(QDS_ERR_NONFINITE, "non-finite field values (NaN or Inf) in the state");
+  return QDS_OK;
 }
 
 }  // namespace
@@ -653,93 +570,65 @@ int qds_batch_create(int n, const qds_params *p, void *state_dev, size_t bytes, 
   if (!out || !p) return fail(QDS_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   qds_handle *h = new qds_handle();
-  int rc = build(h, n, p, state_dev, bytes, 0, 0);
+  int rc = build(h, n, p, state_dev, bytes);
   if (rc) { destroy(h); return rc; }
   *out = h;
   return QDS_OK;
 }
 
-int qds_set_tile(qds_handle *h, int tx, int tr) {
+int qds_set_tile(qds_handle *h, int rows, int cols) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
-  if (tx < 1 || tx > 64 || tr < 4 || tr > 128) return fail(QDS_ERR_INVALID_ARG, "tile out of range");
-  std::vector<qds_params> ps = h->params;
-  void *st = h->state;
-  size_t bytes = qds_batch_state_bytes((int)ps.size(), ps.data());
-  qds_handle *nh = new qds_handle();
-  int rc = build(nh, (int)ps.size(), ps.data(), st, bytes, tx, tr);
-  if (rc) { destroy(nh); return rc; }
-  // keep the step counter
-  CU(cudaMemcpy(nh->d_ctrl, h->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToDevice));
-  for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  h->graphs.clear();
-  for (auto &G : h->groups) cudaFree(G.d_tiles);
-  cudaFree(h->d_inst); cudaFree(h->d_ctrl); cudaFree(h->d_partial); cudaFree(h->d_diag);
-  cudaFree(h->d_partial_all); cudaFree(h->d_scal);
-  for (auto &G : h->pgroups) { cudaFree(G.d_tiles); cudaFree(G.d_w[0]); cudaFree(G.d_w[1]); cudaFree(G.d_flat); cudaFree(G.d_flatk); }
-  h->groups = nh->groups; h->pgroups = nh->pgroups; h->d_inst = nh->d_inst; h->d_ctrl = nh->d_ctrl;
-  h->d_partial_all = nh->d_partial_all; h->d_scal = nh->d_scal;
-  h->d_partial = nh->d_partial; h->d_diag = nh->d_diag; h->h_inst = nh->h_inst;
-  cudaFree(h->d_queue);
-  h->d_queue = nh->d_queue; h->n_queue = nh->n_queue; h->n_sm = nh->n_sm;
-  nh->d_queue = nullptr;
-  for (auto gs : h->gstream) cudaStreamDestroy(gs);
-  for (auto ev : h->gjoin) cudaEventDestroy(ev);
-  if (h->fork) cudaEventDestroy(h->fork);
-  h->gstream = nh->gstream; h->gjoin = nh->gjoin; h->fork = nh->fork;
-  nh->gstream.clear(); nh->gjoin.clear(); nh->fork = nullptr;
-  nh->groups.clear(); nh->pgroups.clear(); nh->d_inst = nullptr; nh->d_ctrl = nullptr; nh->d_partial = nullptr;
-  nh->d_diag = nullptr; nh->d_partial_all = nullptr; nh->d_scal = nullptr;
-  delete nh;
+  if (rows < 0 || rows > 256 || cols < 0 || cols > (1 << 20) || (cols > 0 && cols < 4))
+    return fail(QDS_ERR_INVALID_ARG, "tile out of range (rows 0 or 24..256, columns 0 or >= 4)");
+  const int old_rows = h->rows_override, old_seg = h->seg;
+  h->rows_override = rows;
+  h->seg = cols;
+  int rc = build_march(h);
+  if (rc) {
+    h->rows_override = old_rows;
+    h->seg = old_seg;
+    const std::string msg = g_err;
+    build_march(h);
+    return fail(rc, msg);
+  }
+  drop_graphs(h);
+  return QDS_OK;
+}
+
+int qds_get_tile(qds_handle *h, int *rows, int *cols, int *ntiles, int *smem_bytes) {
+  if (!h || h->groups.empty()) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
+  const auto &G = h->groups[0];
+  if (rows) *rows = G.rows[0];
+  if (cols) *cols = h->seg > 0 ? h->seg : kDefaultSeg;
+  int nt = 0;
+  for (const auto &g : h->groups) nt += g.nitems[0] + g.nitems[1];
+  if (ntiles) *ntiles = nt;
+  if (smem_bytes) *smem_bytes = G.geo[0].bytes;
   return QDS_OK;
 }
 
 int qds_step_launches(const qds_handle *h) {
   if (!h) return 0;
-  const int mode = h->mode == QDS_STEP_DEFAULT ? kDefaultMode : h->mode;
-  if (mode == QDS_STEP_FUSED) return (int)h->groups.size() + 1;
-  int n = mode == QDS_STEP_QUEUE ? 2 : 1;  // step counter (+ work counters)
-  for (const auto &G : h->pgroups) {
-    uint32_t fl = 0;
-    for (int i = 0; i < h->n_inst; i++)
-      if (h->params[i].n_modes == G.M) fl |= h->params[i].flags;
-    const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0, mw = (fl & F_MOVING_WINDOW) != 0;
-    const int stage = (G.n_interior > 0) + (G.ntiles > G.n_interior);
-    const int w1 = (G.nw_interior[0] > 0) + (G.nw[0] > G.nw_interior[0]);
-    const int w2 = (G.nw_interior[1] > 0) + (G.nw[1] > G.nw_interior[1]);
-    if (mode == QDS_STEP_FLAT || mode == QDS_STEP_FLAT_MODES || mode == QDS_STEP_QUEUE) {
-      const int f = (G.nflat_interior > 0) + (G.nflat > G.nflat_interior);
-      n += f * (2 + (ax ? 1 : 0) + (ar ? 2 : 0) + (mw ? 1 : 0));
+  const int mode = effective_mode(h);
+  int n = 1;  // step counter
+  for (const auto &G : h->groups) {
+    const bool ax = (G.flags & (F_AXION | F_AREM)) != 0, ar = (G.flags & F_AREM) != 0,
+               mw = (G.flags & F_MOVING_WINDOW) != 0;
+    if (mode == QDS_STEP_MARCH) {
+      n += 1 + (ar ? 1 : 0);
       continue;
     }
-    if (mode == QDS_STEP_STAGES) n += stage * (1 + (ax ? 1 : 0));
-    else n += w1;
-    if (mode == QDS_STEP_WARP) n += w2;
-    else n += stage * (1 + (ar ? 1 : 0));
-    n += stage * ((ar ? 1 : 0) + (mw ? 1 : 0));
+    const int f = (G.nflat_interior > 0) + (G.nflat > G.nflat_interior);
+    n += f * (2 + (ax ? 1 : 0) + (ar ? 2 : 0) + (mw ? 1 : 0));
   }
   return n;
 }
 
-int qds_set_fused(qds_handle *h, int fused) { return qds_set_step_mode(h, fused ? QDS_STEP_FUSED : QDS_STEP_DEFAULT); }
-
 int qds_set_step_mode(qds_handle *h, int mode) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
-  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_QUEUE) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
+  if (mode < QDS_STEP_DEFAULT || mode > QDS_STEP_MARCH) return fail(QDS_ERR_INVALID_ARG, "unknown step mode");
   h->mode = mode;
-  for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  h->graphs.clear();
-  return QDS_OK;
-}
-
-int qds_get_tile(qds_handle *h, int *tx, int *tr, int *ntiles, int *smem_bytes) {
-  if (!h || h->groups.empty()) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
-  const auto &G = h->groups[0];
-  if (tx) *tx = G.g.TX;
-  if (tr) *tr = G.g.TR;
-  int nt = 0;
-  for (const auto &g : h->groups) nt += g.ntiles;
-  if (ntiles) *ntiles = nt;
-  if (smem_bytes) *smem_bytes = G.L.total * (h->fp32 ? 8 : 16);
+  drop_graphs(h);
   return QDS_OK;
 }
 
@@ -756,10 +645,10 @@ int qds_set_state_i(qds_handle *h, int i, const void *src, void *stream) {
   char *b = h->state + h->inst_off[i];
   if (h->fp32)
     import_kernel<float><<<592, kThreads, 0, st>>>((const double2 *)src, (C<float> *)b, (C<float> *)(b + half),
-                                                   p.n_modes, p.nx, p.nr, s_ax, s_ar);
+                                                   p.n_modes, p.nx, p.nr, row_ld(p), s_ax, s_ar);
   else
     import_kernel<double><<<592, kThreads, 0, st>>>((const double2 *)src, (C<double> *)b, (C<double> *)(b + half),
-                                                    p.n_modes, p.nx, p.nr, s_ax, s_ar);
+                                                    p.n_modes, p.nx, p.nr, row_ld(p), s_ax, s_ar);
   CU(cudaGetLastError());
   reset_kernel<<<1, 32, 0, st>>>(h->d_ctrl);
   CU(cudaGetLastError());
@@ -778,10 +667,11 @@ int qds_get_state_i(qds_handle *h, int i, void *dst, void *stream) {
   char *b = h->state + h->inst_off[i];
   if (h->fp32)
     export_kernel<float><<<592, kThreads, 0, st>>>((const C<float> *)b, (const C<float> *)(b + half), h->d_ctrl,
-                                                   (double2 *)dst, p.n_modes, p.nx, p.nr, p.flags, s_ax, s_ar);
+                                                   (double2 *)dst, p.n_modes, p.nx, p.nr, row_ld(p), p.flags, s_ax, s_ar);
   else
     export_kernel<double><<<592, kThreads, 0, st>>>((const C<double> *)b, (const C<double> *)(b + half), h->d_ctrl,
-                                                    (double2 *)dst, p.n_modes, p.nx, p.nr, p.flags, s_ax, s_ar);
+                                                    (double2 *)dst, p.n_modes, p.nx, p.nr, row_ld(p), p.flags, s_ax,
+                                                    s_ar);
   CU(cudaGetLastError());
   return QDS_OK;
 }
@@ -804,7 +694,7 @@ int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream) {
     if (rc) return rc;
     std::memcpy(h->cur_src, s4, sizeof s4);
   }
-  // Multi-step calls replay a captured graph of G launches.
+  // Multi-step calls replay a captured graph of G steps.
   const int G = 16;
   if (nsteps < G) {
     cudaError_t e = launch_steps(h, nsteps, st);
@@ -837,6 +727,11 @@ int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream) {
   return QDS_OK;
 }
 
+int qds_status(qds_handle *h, void *stream) {
+  if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
+  return read_status(h, (cudaStream_t)stream);
+}
+
 int qds_diagnostics_i(qds_handle *h, int i, double *out_host, double *profile_dev, void *stream) {
   if (!h || !out_host || i < 0 || i >= h->n_inst) return fail(QDS_ERR_INVALID_ARG, "bad handle, instance or output");
   cudaStream_t st = (cudaStream_t)stream;
@@ -846,27 +741,29 @@ int qds_diagnostics_i(qds_handle *h, int i, double *out_host, double *profile_de
   const size_t half = half_bytes(p);
   char *b = h->state + h->inst_off[i];
   const double pref = 3.14159265358979323846 * p.dr * p.dx;
+  const int ld = row_ld(p);
   if (h->fp32)
     diag_partial_kernel<float><<<h->diag_blocks, kThreads, 0, st>>>((const C<float> *)b, (const C<float> *)(b + half),
-                                                                    h->d_ctrl, p.n_modes, p.nx, p.nr, p.dr, p.m_a * p.m_a, h->d_partial);
+                                                                    h->d_ctrl, p.n_modes, p.nx, p.nr, ld, p.dr,
+                                                                    p.m_a * p.m_a, h->d_partial);
   else
     diag_partial_kernel<double><<<h->diag_blocks, kThreads, 0, st>>>((const C<double> *)b, (const C<double> *)(b + half),
-                                                                     h->d_ctrl, p.n_modes, p.nx, p.nr, p.dr, p.m_a * p.m_a, h->d_partial);
+                                                                     h->d_ctrl, p.n_modes, p.nx, p.nr, ld, p.dr,
+                                                                     p.m_a * p.m_a, h->d_partial);
   CU(cudaGetLastError());
-  diag_final_kernel<<<1, 32, 0, st>>>(h->d_partial, h->diag_blocks, pref, g2, g2 * g2, g2, h->d_diag);
+  diag_final_kernel<<<1, 32, 0, st>>>(h->d_partial, h->diag_blocks, pref, g2, g2 * g2, g2, h->d_diag, h->d_ctrl);
   CU(cudaGetLastError());
   if (profile_dev) {
     if (h->fp32)
       profile_kernel<float><<<p.nx, kThreads, 0, st>>>((const C<float> *)b, (const C<float> *)(b + half), h->d_ctrl,
-                                                       p.n_modes, p.nx, p.nr, p.dr, p.flags, profile_dev);
+                                                       p.n_modes, p.nx, p.nr, ld, p.dr, p.flags, profile_dev);
     else
       profile_kernel<double><<<p.nx, kThreads, 0, st>>>((const C<double> *)b, (const C<double> *)(b + half), h->d_ctrl,
-                                                        p.n_modes, p.nx, p.nr, p.dr, p.flags, profile_dev);
+                                                        p.n_modes, p.nx, p.nr, ld, p.dr, p.flags, profile_dev);
     CU(cudaGetLastError());
   }
   CU(cudaMemcpyAsync(out_host, h->d_diag, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
-  CU(cudaStreamSynchronize(st));
-  return QDS_OK;
+  return read_status(h, st);
 }
 
 int qds_diagnostics(qds_handle *h, double *out_host, double *profile_dev, void *stream) {
@@ -885,7 +782,7 @@ int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream) {
     diag_partial_all_kernel<double><<<grid, kThreads, 0, st>>>((const Inst<double> *)h->d_inst, h->d_ctrl, h->d_partial_all);
   CU(cudaGetLastError());
   diag_final_all_kernel<<<(h->n_inst + 127) / 128, 128, 0, st>>>(h->d_partial_all, h->diag_all_blocks, h->d_scal,
-                                                                  h->n_inst, out_dev);
+                                                                  h->n_inst, out_dev, h->d_ctrl);
   CU(cudaGetLastError());
   return QDS_OK;
 }

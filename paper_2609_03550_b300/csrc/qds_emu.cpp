@@ -1,51 +1,213 @@
 #include <algorithm>
-// qds_emu.cpp -- host emulation of the fused step kernel, for CPU tests only.
+// qds_emu.cpp -- host emulation of the step kernels, for CPU tests only.
 //
-// Compiles the same stage code as the CUDA kernel (qds_stages.cuh) for the
-// host with bounds checks on every global and shared-memory access, and runs
-// each tile's stages in kernel order (all threads of a stage before the next
-// stage).  It exists so that the tile indexing can be checked on the CPU
-// before the kernel runs on a GPU; it is a separate library (libqds_emu.so)
-// that the product path never loads.
+// Compiles the same stage code as the CUDA kernels (qds_stages.cuh,
+// qds_march.cuh) for the host with bounds checks on the shared-memory and
+// global accesses, and runs each CTA's stages in kernel order (all threads
+// of a stage before the next stage), the bulk tensor copies replaced by
+// copies with the same zero fill.  It exists so that the indexing can be
+// checked on the CPU before the kernels run on a GPU; it is a separate
+// library (libqds_emu.so) that the product path never loads.
 #define QDS_EMU 1
 #include <cstring>
 #include <vector>
 
-#include "qds_stages.cuh"
+#include "qds_march.cuh"
 
 using namespace qds;
 
 namespace {
 
 template <class R, int M>
+struct EmuState {
+  int nx, nr, ld;
+  size_t P, E;
+  std::vector<C<R>> buf[2], scratch;
+};
+
+// Flat stage passes: blocks of 256 consecutive points in (x, r) order, each
+// point a 1 x 1 tile, unchecked where the block's x-halo is inside the window.
+template <class R, int M>
+void emu_flat_step(EmuState<R, M> &S, const Inst<R> &I, int n, uint32_t flags) {
+  const int nx = S.nx, nr = S.nr;
+  const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
+  const bool per_ = (flags & F_X_PERIODIC) != 0;
+  const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_CURRENT, ST_SHIFT1, ST_ZERO};
+  for (int st : order) {
+    if (st == ST_SOURCE && !ax) continue;
+    if ((st == ST_CURRENT || st == ST_SHIFT1) && !ar) continue;
+    if (st == ST_ZERO && !mw) continue;
+    for (int q0 = 0; q0 < nx * nr; q0 += 256) {
+      const int cnt = std::min(256, nx * nr - q0);
+      const int w0 = q0 / nr, w1 = (q0 + cnt - 1) / nr;
+      const bool inner = per_ ? (nx >= (w1 - w0 + 1) + 4) : (w0 >= 2 && w1 + 3 <= nx - 1);
+      for (int q = q0; q < q0 + cnt; q++) {
+        Tile<R, M, false> t;
+        t.bind(I, &I);
+        t.nx = nx; t.nr = nr; t.ld = S.ld; t.J = nr - 1;
+        t.x0 = q / nr; t.r0 = q % nr;
+        t.per = per_;
+        t.closed = (flags & F_R_CLOSED) != 0;
+        t.mw = mw;
+        t.s = t.mw ? n % nx : 0;
+        t.P = S.P;
+        t.o = S.buf[n & 1].data();
+        t.n = S.buf[(n & 1) ^ 1].data();
+        t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
+        t.scr = S.scratch.data();
+        t.state_len = S.E;
+        if (inner) {
+          Tile<R, M, true> tf;
+          std::memcpy((void *)&tf, (const void *)&t, sizeof t);
+          run_stage<R, M, true>(tf, st);
+        } else {
+          run_stage<R, M, false>(t, st);
+        }
+      }
+    }
+  }
+}
+
+// The bulk tensor copy of one column: box [nbox planes][M][RB rows] of the
+// planes f0.. of base (stride P), rows rb0.., column coordinate coord;
+// coordinates outside (rows < 0 or >= nr, coord >= nx) read as zero.
+template <class R, int M>
+void emu_copy_box(const EmuState<R, M> &S, const C<R> *base, int f0, int nbox, int coord, int rb0, int RB,
+                  C<R> *dst) {
+  for (int f = 0; f < nbox; f++)
+    for (int k = 0; k < M; k++)
+      for (int r = 0; r < RB; r++) {
+        const int row = rb0 + r;
+        C<R> v = zero<R>();
+        if (coord >= 0 && coord < S.nx && row >= 0 && row < S.nr)
+          v = base[(size_t)(f0 + f) * S.P + ((size_t)k * S.nx + coord) * S.ld + row];
+        dst[(f * M + k) * RB + r] = v;
+      }
+}
+
+// One x-marching kernel (KIND 0: EM + axion + j_a, 1: regenerated EM) over
+// all its work items, CTA by CTA, every stage over all threads of the CTA
+// before the next (the kernel's barriers), the ring filled as the bulk
+// copies would fill it.
+template <class R, int M, int KIND>
+void emu_march_kernel(EmuState<R, M> &S, const Inst<R> &I, int n, uint32_t flags, int RB, int seg) {
+  const int nx = S.nx, nr = S.nr;
+  const MarchGeo geo = march_geo<R>(KIND, M, RB);
+  const int halo = KIND == 0 ? kHalo1 : kHalo2;
+  std::vector<C<R>> sm(geo.off_bar / sizeof(C<R>) + 1);
+  const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0;
+  // work items as the host library builds them
+  std::vector<MarchItem> items;
+  {
+    const int first = RB - halo, tr = RB - 2 * halo;
+    for (int r0 = 0; r0 < nr;) {
+      const int r1 = std::min(nr, r0 == 0 ? first : r0 + tr);
+      const int rb0 = r0 == 0 ? 0 : r0 - halo;
+      for (int xa = 0; xa < nx; xa += seg) {
+        MarchItem it{};
+        it.inst = 0; it.r0 = r0; it.r1 = r1; it.rb0 = rb0; it.xa = xa; it.xb = std::min(nx, xa + seg);
+        items.push_back(it);
+      }
+      r0 = r1;
+    }
+  }
+  const int nth = M * RB;
+  for (const MarchItem &it : items) {
+    MarchTile<R, M, KIND> t;
+    t.jx = I.jx; t.jr = I.jr; t.jt = I.jt; t.sext = I.sext;
+    t.gs = I.gs; t.gj = I.gj; t.ma2 = I.ma2;
+    t.flags = flags;
+    t.nx = nx; t.nr = nr; t.J = nr - 1; t.ld = S.ld;
+    t.x0 = 0; t.r0 = 0;
+    t.per = (flags & F_X_PERIODIC) != 0;
+    t.closed = (flags & F_R_CLOSED) != 0;
+    t.mw = (flags & F_MOVING_WINDOW) != 0;
+    t.s = t.mw ? n % nx : 0;
+    t.P = S.P;
+    t.o = S.buf[n & 1].data();
+    t.n = S.buf[(n & 1) ^ 1].data();
+    t.scr = S.scratch.data();
+    t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
+    // the kernel zeroes the intermediate planes; the ring holds whatever the
+    // shared memory held (poisoned here, so that a read of a slot no copy
+    // filled shows up in the result)
+    for (size_t q = 0; q < sm.size(); q++) sm[q] = (int)q < geo.off_a ? mk<R>((R)NAN, (R)NAN) : zero<R>();
+    t.ring = sm.data();
+    t.sa = sm.data() + geo.off_a;
+    t.sg = sm.data() + geo.off_g;
+    t.st = sm.data() + geo.off_t;
+    t.sp = sm.data() + geo.off_p;
+    t.RB = RB; t.rb0 = it.rb0; t.SS = geo.slot;
+    t.xa = it.xa; t.xb = it.xb; t.b_r0 = it.r0; t.b_r1 = it.r1;
+    t.sm_len = (int)sm.size();
+    const int L0 = march_first(KIND, it.xa), L1 = march_last(KIND, it.xb), C1 = march_last_col(KIND, it.xb);
+    auto load = [&](int c) {
+      C<R> *slot = sm.data() + ((c + 4 * kRing) % kRing) * geo.slot;
+      const int coord = march_coord(c, nx, t.s, t.per);
+      if (KIND == 0) {
+        emu_copy_box<R, M>(S, t.o, 0, 9, coord, it.rb0, RB, slot);
+      } else {
+        emu_copy_box<R, M>(S, t.o, TRP1, 6, coord, it.rb0, RB, slot);
+        emu_copy_box<R, M>(S, S.scratch.data(), 1, 3, coord, it.rb0, RB, slot + 6 * M * RB);
+      }
+    };
+    // the copies land when the kernel issues them (three ahead, then one per
+    // iteration after the first phase), which is no later than they are read
+    for (int c = L0; c <= C1 && c < L0 + 3; c++) load(c);
+    for (int L = L0; L <= L1; L++) {
+      if constexpr (KIND == 0) {
+        for (int tid = 0; tid < nth; tid++) m1_phase1<R, M>(t, L, ar, tid, nth);
+        if (L + 3 <= C1) load(L + 3);
+        for (int tid = 0; tid < nth; tid++) m1_phase2<R, M>(t, L, ax, tid, nth);
+      } else {
+        for (int tid = 0; tid < nth; tid++) m2_phase<R, M>(t, L, tid, nth);
+        if (L + 3 <= C1) load(L + 3);
+      }
+    }
+  }
+}
+
+// mode 0: flat stage passes; mode 1: the x-marching kernels with rows per
+// CTA RB1 (first kernel), RB2 (second) and seg columns per CTA.
+template <class R, int M>
 void emu_steps(const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
                uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext,
-               int nsteps, int TX, int TR, int nthreads, int fused) {
-  const size_t P = plane_elems(M, nx, nr), E = state_elems(M, nx, nr);
+               int nsteps, int RB1, int RB2, int seg, int mode) {
+  EmuState<R, M> S;
+  S.nx = nx; S.nr = nr; S.ld = row_stride<R>(nr);
+  const int ld = S.ld;
+  S.P = plane_elems(M, nx, ld);
+  S.E = state_elems(M, nx, ld);
+  const size_t P = S.P, Pc = plane_elems(M, nx, nr), Ec = state_elems(M, nx, nr);
   const bool sc = (flags & (F_FP32 | F_SCALE_G)) && g != 0.0;
   const double s_ax = sc ? 1.0 / g : 1.0, s_ar = sc ? 1.0 / (g * g) : 1.0;
-  std::vector<C<R>> buf[2];
-  buf[0].resize(E);
-  buf[1].resize(E);
-  for (size_t q = 0; q < E; q++) {
+  S.buf[0].assign(S.E, zero<R>());
+  S.buf[1].assign(S.E, zero<R>());
+  for (size_t q = 0; q < Ec; q++) {
     double sc_ = 1.0;
-    if (q < (size_t)NFIELD * P) {
-      int f = (int)(q / P);
+    size_t to;
+    if (q < (size_t)NFIELD * Pc) {
+      const int f = (int)(q / Pc);
       if (f == PHI || f == TAP || f == TAM) sc_ = s_ax;
       else if (f >= TRP1) sc_ = s_ar;
-    } else sc_ = s_ax;
-    buf[0][q] = buf[1][q] = mk<R>((R)(canon[2 * q] * sc_), (R)(canon[2 * q + 1] * sc_));
+      const size_t rem = q % Pc;
+      to = (size_t)f * P + (rem / nr) * ld + rem % nr;
+    } else {
+      sc_ = s_ax;
+      to = (size_t)NFIELD * P + (q - (size_t)NFIELD * Pc);
+    }
+    S.buf[0][to] = S.buf[1][to] = mk<R>((R)(canon[2 * q] * sc_), (R)(canon[2 * q + 1] * sc_));
   }
   std::vector<C<R>> sj[4];
   const double *srcs[4] = {jx, jr, jt, sext};
   for (int a = 0; a < 4; a++)
     if (srcs[a]) {
-      sj[a].resize(P);
-      for (size_t q = 0; q < P; q++) sj[a][q] = mk<R>((R)srcs[a][2 * q], (R)srcs[a][2 * q + 1]);
+      sj[a].resize(Pc);
+      for (size_t q = 0; q < Pc; q++) sj[a][q] = mk<R>((R)srcs[a][2 * q], (R)srcs[a][2 * q + 1]);
     }
   Inst<R> I;
   std::memset(&I, 0, sizeof I);
-  I.nx = nx; I.nr = nr; I.M = M; I.flags = flags;
+  I.nx = nx; I.nr = nr; I.ld = ld; I.M = M; I.flags = flags;
   I.h = (R)h; I.dr = (R)dr; I.inv_h = (R)(1.0 / h); I.inv_dr = (R)(1.0 / dr);
   I.ma2 = (R)(m_a * m_a);
   I.gs = sc ? (R)1 : (R)g;
@@ -54,198 +216,35 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
   I.jr = jr ? sj[1].data() : nullptr;
   I.jt = jt ? sj[2].data() : nullptr;
   I.sext = sext ? sj[3].data() : nullptr;
-  Geo geo;
-  geo.TX = TX;
-  geo.TR = TR;
-  Smem L = smem_layout(geo, M, flags);
-  std::vector<C<R>> sm(L.total);
-  std::vector<C<R>> scratch(4 * P);
-  for (int q = 0; q < (int)scratch.size(); q++) scratch[q] = mk<R>((R)1e30, (R)1e30);
-  I.scratch = scratch.data();
-  auto pass_tile_at = [&](int n, int x0, int r0) {
-    Tile<R, M, false, false> t;
-    t.bind(I, &I);
-    t.nx = nx; t.nr = nr; t.J = nr - 1;
-    t.x0 = x0; t.r0 = r0;
-    t.per = (flags & F_X_PERIODIC) != 0;
-    t.closed = (flags & F_R_CLOSED) != 0;
-    t.mw = (flags & F_MOVING_WINDOW) != 0;
-    t.s = t.mw ? n % nx : 0;
-    t.P = P;
-    t.o = buf[n & 1].data();
-    t.n = buf[(n & 1) ^ 1].data();
-    t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
-    t.g = Geo{};
-    t.g.TX = 8; t.g.TR = 32;
-    t.L = Smem{};
-    t.sm = nullptr;
-    t.scr = scratch.data();
-    t.state_len = E;
-    t.sm_len = 0;
-    return t;
-  };
-  // pass mode (fused == 0): the warp-column passes P1, P2, then the
-  // regenerated shift and the window zeroing as stage passes; warps and
-  // lanes run in order, phase 1 of all 32 lanes before phase 2
-  for (int n = 0; n < nsteps && fused == 0; n++) {
-    const bool ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
-    const bool per_ = (flags & F_X_PERIODIC) != 0;
-    for (int pass = 1; pass <= 2; pass++) {
-      const int stride = pass == 1 ? 31 : 30;
-      for (int x0 = 0; x0 < nx; x0 += 8)
-        for (int r0 = 0; r0 < nr; r0 += stride) {
-          const bool inner = per_ ? (nx >= 8 + 4) : (x0 >= 2 && x0 + 8 + 2 <= nx - 1);
-          const int base = pass == 1 ? r0 : (r0 > 0 ? r0 - 1 : 0);
-          Tile<R, M, false, false> t = pass_tile_at(n, x0, base);
-          Tile<R, M, false, true> tf;
-          std::memcpy((void *)&tf, (const void *)&t, sizeof t);
-          for (int lx = 0; lx < 8 && x0 + lx < nx; lx++) {
-            std::vector<P1Lane<R, M>> L1(32);
-            std::vector<P2Lane<R, M>> L2(32);
-            for (int ph = 0; ph < 2; ph++)
-              for (int lane = 0; lane < 32; lane++) {
-                const int j = base + lane;
-                const bool out = pass == 1 ? (lane < 31 && j < nr) : (j >= r0 && j < r0 + 30 && j < nr);
-                if (pass == 1 && ph == 0) { if (inner) p1_leap(tf, lx, lane, out, L1[lane]); else p1_leap(t, lx, lane, out, L1[lane]); }
-                if (pass == 1 && ph == 1) { if (inner) p1_source(tf, lx, lane, out, L1.data()); else p1_source(t, lx, lane, out, L1.data()); }
-                if (pass == 2 && ph == 0) { if (inner) p2_shift(tf, lx, lane, out, L2[lane]); else p2_shift(t, lx, lane, out, L2[lane]); }
-                if (pass == 2 && ph == 1) { if (inner) p2_current(tf, lx, lane, out, L2.data()); else p2_current(t, lx, lane, out, L2.data()); }
-              }
-          }
-        }
+  S.scratch.assign(4 * P, mk<R>((R)1e30, (R)1e30));
+  const bool ar = (flags & F_AREM) != 0;
+  for (int n = 0; n < nsteps; n++) {
+    if (mode == 0) {
+      emu_flat_step<R, M>(S, I, n, flags);
+    } else {
+      emu_march_kernel<R, M, 0>(S, I, n, flags, RB1, seg);
+      if (ar) emu_march_kernel<R, M, 1>(S, I, n, flags, RB2, seg);
     }
-    for (int st : {(int)ST_SHIFT1, (int)ST_ZERO}) {
-      if (st == ST_SHIFT1 && !ar) continue;
-      if (st == ST_ZERO && !mw) continue;
-      for (int x0 = 0; x0 < nx; x0 += TX)
-        for (int r0 = 0; r0 < nr; r0 += TR) {
-          Tile<R, M, false, false> t = pass_tile_at(n, x0, r0);
-          t.g.TX = TX; t.g.TR = TR;
-          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false, false>(t, st, tid, nthreads);
-        }
-    }
-  }
-  // flat stage passes (fused == 3): blocks of 256 consecutive points in
-  // (x, r) order, each point a 1 x 1 tile
-  // (fused == 4: the same, one (point, mode) per thread in the
-  // mode-independent passes)
-  for (int n = 0; n < nsteps && (fused == 3 || fused == 4); n++) {
-    const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
-    const bool per_ = (flags & F_X_PERIODIC) != 0;
-    const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_CURRENT, ST_SHIFT1, ST_ZERO};
-    for (int st : order) {
-      if (st == ST_SOURCE && !ax) continue;
-      if ((st == ST_CURRENT || st == ST_SHIFT1) && !ar) continue;
-      if (st == ST_ZERO && !mw) continue;
-      const bool per_mode = fused == 4 && st != ST_SOURCE && st != ST_CURRENT;
-      for (int kk = 0; kk < (per_mode ? M : 1); kk++)
-      for (int q0 = 0; q0 < nx * nr; q0 += 256) {
-        const int cnt = std::min(256, nx * nr - q0);
-        const int w0 = q0 / nr, w1 = (q0 + cnt - 1) / nr;
-        const bool inner = per_ ? (nx >= (w1 - w0 + 1) + 4) : (w0 >= 2 && w1 + 3 <= nx - 1);
-        for (int q = q0; q < q0 + cnt; q++) {
-          Tile<R, M, false, false> t = pass_tile_at(n, q / nr, q % nr);
-          t.g.TX = 1; t.g.TR = 1;
-          if (per_mode) { t.k_lo = kk; t.k_hi = kk + 1; }
-          if (inner) {
-            Tile<R, M, false, true> tf;
-            std::memcpy((void *)&tf, (const void *)&t, sizeof t);
-            run_stage<R, M, false, true>(tf, st, 0, 1);
-          } else {
-            run_stage<R, M, false, false>(t, st, 0, 1);
-          }
-        }
-      }
-    }
-  }
-  for (int n = 0; n < nsteps && fused == 2; n++) {
-    // stage passes: every stage over every tile before the next stage
-    const int par = n & 1;
-    const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
-    const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, ST_ZERO};
-    for (int st : order) {
-      if ((st == ST_SOURCE || st == ST_PHI) && !ax) continue;
-      if ((st == ST_CURRENT || st == ST_LEAP1 || st == ST_SHIFT1) && !ar) continue;
-      if (st == ST_ZERO && !mw) continue;
-      for (int x0 = 0; x0 < nx; x0 += TX)
-        for (int r0 = 0; r0 < nr; r0 += TR) {
-          const bool per_ = (flags & F_X_PERIODIC) != 0;
-          const bool inner = per_ ? (nx >= TX + 4) : (x0 >= 2 && x0 + TX + 2 <= nx - 1);
-          Tile<R, M, false, false> t;
-          t.bind(I, &I);
-          t.nx = nx; t.nr = nr; t.J = nr - 1;
-          t.x0 = x0; t.r0 = r0;
-          t.per = (flags & F_X_PERIODIC) != 0;
-          t.closed = (flags & F_R_CLOSED) != 0;
-          t.mw = mw;
-          t.s = t.mw ? n % nx : 0;
-          t.P = P;
-          t.o = buf[par].data();
-          t.n = buf[par ^ 1].data();
-          t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
-          t.g = geo;
-          t.L = L;
-          t.sm = nullptr;
-          t.scr = scratch.data();
-          t.state_len = E;
-          t.sm_len = 0;
-          if (inner) {
-            Tile<R, M, false, true> tf;
-            std::memcpy((void *)&tf, (const void *)&t, sizeof t);
-            for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false, true>(tf, st, tid, nthreads);
-          } else {
-            for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, false, false>(t, st, tid, nthreads);
-          }
-        }
-    }
-  }
-  for (int n = 0; n < nsteps && fused == 1; n++) {
-    const int par = n & 1;
-    for (int x0 = 0; x0 < nx; x0 += TX)
-      for (int r0 = 0; r0 < nr; r0 += TR) {
-        Tile<R, M, true> t;
-        t.bind(I, &I);
-        t.nx = nx; t.nr = nr; t.J = nr - 1;
-        t.x0 = x0; t.r0 = r0;
-        t.per = (flags & F_X_PERIODIC) != 0;
-        t.closed = (flags & F_R_CLOSED) != 0;
-        t.mw = (flags & F_MOVING_WINDOW) != 0;
-        t.s = t.mw ? n % nx : 0;
-        t.P = P;
-        t.o = buf[par].data();
-        t.n = buf[par ^ 1].data();
-        t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
-        t.g = geo;
-        t.L = L;
-        // poison shared memory so that a read of a slot no stage wrote shows up
-        for (auto &z : sm) z = mk<R>((R)1e30, (R)1e30);
-        t.sm = sm.data();
-        t.scr = nullptr;
-        t.state_len = E;
-        t.sm_len = L.total;
-        for (int st = 0; st < N_STAGE; st++)
-          for (int tid = 0; tid < nthreads; tid++) run_stage<R, M, true>(t, st, tid, nthreads);
-      }
   }
   // export in window order
-  const auto &b = buf[nsteps & 1];
+  const auto &b = S.buf[nsteps & 1];
   const int s = (flags & F_MOVING_WINDOW) ? nsteps % nx : 0;
-  for (size_t q = 0; q < E; q++) {
+  for (size_t q = 0; q < Ec; q++) {
     double sc_ = 1.0;
     size_t from;
-    if (q < (size_t)NFIELD * P) {
-      int f = (int)(q / P);
+    if (q < (size_t)NFIELD * Pc) {
+      int f = (int)(q / Pc);
       if (f == PHI || f == TAP || f == TAM) sc_ = 1.0 / s_ax;
       else if (f >= TRP1) sc_ = 1.0 / s_ar;
-      size_t rem = q % P;
+      size_t rem = q % Pc;
       int j = (int)(rem % nr);
       size_t kw = rem / nr;
       int w = (int)(kw % nx), k = (int)(kw / nx);
       int sl = (w + s) % nx;
-      from = (size_t)f * P + ((size_t)k * nx + sl) * nr + j;
+      from = (size_t)f * P + ((size_t)k * nx + sl) * ld + j;
     } else {
       sc_ = 1.0 / s_ax;
-      size_t rem = q - (size_t)NFIELD * P;
+      size_t rem = q - (size_t)NFIELD * Pc;
       int w = (int)(rem % nx), k = (int)(rem / nx);
       from = (size_t)NFIELD * P + (size_t)k * nx + (w + s) % nx;
     }
@@ -257,25 +256,28 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
 template <class R>
 int dispatch(int M, const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
              uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext, int nsteps,
-             int TX, int TR, int nth, int fused) {
+             int RB1, int RB2, int seg, int mode) {
   switch (M) {
-    case 1: emu_steps<R, 1>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
-    case 2: emu_steps<R, 2>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
-    case 3: emu_steps<R, 3>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
-    case 4: emu_steps<R, 4>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nth, fused); return 0;
+    case 1: emu_steps<R, 1>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
+    case 2: emu_steps<R, 2>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
+    case 3: emu_steps<R, 3>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
+    case 4: emu_steps<R, 4>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
   }
   return 1;
 }
 
 }  // namespace
 
+// mode 0: flat stage passes; 1: x-marching kernels (rows RB1, RB2 per CTA,
+// seg columns per CTA).
 extern "C" int qds_emu_steps(int M, const double *canon, double *out, int nx, int nr, double h, double dr,
                              double m_a, double g, uint32_t flags, const double *jx, const double *jr,
-                             const double *jt, const double *sext, int nsteps, int TX, int TR, int nthreads,
-                             int fused) {
+                             const double *jt, const double *sext, int nsteps, int RB1, int RB2, int seg,
+                             int mode) {
+  if (RB1 < 2 * kHalo1 + 8 || RB2 < 2 * kHalo2 + 8 || RB1 % 8 || RB2 % 8 || seg < 1) return 2;
   if (flags & F_FP32)
-    return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads, fused);
-  return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, TX, TR, nthreads, fused);
+    return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode);
+  return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode);
 }
 
 // ---------------------------------------------------------------------------
@@ -299,22 +301,22 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   if (jt) { sjt.resize(P); for (size_t q = 0; q < P; q++) sjt[q] = mk<R>((R)jt[2 * q], (R)jt[2 * q + 1]); }
   Inst<R> I;
   std::memset(&I, 0, sizeof I);
-  I.nx = nx; I.nr = nr; I.M = M; I.flags = flags;
+  I.nx = nx; I.nr = nr; I.ld = nr; I.M = M; I.flags = flags;
   I.h = (R)h; I.dr = (R)dr; I.inv_h = (R)(1.0 / h); I.inv_dr = (R)(1.0 / dr);
   I.ma2 = (R)(m_a * m_a);
   I.gs = (R)g; I.gj = (R)g;
   I.jx = jx ? sjx.data() : nullptr;
   I.jt = jt ? sjt.data() : nullptr;
   Adj<R, M> a;
-  Tile<R, M, false, false> &t = a.f;
+  Tile<R, M, false> &t = a.f;
   t.bind(I, &I);
-  t.nx = nx; t.nr = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
+  t.nx = nx; t.nr = nr; t.ld = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
   t.per = false; t.closed = false; t.mw = false;
   t.P = P; t.o = F.data(); t.n = nullptr;
   t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
-  t.sm = nullptr; t.scr = nullptr;
+  t.scr = nullptr;
   t.cw = -(1 << 28);  // set per column below
-  t.state_len = E; t.sm_len = 0;
+  t.state_len = E;
   a.ln = LN.data(); a.lo = LO.data(); a.sb = SB.data(); a.dg = dg;
   a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
   a.mw = (flags & F_MOVING_WINDOW) != 0;

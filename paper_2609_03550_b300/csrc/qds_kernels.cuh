@@ -1,5 +1,6 @@
-// qds_kernels.cuh -- CUDA kernels of the QDS library: the fused step, the
-// step-counter advance, state import/export and the diagnostics reductions.
+// qds_kernels.cuh -- CUDA kernels of the QDS library: the pass-mode stage
+// kernels, the step-counter advance, state import/export and the
+// diagnostics reductions.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,65 +11,29 @@ namespace qds {
 
 struct Ctrl {
   unsigned long long step;  // steps taken since the last state import
-  unsigned int err;         // device-side error flags
+  unsigned int err;         // device-side error flags (kErr*)
   unsigned int pad;
 };
 
-// One CTA per (instance, x-tile, r-tile); every stage of the step runs on
-// the tile in order with a barrier in between.
-template <class R, int M>
-__global__ void __launch_bounds__(256) step_kernel(const Inst<R> *__restrict__ insts,
-                                                   const int4 *__restrict__ tiles,
-                                                   const Ctrl *__restrict__ ctrl, Geo g, Smem L) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int4 td = tiles[blockIdx.x];
-  const Inst<R> &I = insts[td.x];
-  const unsigned long long n = ctrl->step;
-  Tile<R, M, true> t;
-  t.bind(I, &I);
-  t.nx = I.nx;
-  t.nr = I.nr;
-  t.J = I.nr - 1;
-  t.x0 = td.y;
-  t.r0 = td.z;
-  t.per = (I.flags & F_X_PERIODIC) != 0;
-  t.closed = (I.flags & F_R_CLOSED) != 0;
-  t.mw = (I.flags & F_MOVING_WINDOW) != 0;
-  t.s = t.mw ? (int)(n % (unsigned long long)I.nx) : 0;
-  t.P = plane_elems(M, I.nx, I.nr);
-  const int par = (int)(n & 1ull);
-  t.o = I.state[par];
-  t.n = I.state[par ^ 1];
-  t.h = I.h;
-  t.dr = I.dr;
-  t.ih = I.inv_h;
-  t.idr = I.inv_dr;
-  t.g = g;
-  t.L = L;
-  t.sm = reinterpret_cast<C<R> *>(smraw);
-  t.scr = nullptr;
-#pragma unroll 1
-  for (int st = 0; st < N_STAGE; st++) {
-    run_stage<R, M, true>(t, st, threadIdx.x, blockDim.x);
-    __syncthreads();
-  }
-}
+// Per-instance prefactors of the energies (diag_final_all_kernel).
+struct Scal4 {
+  double x, y, z, w;
+};
 
-// One stage ST of the step over the whole grid, one thread per (x, r) point
-// of a tile, all modes per thread; each stage is its own kernel so that it
-// carries only its own registers.
-//
-// FAST: the tile list holds only tiles whose halo lies inside the window
-// (checks skipped).  The heavy stages (axion source and current) keep their
-// registers; the light ones are held to three CTAs per SM.
-// Pass-mode view of one tile (origin x0 = td.y, row r0 = td.z) of
-// instance td.x at step n.
+// Device error bits in Ctrl::err
+constexpr unsigned kErrTimeout = 1u;    // a bounded wait of a step kernel ran out
+constexpr unsigned kErrNonfinite = 2u;  // a NaN or Inf reached the state
+
+
+// Pass-mode view of the point (x0 = td.y, r0 = td.z) of instance td.x at
+// step n.
 template <class R, int M, bool FAST>
-__device__ __forceinline__ Tile<R, M, false, FAST> pass_tile(const Inst<R> &I, int4 td, unsigned long long n, Geo g) {
-  Tile<R, M, false, FAST> t;
+__device__ __forceinline__ Tile<R, M, FAST> pass_tile(const Inst<R> &I, int4 td, unsigned long long n) {
+  Tile<R, M, FAST> t;
   t.bind(I, &I);
   t.nx = I.nx;
   t.nr = I.nr;
+  t.ld = I.ld;
   t.J = I.nr - 1;
   t.x0 = td.y;
   t.r0 = td.z;
@@ -76,7 +41,7 @@ __device__ __forceinline__ Tile<R, M, false, FAST> pass_tile(const Inst<R> &I, i
   t.closed = (I.flags & F_R_CLOSED) != 0;
   t.mw = (I.flags & F_MOVING_WINDOW) != 0;
   t.s = t.mw ? (int)(n % (unsigned long long)I.nx) : 0;
-  t.P = plane_elems(M, I.nx, I.nr);
+  t.P = plane_elems(M, I.nx, I.ld);
   const int par = (int)(n & 1ull);
   t.o = I.state[par];
   t.n = I.state[par ^ 1];
@@ -84,36 +49,25 @@ __device__ __forceinline__ Tile<R, M, false, FAST> pass_tile(const Inst<R> &I, i
   t.dr = I.dr;
   t.ih = I.inv_h;
   t.idr = I.inv_dr;
-  t.g = g;
-  t.sm = nullptr;
   t.scr = I.scratch;
   return t;
 }
 
-template <class R, int M, int ST, bool FAST>
-__global__ void __launch_bounds__(256, (ST == ST_SOURCE || ST == ST_CURRENT) ? 3 : 4)
-    pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
-                const Ctrl *__restrict__ ctrl, Geo g) {
-  const int4 td = tiles[blockIdx.x];
-  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(insts[td.x], td, ctrl->step, g);
-  run_stage<R, M, false, FAST>(t, ST, threadIdx.x, blockDim.x);
-}
-
 // Stage pass over a flat range of points: block td covers points
 // td.y .. td.y + td.z - 1 of instance td.x in (x, r) order (r fastest), one
-// point per thread, so no lane idles on rows beyond nr.  Each thread views
-// its point as a 1 x 1 tile.
+// point per thread, so no lane idles on rows beyond nr.
+//
+// FAST: the block list holds only blocks whose x-halo lies inside the window
+// (checks skipped).  The heavy stages (axion source and current) keep more
+// registers; the light ones run more CTAs per SM.
 template <class R, int M, int ST, bool FAST>
 __device__ __forceinline__ void flat_point(const Inst<R> *__restrict__ insts, int4 td, const Ctrl *__restrict__ ctrl) {
   if ((int)threadIdx.x >= td.z) return;
   const Inst<R> &I = insts[td.x];
   const int q = td.y + (int)threadIdx.x;
   const int w = q / I.nr, j = q - w * I.nr;
-  Geo g{};
-  g.TX = 1;
-  g.TR = 1;
-  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl->step, g);
-  run_stage<R, M, false, FAST>(t, ST, 0, 1);
+  Tile<R, M, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl->step);
+  run_stage<R, M, FAST>(t, ST);
 }
 
 template <int M, int ST>
@@ -128,83 +82,6 @@ __global__ void __launch_bounds__(256, flat_ctas_per_sm<M, ST>())
   flat_point<R, M, ST, FAST>(insts, tiles[blockIdx.x], ctrl);
 }
 
-// Persistent form of the same pass: a grid of (SMs x resident CTAs) blocks
-// takes the blocks of the point list from a work counter (zeroed at the
-// start of each step) until the list is exhausted.
-template <class R, int M, int ST, bool FAST>
-__global__ void __launch_bounds__(256, flat_ctas_per_sm<M, ST>())
-    queue_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles, int ntiles,
-                      int *__restrict__ counter, const Ctrl *__restrict__ ctrl) {
-  __shared__ int next;
-  for (;;) {
-    __syncthreads();  // every thread has read the previous value of next
-    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
-    __syncthreads();
-    const int b = next;
-    if (b >= ntiles) return;
-    flat_point<R, M, ST, FAST>(insts, tiles[b], ctrl);
-  }
-}
-
-static __global__ void zero_counters_kernel(int *c, int n) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) c[i] = 0;
-}
-
-// Mode-independent stage pass (leapfrog, shift, regenerated shift, window
-// zeroing) over a flat range of points of one mode: block td covers points
-// td.y .. td.y + td.z - 1 of mode td.w of instance td.x, one (point, mode)
-// per thread.
-template <class R, int M, int ST, bool FAST>
-__global__ void __launch_bounds__(256, 4)
-    flatk_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
-                      const Ctrl *__restrict__ ctrl) {
-  const int4 td = tiles[blockIdx.x];
-  if ((int)threadIdx.x >= td.z) return;
-  const Inst<R> &I = insts[td.x];
-  const int q = td.y + (int)threadIdx.x;
-  const int w = q / I.nr, j = q - w * I.nr;
-  Geo g{};
-  g.TX = 1;
-  g.TR = 1;
-  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl->step, g);
-  t.k_lo = td.w;
-  t.k_hi = td.w + 1;
-  run_stage<R, M, false, FAST>(t, ST, 0, 1);
-}
-
-// Warp-column passes (P1: leapfrog + Gamma_a; P2: shift + phi + j_a +
-// regenerated leapfrog).  Block = 8 warps = 8 columns x0..x0+7; lane l of a
-// warp holds row td.z + l; P2 outputs rows [td.w, td.w + 30).
-template <class R, int M>
-constexpr size_t warp_pass_smem(int pass) {
-  return 256 * (pass == 1 ? sizeof(P1Lane<R, M>) : sizeof(P2Lane<R, M>));
-}
-
-template <class R, int M, int PASS, bool FAST>
-__global__ void __launch_bounds__(256, 2)
-    warp_pass_kernel(const Inst<R> *__restrict__ insts, const int4 *__restrict__ tiles,
-                     const Ctrl *__restrict__ ctrl, Geo g) {
-  extern __shared__ __align__(16) unsigned char wsm[];
-  const int4 td = tiles[blockIdx.x];
-  Tile<R, M, false, FAST> t = pass_tile<R, M, FAST>(insts[td.x], td, ctrl->step, g);
-  const int lx = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (t.x0 + lx >= t.nx) return;  // the whole warp: its column lies beyond the window
-  const int j = t.r0 + lane;
-  if (PASS == 1) {
-    P1Lane<R, M> *L = reinterpret_cast<P1Lane<R, M> *>(wsm) + lx * 32;
-    const bool out = lane < 31 && j < t.nr;
-    p1_leap(t, lx, lane, out, L[lane]);
-    __syncwarp();
-    p1_source(t, lx, lane, out, L);
-  } else {
-    P2Lane<R, M> *L = reinterpret_cast<P2Lane<R, M> *>(wsm) + lx * 32;
-    const bool out = j >= td.w && j < td.w + 30 && j < t.nr;
-    p2_shift(t, lx, lane, out, L[lane]);
-    __syncwarp();
-    p2_current(t, lx, lane, out, L);
-  }
-}
-
 static __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {
   if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->step += (unsigned long long)nsteps;
 }
@@ -213,24 +90,31 @@ static __global__ void reset_kernel(Ctrl *ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) { ctrl->step = 0; ctrl->err = 0; }
 }
 
-// Canonical complex128 layout <-> working storage (precision, ring offset,
-// 1/g scaling of the axion and regenerated groups).
+// Canonical complex128 layout <-> working storage (precision, row stride,
+// ring offset, 1/g scaling of the axion and regenerated groups).  The import
+// walks the working layout so that the padding rows are written as zero.
 template <class R>
-__global__ void import_kernel(const double2 *__restrict__ src, C<R> *b0, C<R> *b1, int M, int nx, int nr,
+__global__ void import_kernel(const double2 *__restrict__ src, C<R> *b0, C<R> *b1, int M, int nx, int nr, int ld,
                               double s_ax, double s_ar) {
-  const size_t P = plane_elems(M, nx, nr);
-  const size_t total = state_elems(M, nx, nr);
+  const size_t P = plane_elems(M, nx, ld), Pc = plane_elems(M, nx, nr);
+  const size_t total = state_elems(M, nx, ld);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     double sc = 1.0;
+    C<R> z = zero<R>();
     if (q < (size_t)NFIELD * P) {
-      int f = (int)(q / P);
+      const int f = (int)(q / P);
       if (f == PHI || f == TAP || f == TAM) sc = s_ax;
       else if (f >= TRP1) sc = s_ar;
+      const size_t rem = q - (size_t)f * P;
+      const int j = (int)(rem % ld);
+      if (j < nr) {
+        const double2 v = src[(size_t)f * Pc + (rem / ld) * nr + j];
+        z = mk<R>((R)(v.x * sc), (R)(v.y * sc));
+      }
     } else {
-      sc = s_ax;  // phi_prev
+      const double2 v = src[(size_t)NFIELD * Pc + (q - (size_t)NFIELD * P)];  // phi_prev
+      z = mk<R>((R)(v.x * s_ax), (R)(v.y * s_ax));
     }
-    double2 v = src[q];
-    C<R> z = mk<R>((R)(v.x * sc), (R)(v.y * sc));
     b0[q] = z;
     b1[q] = z;
   }
@@ -238,28 +122,28 @@ __global__ void import_kernel(const double2 *__restrict__ src, C<R> *b0, C<R> *b
 
 template <class R>
 __global__ void export_kernel(const C<R> *__restrict__ b0, const C<R> *__restrict__ b1, const Ctrl *ctrl,
-                              double2 *dst, int M, int nx, int nr, uint32_t flags, double s_ax, double s_ar) {
+                              double2 *dst, int M, int nx, int nr, int ld, uint32_t flags, double s_ax, double s_ar) {
   const unsigned long long n = ctrl->step;
   const C<R> *b = (n & 1ull) ? b1 : b0;
   const int s = (flags & F_MOVING_WINDOW) ? (int)(n % (unsigned long long)nx) : 0;
-  const size_t P = plane_elems(M, nx, nr);
+  const size_t P = plane_elems(M, nx, ld), Pc = plane_elems(M, nx, nr);
   const size_t total = state_elems(M, nx, nr);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
     double sc = 1.0;
     size_t from;
-    if (q < (size_t)NFIELD * P) {
-      int f = (int)(q / P);
+    if (q < (size_t)NFIELD * Pc) {
+      int f = (int)(q / Pc);
       if (f == PHI || f == TAP || f == TAM) sc = s_ax;
       else if (f >= TRP1) sc = s_ar;
-      size_t rem = q % P;
+      size_t rem = q % Pc;
       int j = (int)(rem % nr);
       size_t kw = rem / nr;
       int w = (int)(kw % nx), k = (int)(kw / nx);
       int sl = w + s; if (sl >= nx) sl -= nx;
-      from = (size_t)f * P + ((size_t)k * nx + sl) * nr + j;
+      from = (size_t)f * P + ((size_t)k * nx + sl) * ld + j;
     } else {
       sc = s_ax;
-      size_t rem = q - (size_t)NFIELD * P;
+      size_t rem = q - (size_t)NFIELD * Pc;
       int w = (int)(rem % nx), k = (int)(rem / nx);
       int sl = w + s; if (sl >= nx) sl -= nx;
       from = (size_t)NFIELD * P + (size_t)k * nx + sl;
@@ -307,10 +191,11 @@ __device__ __forceinline__ R dotR(C<R> a, C<R> b) { return a.re * b.re + a.im * 
 // Energy densities of one (mode, x, r) element of one instance, added to the
 // four accumulators em0, axion, em1, cross (without the common prefactor).
 template <class R>
-__device__ __forceinline__ void diag_element(const C<R> *S, size_t P, size_t q, int nx, int nr, R dr,
+__device__ __forceinline__ void diag_element(const C<R> *S, size_t P, size_t q, int nx, int nr, int ld, R dr,
                                              R ma2, NeuR<R> &a0, NeuR<R> &a1, NeuR<R> &a2, NeuR<R> &a3) {
-  const int j = (int)(q % nr);
-  const int k = (int)(q / ((size_t)nx * nr));
+  const int j = (int)(q % ld);
+  if (j >= nr) return;  // padding row
+  const int k = (int)(q / ((size_t)nx * ld));
   const R wm = k == 0 ? R(1) : R(0.5);
   const R rh = (R(j) + R(0.5)) * dr, rs = j == 0 ? dr / R(8) : R(j) * dr;
   R e[2];
@@ -358,12 +243,12 @@ __device__ __forceinline__ void block_reduce4(A &a0, A &a1, A &a2, A &a3, double
 // partial[b*4 + 0..3]: em0, axion, em1, cross of one instance
 template <class R>
 __global__ void diag_partial_kernel(const C<R> *__restrict__ b0, const C<R> *__restrict__ b1, const Ctrl *ctrl,
-                                    int M, int nx, int nr, double dr, double ma2, double *partial) {
+                                    int M, int nx, int nr, int ld, double dr, double ma2, double *partial) {
   const C<R> *S = (ctrl->step & 1ull) ? b1 : b0;
-  const size_t P = plane_elems(M, nx, nr);
+  const size_t P = plane_elems(M, nx, ld);
   NeuR<R> a0, a1, a2, a3;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x)
-    diag_element<R>(S, P, q, nx, nr, (R)dr, (R)ma2, a0, a1, a2, a3);
+    diag_element<R>(S, P, q, nx, nr, ld, (R)dr, (R)ma2, a0, a1, a2, a3);
   block_reduce4(a0, a1, a2, a3, partial + blockIdx.x * 4);
 }
 
@@ -372,29 +257,34 @@ template <class R>
 __global__ void diag_partial_all_kernel(const Inst<R> *__restrict__ insts, const Ctrl *ctrl, double *partial) {
   const Inst<R> &I = insts[blockIdx.y];
   const C<R> *S = I.state[ctrl->step & 1ull];
-  const size_t P = plane_elems(I.M, I.nx, I.nr);
+  const size_t P = plane_elems(I.M, I.nx, I.ld);
   NeuR<R> a0, a1, a2, a3;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < P; q += (size_t)gridDim.x * blockDim.x)
-    diag_element<R>(S, P, q, I.nx, I.nr, I.dr, I.ma2, a0, a1, a2, a3);
+    diag_element<R>(S, P, q, I.nx, I.nr, I.ld, I.dr, I.ma2, a0, a1, a2, a3);
   block_reduce4(a0, a1, a2, a3, partial + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4);
 }
 
-// scal[i] = {pi dr dx, g^2 or 1, g^4 or 1, g^2 or 1} per instance
-static __global__ void diag_final_all_kernel(const double *partial, int nblk, const double4 *scal, int n, double *out) {
+// scal[i] = {pi dr dx, g^2 or 1, g^4 or 1, g^2 or 1} per instance; a
+// non-finite energy sets kErrNonfinite
+static __global__ void diag_final_all_kernel(const double *partial, int nblk, const Scal4 *scal, int n, double *out,
+                                             Ctrl *ctrl) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   Neu s[4];
   for (int b = 0; b < nblk; b++)
     for (int c = 0; c < 4; c++) s[c].add(partial[((size_t)i * nblk + b) * 4 + c]);
-  const double4 f = scal[i];
+  const Scal4 f = scal[i];
   out[4 * i + 0] = f.x * s[0].val();
   out[4 * i + 1] = f.x * s[1].val() * f.y;
   out[4 * i + 2] = f.x * s[2].val() * f.z;
   out[4 * i + 3] = 2.0 * f.x * s[3].val() * f.w;
+  bool ok = true;
+  for (int c = 0; c < 4; c++) ok = ok && isfinite(out[4 * i + c]);
+  if (!ok) atomicOr(&ctrl->err, kErrNonfinite);
 }
 
 static __global__ void diag_final_kernel(const double *partial, int nblk, double pref, double s_ax2, double s_ar2,
-                                  double s_cross, double *out) {
+                                         double s_cross, double *out, Ctrl *ctrl) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   Neu s[4];
   for (int b = 0; b < nblk; b++)
@@ -403,23 +293,24 @@ static __global__ void diag_final_kernel(const double *partial, int nblk, double
   out[1] = pref * s[1].val() * s_ax2;
   out[2] = pref * s[2].val() * s_ar2;
   out[3] = 2.0 * pref * s[3].val() * s_cross;
+  if (!(isfinite(out[0]) && isfinite(out[1]) && isfinite(out[2]) && isfinite(out[3]))) atomicOr(&ctrl->err, kErrNonfinite);
 }
 
 // U(x_w) = int (1/2)(|E_perp|^2 + |B_perp|^2) dA of group 0 (Sec. 4.1), one
 // block per window column.
 template <class R>
 __global__ void profile_kernel(const C<R> *__restrict__ b0, const C<R> *__restrict__ b1, const Ctrl *ctrl,
-                               int M, int nx, int nr, double dr, uint32_t flags, double *prof) {
+                               int M, int nx, int nr, int ld, double dr, uint32_t flags, double *prof) {
   const unsigned long long n = ctrl->step;
   const C<R> *S = (n & 1ull) ? b1 : b0;
   const int s = (flags & F_MOVING_WINDOW) ? (int)(n % (unsigned long long)nx) : 0;
   const int w = blockIdx.x;
   int sl = w + s; if (sl >= nx) sl -= nx;
-  const size_t P = plane_elems(M, nx, nr);
+  const size_t P = plane_elems(M, nx, ld);
   Neu acc;
   for (int q = threadIdx.x; q < M * nr; q += blockDim.x) {
     const int k = q / nr, j = q % nr;
-    const size_t e = ((size_t)k * nx + sl) * nr + j;
+    const size_t e = ((size_t)k * nx + sl) * ld + j;
     C<R> tp = S[(size_t)TRP * P + e], tm = S[(size_t)TRM * P + e];
     C<R> up = S[(size_t)TTP * P + e], um = S[(size_t)TTM * P + e];
     const double wm = k == 0 ? 1.0 : 0.5;

@@ -1,6 +1,8 @@
-// qds_stages.cuh -- the stages of one fused QDS + axion + AREM step on an
-// (x, r) tile.  Every stage is a loop over the points of a tile-local region
-// with a barrier between stages; each point handles all retained modes.
+// qds_stages.cuh -- the point formulas of one QDS + axion + AREM step and
+// the pass-mode accessor over the whole grid.  The formulas are written
+// against an accessor type TT (the pass-mode Tile below, or the x-marching
+// kernels' shared-memory view in qds_march.cuh) that supplies the old state,
+// the intermediate planes of the step and the sources.
 //
 // Window coordinates: cell w sits at x_w, face w at x_{w+1/2}; the storage
 // slot of window position w is (w + s) mod nx, where s advances by one per
@@ -49,23 +51,21 @@ QDS_HD C<R> ldg(const C<R> *p) {
 #endif
 }
 
-// SM = true: the fused step, intermediates in the CTA's shared memory with
-// halos recomputed per tile.  SM = false: one pass per stage over the whole
-// grid, intermediates in the new state buffer and the scratch planes.
-// FAST = true: every access of the tile (its halo included) lies inside the
-// window, so the accessors skip their checks (the formulas themselves only
-// touch rows 0..nr-1).
-template <class R, int M, bool SM = true, bool FAST = false>
+// Pass-mode accessor: one pass per stage over the whole grid, intermediates
+// in the new state buffer and the scratch planes.  FAST = true: every access
+// of the point (its x-halo included) lies inside the window, so the accessors
+// skip their checks (the formulas themselves only touch rows 0..nr-1).
+template <class R, int M, bool FAST = false>
 struct Tile {
+  using Real = R;
+  static constexpr int kM = M;
+  static constexpr bool kSM = false;  // intermediates are global planes
   const Inst<R> *I;
   // values of the descriptor used per point, held in registers (loads
   // through I could not be hoisted past the stores of a pass)
   const C<R> *jx, *jr, *jt, *sext;
   R gs, gj, ma2;
   uint32_t flags;
-  // modes k_lo .. k_hi-1 of the mode-independent stages (leapfrog, shift,
-  // window zeroing); a pass over single modes narrows the range
-  int k_lo = 0, k_hi = M;
   QDS_HD void bind(const Inst<R> &d, const Inst<R> *dev) {
     I = dev;
     jx = d.jx; jr = d.jr; jt = d.jt; sext = d.sext;
@@ -73,21 +73,18 @@ struct Tile {
     flags = d.flags;
   }
   int nx, nr, J;       // J = nr - 1: last integer row / last half row
-  int x0, r0;          // tile origin in window coordinates
+  int ld;              // row stride of the working planes
+  int x0, r0;          // point origin in window coordinates
   int s;               // ring offset of the window
   bool per, closed, mw;
   size_t P;            // elements per field (M planes)
   const C<R> *o;       // old state
   C<R> *n;             // new state
   R h, dr, ih, idr;
-  Geo g;
-  Smem L;
-  C<R> *sm;
-  C<R> *scr;              // pass mode: scratch planes Gamma_a, j_a,x, j_a,r, j_a,th
-  mutable C<R> dummy;     // pass mode: target of out-of-domain accesses
+  C<R> *scr;              // scratch planes Gamma_a, j_a,x, j_a,r, j_a,th
+  mutable C<R> dummy;     // target of out-of-domain accesses
 #if defined(QDS_EMU)
   size_t state_len;    // bounds for the emulator
-  int sm_len;
 #endif
 
   // ---------------- index helpers ----------------
@@ -121,12 +118,12 @@ struct Tile {
     return slot_slow(w);
   }
   QDS_HD unsigned eidx(int field, int k, int sl, int j) const {
-    return (unsigned)field * (unsigned)P + ((unsigned)k * (unsigned)nx + (unsigned)sl) * (unsigned)nr + (unsigned)j;
+    return (unsigned)field * (unsigned)P + ((unsigned)k * (unsigned)nx + (unsigned)sl) * (unsigned)ld + (unsigned)j;
   }
   QDS_HD size_t gidx(int field, int k, int w, int j) const { return eidx(field, k, slot(w), j); }
   QDS_HD C<R> cell(int field, int k, int w, int j) const {
     const int sl = slot(w);
-    if (FAST) {  // the tile and its halo lie inside the window
+    if (FAST) {  // the point and its halo lie inside the window
 #if defined(QDS_EMU)
       QDS_CHECK(j >= 0 && j < nr && sl >= 0, "unchecked cell access");
 #endif
@@ -164,18 +161,16 @@ struct Tile {
     return ldg(a + ((size_t)k * nx + w) * nr + j);
   }
   QDS_HD void store(int field, int k, int w, int j, C<R> v) const {
-    if (SM && mw && w == 0) v = zero<R>();  // the rear column becomes the new front
 #if defined(QDS_EMU)
     QDS_CHECK(gidx(field, k, w, j) < state_len, "store");
 #endif
     n[gidx(field, k, w, j)] = v;
   }
   QDS_HD void store_prev(int k, int w, C<R> v) const {
-    if (SM && mw && w == 0) v = zero<R>();
     n[(size_t)NFIELD * P + (size_t)k * nx + slot(w)] = v;
   }
   QDS_HD bool owned(int lx, int lr) const {
-    return lx >= 0 && lx < g.TX && lr >= 0 && lr < g.TR && x0 + lx < nx && r0 + lr < nr;
+    return lx == 0 && lr == 0 && x0 < nx && r0 < nr;
   }
 
   // transverse fields at time n of group grp (0 or 9), Eq. reconstruct_fields
@@ -185,12 +180,11 @@ struct Tile {
   QDS_HD C<R> Br(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) - cell(grp + TTM, k, w, j)); }
 
   // ---------------- intermediate planes ----------------
-  // pass mode: a plane of the new state (or scratch) at window position w;
-  // out-of-domain positions read as zero and absorb writes
-  // Every window position 0..nx-1 is a storage slot (the held-zero face
-  // nx-1 included, so that it is written as zero each step); positions
-  // outside the window read as zero.
-  QDS_HD C<R> &gnew(int field, int k, int w, int j, bool /*face_pos*/) const {
+  // A plane of the new state (or scratch) at window position w;
+  // out-of-domain positions read as zero and absorb writes.  Every window
+  // position 0..nx-1 is a storage slot (the held-zero face nx-1 included,
+  // so that it is written as zero each step).
+  QDS_HD C<R> &gnew(int field, int k, int w, int j) const {
     if (FAST) {
 #if defined(QDS_EMU)
       QDS_CHECK(cell_ok(w) && j >= 0 && j < nr, "unchecked new-state access");
@@ -205,52 +199,20 @@ struct Tile {
     return n[gidx(field, k, w, j)];
   }
   QDS_HD C<R> &gscr(int plane, int k, int w, int j) const {
-    if (FAST) return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * nr + j];
+    if (FAST) return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * ld + j];
     if (!cell_ok(w) || j < 0 || j >= nr) { dummy = zero<R>(); return dummy; }
-    return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * nr + j];
+    return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * ld + j];
   }
-  QDS_HD C<R> &sA(int pl, int k, int lx, int lr) const {  // pl 0: Ex0n, 1: Bx0n
-    if (!SM) return gnew(pl ? BX : EX, k, x0 + lx, r0 + lr, true);
-    int i = L.off_a + ((pl * M + k) * g.a_nx() + (lx - g.a_x0())) * g.a_nr() + (lr - g.a_r0());
-#if defined(QDS_EMU)
-    QDS_CHECK(lx >= g.a_x0() && lx < g.a_x0() + g.a_nx() && lr >= g.a_r0() && lr < g.a_r0() + g.a_nr(), "sA");
-#endif
-    return sm[i];
-  }
-  QDS_HD C<R> &sG(int k, int lx, int lr) const {
-    if (!SM) return gscr(0, k, x0 + lx, r0 + lr);
-    int i = L.off_j + (k * g.g_nx() + (lx - g.g_x0())) * g.g_nr() + (lr - g.g_r0());
-#if defined(QDS_EMU)
-    QDS_CHECK(lx >= g.g_x0() && lx < g.g_x0() + g.g_nx() && lr >= g.g_r0() && lr < g.g_r0() + g.g_nr(), "sG");
-#endif
-    return sm[i];
-  }
+  // lx, lr are offsets from the point (x0, r0)
+  QDS_HD C<R> &sA(int pl, int k, int lx, int lr) const { return gnew(pl ? BX : EX, k, x0 + lx, r0 + lr); }  // 0: Ex0n, 1: Bx0n
+  QDS_HD C<R> &sG(int k, int lx, int lr) const { return gscr(0, k, x0 + lx, r0 + lr); }
   QDS_HD C<R> &sT(int pl, int k, int lx, int lr) const {  // 0..3 T0 new, 4 Tap new, 5 Tam new
-    if (!SM) return gnew(pl < 4 ? TRP + pl : TAP + (pl - 4), k, x0 + lx, r0 + lr, false);
-    int i = L.off_t + ((pl * M + k) * g.t_nx() + (lx - g.t_x0())) * g.t_nr() + (lr - g.t_r0());
-#if defined(QDS_EMU)
-    QDS_CHECK(lx >= g.t_x0() && lx < g.t_x0() + g.t_nx() && lr >= g.t_r0() && lr < g.t_r0() + g.t_nr(), "sT");
-#endif
-    return sm[i];
+    return gnew(pl < 4 ? TRP + pl : TAP + (pl - 4), k, x0 + lx, r0 + lr);
   }
-  QDS_HD C<R> &sP(int k, int lx, int lr) const {
-    if (!SM) return gnew(PHI, k, x0 + lx, r0 + lr, true);
-    int i = L.off_p + (k * g.p_nx() + (lx - g.p_x0())) * g.p_nr() + (lr - g.p_r0());
-#if defined(QDS_EMU)
-    QDS_CHECK(lx >= g.p_x0() && lx < g.p_x0() + g.p_nx() && lr >= g.p_r0() && lr < g.p_r0() + g.p_nr(), "sP");
-#endif
-    return sm[i];
-  }
+  QDS_HD C<R> &sP(int k, int lx, int lr) const { return gnew(PHI, k, x0 + lx, r0 + lr); }
   QDS_HD C<R> &sJ(int pl, int k, int lx, int lr) const {  // 0 Ex1n 1 Bx1n 2 jax 3 jar 4 jat
-    if (!SM) {
-      if (pl < 2) return gnew(pl ? BX1 : EX1, k, x0 + lx, r0 + lr, true);
-      return gscr(pl - 1, k, x0 + lx, r0 + lr);
-    }
-    int i = L.off_j + ((pl * M + k) * g.j_nx() + (lx - g.j_x0())) * g.j_nr() + (lr - g.j_r0());
-#if defined(QDS_EMU)
-    QDS_CHECK(lx >= g.j_x0() && lx < g.j_x0() + g.j_nx() && lr >= g.j_r0() && lr < g.j_r0() + g.j_nr(), "sJ");
-#endif
-    return sm[i];
+    if (pl < 2) return gnew(pl ? BX1 : EX1, k, x0 + lx, r0 + lr);
+    return gscr(pl - 1, k, x0 + lx, r0 + lr);
   }
 };
 
@@ -287,8 +249,8 @@ QDS_HD C<R> conv(int m, const C<R> *A, const C<R> *B) {
 // conservative form, (1/r) d(r F)/dr = (r_+ F_+ - r_- F_-)/(r dr), which is
 // algebraically the paper's average-plus-centred-difference form.
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM, bool FAST>
-QDS_NOINL C<R> ex_update(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, int j, C<R> jx) {
+template <class TT, class R = typename TT::Real>
+QDS_NOINL C<R> ex_update(const TT &t, int grp, int k, int w, int j, C<R> jx) {
   C<R> e0 = t.face(grp + EX, k, w, j);
   if (j == 0) {
     if (k != 0) return zero<R>();
@@ -304,8 +266,8 @@ QDS_NOINL C<R> ex_update(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, i
   return e0 + t.h * gx;
 }
 
-template <class R, int M, bool SM, bool FAST>
-QDS_NOINL C<R> bx_interior(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, int j) {
+template <class TT, class R = typename TT::Real>
+QDS_NOINL C<R> bx_interior(const TT &t, int grp, int k, int w, int j) {
   C<R> b0 = t.face(grp + BX, k, w, j);
   R rh = (R(j) + R(0.5)) * t.dr;
   C<R> elo = R(0.5) * (t.Et(grp, k, w, j) + t.Et(grp, k, w + 1, j));
@@ -317,8 +279,8 @@ QDS_NOINL C<R> bx_interior(const Tile<R, M, SM, FAST> &t, int grp, int k, int w,
 
 // Outer half row J+1/2, Eq. em_r_open_bx by the box scheme over
 // [r_{J-1/2}, r_{J+1/2}] x [t^{n-1/2}, t^{n+1/2}], right side at (x_{w+1/2}, r_J, t^n).
-template <class R, int M, bool SM, bool FAST>
-QDS_NOINL C<R> bx_outer(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
+template <class TT, class R = typename TT::Real>
+QDS_NOINL C<R> bx_outer(const TT &t, int grp, int k, int w, C<R> jt_face, C<R> b_in_new) {
   const int J = t.J;
   R rJ = R(J) * t.dr;
   C<R> dxbr = t.ih * (t.Br(grp, k, w + 1, J) - t.Br(grp, k, w, J));
@@ -335,8 +297,8 @@ QDS_NOINL C<R> bx_outer(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, C<
 // value loaded once: E_x from B_theta on half rows j-1, j and B_r on row j;
 // B_x from E_theta on rows j, j+1 and E_r on half row j (the same
 // expressions as ex_update and bx_interior; the outer row takes bx_outer).
-template <class R, int M, bool SM, bool FAST>
-QDS_NOINL void leap_point(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, int j, C<R> jx, C<R> jt_face,
+template <class TT, class R = typename TT::Real>
+QDS_NOINL void leap_point(const TT &t, int grp, int k, int w, int j, C<R> jx, C<R> jt_face,
                           C<R> &ex, C<R> &bx) {
   // cell sums over w, w+1 of the reconstructed fields (Eq. reconstruct_fields)
   const C<R> rp = t.cell(grp + TRP, k, w, j) + t.cell(grp + TRP, k, w + 1, j);
@@ -376,9 +338,10 @@ QDS_NOINL void leap_point(const Tile<R, M, SM, FAST> &t, int grp, int k, int w, 
 // from the tile's shared memory and x-averages the caller's cell currents;
 // group 1 (the regenerated field) reads E_x1, B_x1 and j_a from shared memory.
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM, bool FAST>
+template <class TT>
 struct Faces0 {
-  const Tile<R, M, SM, FAST> &t;
+  using R = typename TT::Real;
+  const TT &t;
   QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sA(0, k, lx, lr); }
   QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sA(1, k, lx, lr); }
   QDS_HD C<R> jr(int k, int lx, int lr) const {
@@ -398,9 +361,10 @@ struct Faces0 {
   }
 };
 
-template <class R, int M, bool SM, bool FAST>
+template <class TT>
 struct Faces1 {
-  const Tile<R, M, SM, FAST> &t;
+  using R = typename TT::Real;
+  const TT &t;
   QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sJ(0, k, lx, lr); }
   QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sJ(1, k, lx, lr); }
   QDS_HD C<R> jx(int k, int lx, int lr) const { return t.sJ(2, k, lx, lr); }
@@ -414,9 +378,8 @@ struct Faces1 {
 // behind through face c-1, T_r^- and T_th^+ from the cell ahead through face
 // c.  Axis rules of Sec. 2.3 (Eq. axis_Ttheta; T_th^(m!=1) = 0 on the axis).
 // ---------------------------------------------------------------------------
-template <class R, int M, bool SM, bool FAST, class FS>
-QDS_NOINL void tr_interior(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, int k, int lx, int lr,
-                        C<R> &tp, C<R> &tm) {
+template <class TT, class FS, class R = typename TT::Real>
+QDS_NOINL void tr_interior(const TT &t, const FS &fs, int grp, int k, int lx, int lr, C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   R rh = (R(j) + R(0.5)) * t.dr;
   C<R> sp = zero<R>(), sm = zero<R>();
@@ -437,9 +400,9 @@ QDS_NOINL void tr_interior(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp,
 // Outer half row: E_r by the shift with the Gamma_r source alone, B_theta by
 // the box scheme of Eq. em_r_open_bt over [r_{J-1/2}, r_{J+1/2}] x [t^n, t^{n+1}]
 // with its right side from time-n fields.
-template <class R, int M, bool SM, bool FAST, class FS>
-QDS_NOINL void tr_outer(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new,
-                     int lr_J, C<R> &tp, C<R> &tm) {
+template <class TT, class FS, class R = typename TT::Real>
+QDS_NOINL void tr_outer(const TT &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new, int lr_J, C<R> &tp,
+                        C<R> &tm) {
   const int c = t.x0 + lx, J = t.J;
   R rh = (R(J) + R(0.5)) * t.dr, rJ = R(J) * t.dr;
   C<R> gl = zero<R>(), gr = zero<R>();
@@ -460,9 +423,8 @@ QDS_NOINL void tr_outer(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, in
   tm = er_new - bt_new;
 }
 
-template <class R, int M, bool SM, bool FAST, class FS>
-QDS_NOINL void tt_update(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, int k, int lx, int lr,
-                      C<R> &tp, C<R> &tm) {
+template <class TT, class FS, class R = typename TT::Real>
+QDS_NOINL void tt_update(const TT &t, const FS &fs, int grp, int k, int lx, int lr, C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
   if (j == 0 && k != 1) { tp = zero<R>(); tm = zero<R>(); return; }
   C<R> sp = zero<R>(), sm = zero<R>();
@@ -494,20 +456,26 @@ QDS_NOINL void tt_update(const Tile<R, M, SM, FAST> &t, const FS &fs, int grp, i
 // centred at r_J (Eq. axion_r_ghost) with d_t phi taken half a step back.
 // ---------------------------------------------------------------------------
 // Provider of E_x^(n+1/2), B_x^(n+1/2) at face x0+lx (rows lr, lr+1): the
-// tile's intermediate planes (fused step, pass mode).
-template <class R, int M, bool SM, bool FAST>
+// accessor's intermediate planes.
+template <class TT>
 struct TileLeapVals {
-  const Tile<R, M, SM, FAST> &t;
+  using R = typename TT::Real;
+  const TT &t;
   int lx, lr;
   QDS_HD C<R> exn(int k, int dj) const { return t.sA(0, k, lx, lr + dj); }
   QDS_HD C<R> bxn(int k) const { return t.sA(1, k, lx, lr); }
 };
 
-template <class R, int M, bool SM, bool FAST, class NV>
-QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, const NV &nv) {
+// m_only >= 0: only the output mode m_only (the inputs of all modes are
+// still formed), so that the modes of a point can be spread over threads.
+template <class TT, class NV>
+QDS_NOINL void source_point(const TT &t, int lx, int lr, const NV &nv, int m_only = -1) {
+  using R = typename TT::Real;
+  constexpr int M = TT::kM;
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
-    for (int k = 0; k < M; k++) t.sG(k, lx, lr) = zero<R>();
+    for (int k = 0; k < M; k++)
+      if (m_only < 0 || k == m_only) t.sG(k, lx, lr) = zero<R>();
     return;
   }
   const bool top = (j == t.J);
@@ -541,6 +509,7 @@ QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, const
   const R rh = (R(j) + R(0.5)) * t.dr;
 #pragma unroll
   for (int m = 0; m < M; m++) {
+    if (m_only >= 0 && m != m_only) continue;
     C<R> S = conv<R, M>(m, eX, bX) + R(0.5) * (conv<R, M>(m, rp, qp) - conv<R, M>(m, rm, qm));
     S += t.srcv(t.sext, m, w, j);
     C<R> pc = t.face(PHI, m, w, j);
@@ -555,9 +524,9 @@ QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, const
   }
 }
 
-template <class R, int M, bool SM, bool FAST>
-QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
-  source_point(t, lx, lr, TileLeapVals<R, M, SM, FAST>{t, lx, lr});
+template <class TT>
+QDS_NOINL void source_point(const TT &t, int lx, int lr) {
+  source_point(t, lx, lr, TileLeapVals<TT>{t, lx, lr});
 }
 
 // ---------------------------------------------------------------------------
@@ -573,9 +542,10 @@ QDS_NOINL void source_point(const Tile<R, M, SM, FAST> &t, int lx, int lr) {
 // x0+lx: ns(pl, k, jj) = sum over cells x0+lx, x0+lx+1 of plane pl (0..3:
 // T_r^+, T_r^-, T_th^+, T_th^- at n+1; 4, 5: T_a^+, T_a^- at n+1/2) on row
 // jj, and pn(k, jj) = phi^(n+1) at the face on row jj.
-template <class R, int M, bool SM, bool FAST>
+template <class TT>
 struct TileNewVals {
-  const Tile<R, M, SM, FAST> &t;
+  using R = typename TT::Real;
+  const TT &t;
   int lx;
   QDS_HD C<R> ns(int pl, int k, int jj) const {
     const int l = jj - t.r0;
@@ -584,14 +554,18 @@ struct TileNewVals {
   QDS_HD C<R> pn(int k, int jj) const { return t.sP(k, lx, jj - t.r0); }
 };
 
-template <class R, int M, bool SM, bool FAST, class NV>
-QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R> (&jax)[M], C<R> (&jat)[M],
-                             const NV &nv) {
+// comp selects the components computed (bit 0: j_a,x, 1: j_a,r, 2:
+// j_a,theta), so that they can be spread over threads.
+template <class TT, class NV, class R = typename TT::Real, int M = TT::kM>
+QDS_NOINL void current_point(const TT &t, int lx, int lr, C<R> (&jax)[M], C<R> (&jat)[M], const NV &nv,
+                             int comp = 7) {
+  constexpr bool SM = TT::kSM;
   const int w = t.x0 + lx, j = t.r0 + lr;
   if (!t.face_ok(w) || j < 0 || j >= t.nr) {
     for (int k = 0; k < M; k++) {
       for (int q = 2; q < 5; q++)
-        if (SM || q > 2 || j == t.J) t.sJ(q, k, lx, lr) = zero<R>();
+        if ((comp >> (q - 2)) & 1)
+          if (SM || q > 2 || j == t.J) t.sJ(q, k, lx, lr) = zero<R>();
       jax[k] = jat[k] = zero<R>();
     }
     return;
@@ -601,7 +575,7 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R>
   const R gj = t.gj;
   const R ih = t.ih;
   // ---- j_a,x at (w, j, n) ----
-  {
+  if (comp & 1) {
     C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
@@ -665,7 +639,7 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R>
   // ---- j_a,r at (w, j + 1/2, n + 1/2) ----
   //   C{B_r, d_t phi} - C{E_th, d_x phi} = (1/2)(C{Tth+, Ta+} - C{Tth-, Ta-})
   // with T_theta averaged over cells w, w+1, rows j, j+1 and levels n, n+1.
-  {
+  if (comp & 2) {
     C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
@@ -698,7 +672,7 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R>
   // n+1; below the axis T_r^+-(-1/2) = 2i T_th^-+(0) - T_r^+-(1/2) (m = 1,
   // Eq. axis_Tr) and -T_r(1/2) otherwise, so on the axis the average is
   // i T_th^-+(0) for m = 1 and zero otherwise.
-  {
+  if (comp & 4) {
     C<R> a1[M], b1[M], a2[M], b2[M], a3[M], b3[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
@@ -733,371 +707,134 @@ QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R>
   }
 }
 
-template <class R, int M, bool SM, bool FAST>
-QDS_NOINL void current_point(const Tile<R, M, SM, FAST> &t, int lx, int lr, C<R> (&jax)[M], C<R> (&jat)[M]) {
-  current_point(t, lx, lr, jax, jat, TileNewVals<R, M, SM, FAST>{t, lx});
+template <class TT, class R = typename TT::Real, int M = TT::kM>
+QDS_NOINL void current_point(const TT &t, int lx, int lr, C<R> (&jax)[M], C<R> (&jat)[M]) {
+  current_point(t, lx, lr, jax, jat, TileNewVals<TT>{t, lx});
 }
 
 // ---------------------------------------------------------------------------
-// Warp-column passes.  A warp owns one window column (face and cell w) and
-// 32 consecutive rows, one row per lane, all modes per lane.  Values that a
-// pass computes and needs again on the neighbouring rows go through the
-// warp's slice of shared memory between the two phases of the pass:
-//   P1  phase 1: E_x, B_x leapfrog (ST_LEAP0);      phase 2: Gamma_a (ST_SOURCE)
-//   P2  phase 1: shift of T, T_a of cells w, w+1, and phi at face w (ST_SHIFT0);
-//       phase 2: j_a and the regenerated leapfrog of face w (ST_CURRENT).
-// The warp recomputes the shift of cell w+1 instead of reading it back, so
-// the two stages of each pass share one read of the state.  P1 outputs
-// lanes 0..30 (lane 31 gives E_x^(n+1/2) on the row above); a P2 warp based
-// at row max(r0-1, 0) outputs rows [r0, r0+30).
+// Pass-mode stages over single points (x0, r0) of the grid, one point per
+// thread with all modes; each stage is its own kernel (qds_kernels.cuh):
+//   ST_LEAP0    E_x, B_x to n+1/2 (into the new state)
+//   ST_SOURCE   Gamma_a at n (scratch plane 0)
+//   ST_SHIFT0   T, T_a to n+1 / n+1/2 and phi to n+1 (phi of face c is formed
+//               from T_a^(n+1/2) of cells c and c+1, the latter rebuilt here
+//               from Gamma_a of faces c, c+1)
+//   ST_CURRENT  j_a (scratch planes 1..3) and the regenerated leapfrog
+//   ST_SHIFT1   the regenerated shift
+//   ST_ZERO     moving window: the rear column of every field becomes the new
+//               (empty) front column once all passes have read it
 // ---------------------------------------------------------------------------
-template <class R, int M>
-struct P1Lane {
-  C<R> exn[M], bxn[M];
-};
-template <class R, int M>
-struct P2Lane {
-  C<R> ns[6][M];  // cell sums (w, w+1) of T_r^+-, T_th^+- (n+1), T_a^+- (n+1/2)
-  C<R> phn[M];    // phi^(n+1) at face w
-};
+enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_CURRENT, ST_SHIFT1, ST_ZERO, N_STAGE };
 
-template <class R, int M>
-struct P1Vals {
-  const P1Lane<R, M> *L;
-  int lane;
-  QDS_HD C<R> exn(int k, int dj) const { return L[lane + dj].exn[k]; }
-  QDS_HD C<R> bxn(int k) const { return L[lane].bxn[k]; }
-};
-template <class R, int M>
-struct P2Vals {
-  const P2Lane<R, M> *L;
-  int base;  // row of lane 0
-  QDS_HD C<R> ns(int pl, int k, int jj) const {
-#if defined(QDS_EMU)
-    QDS_CHECK(jj - base >= 0 && jj - base < 32, "P2 lane range");
-#endif
-    return L[jj - base].ns[pl][k];
-  }
-  QDS_HD C<R> pn(int k, int jj) const {
-#if defined(QDS_EMU)
-    QDS_CHECK(jj - base >= 0 && jj - base < 32, "P2 lane range");
-#endif
-    return L[jj - base].phn[k];
-  }
-};
-
-// P1 phase 1: E_x^(n+1/2), B_x^(n+1/2) of the lane's row (stored if out).
-template <class R, int M, bool FAST>
-QDS_HD void p1_leap(Tile<R, M, false, FAST> t, int lx, int lane, bool out, P1Lane<R, M> &my) {
-  const int w = t.x0 + lx, j = t.r0 + lane;
-  t.set_point(w);
-  const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
-#pragma unroll 1
-  for (int k = 0; k < M; k++) {
-    C<R> ex = zero<R>(), bx = zero<R>();
-    if (live) {
-      C<R> jtf = zero<R>();
-      if (j == t.J && !t.closed) jtf = R(0.5) * (t.srcv(t.jt, k, w, j) + t.srcv(t.jt, k, w + 1, j));
-      leap_point(t, 0, k, w, j, t.srcv(t.jx, k, w, j), jtf, ex, bx);
-    }
-    my.exn[k] = ex;
-    my.bxn[k] = bx;
-    if (out) {
-      t.sA(0, k, lx, lane) = ex;
-      t.sA(1, k, lx, lane) = bx;
-    }
-  }
-}
-
-// P1 phase 2: Gamma_a of the lane's row, E_x^(n+1/2) of the row above from
-// the next lane.
-template <class R, int M, bool FAST>
-QDS_HD void p1_source(Tile<R, M, false, FAST> t, int lx, int lane, bool out, const P1Lane<R, M> *L) {
-  if (!out || !(t.flags & (F_AXION | F_AREM))) return;
-  t.set_point(t.x0 + lx);
-  source_point(t, lx, lane, P1Vals<R, M>{L, lane});
-}
-
-// P2 phase 1: the shift of cells w and w+1 (T^(n+1), T_a^(n+1/2)) and phi^(n+1)
-// at face w; cell w and face w are stored if out.
-template <class R, int M, bool FAST>
-QDS_HD void p2_shift(Tile<R, M, false, FAST> t, int lx, int lane, bool out, P2Lane<R, M> &my) {
-  const int c = t.x0 + lx, j = t.r0 + lane;
-  const bool ax = (t.flags & (F_AXION | F_AREM)) != 0;
-  Faces0<R, M, false, FAST> fs{t};
-#pragma unroll 1
-  for (int k = 0; k < M; k++) {
-    C<R> ns[6], ap[2], am[2];
-    for (int q = 0; q < 6; q++) ns[q] = zero<R>();
-    for (int dc = 0; dc < 2; dc++) {
-      const int cc = c + dc, lxx = lx + dc;
-      t.set_point(cc);
-      const bool live = t.cell_ok(cc) && j >= 0 && j < t.nr;
-      C<R> tp = zero<R>(), tm = zero<R>(), up = zero<R>(), um = zero<R>();
-      ap[dc] = am[dc] = zero<R>();
-      if (live) {
-        if (j < t.J || t.closed) tr_interior(t, fs, 0, k, lxx, lane, tp, tm);
-        else {
-          C<R> ip, im_;
-          tr_interior(t, fs, 0, k, lxx, lane - 1, ip, im_);
-          tr_outer(t, fs, 0, k, lxx, R(0.5) * (ip - im_), lane, tp, tm);
-        }
-        tt_update(t, fs, 0, k, lxx, lane, up, um);
-        if (ax) {
-          ap[dc] = t.cell(TAP, k, cc - 1, j) + t.h * t.sG(k, lxx - 1, lane);
-          am[dc] = t.cell(TAM, k, cc + 1, j) + t.h * t.sG(k, lxx, lane);
-        }
-      }
-      ns[0] += tp; ns[1] += tm; ns[2] += up; ns[3] += um; ns[4] += ap[dc]; ns[5] += am[dc];
-      if (dc == 0 && out) {
-        t.store(TRP, k, c, j, tp); t.store(TRM, k, c, j, tm);
-        t.store(TTP, k, c, j, up); t.store(TTM, k, c, j, um);
-        if (ax) { t.store(TAP, k, c, j, ap[0]); t.store(TAM, k, c, j, am[0]); }
-      }
-    }
-    for (int q = 0; q < 6; q++) my.ns[q][k] = ns[q];
-    my.phn[k] = zero<R>();
-    if (ax) {
-      t.set_point(c);
-      const bool flive = t.face_ok(c) && j >= 0 && j < t.nr;
-      C<R> v = zero<R>(), po = zero<R>();
-      if (flive) {
-        po = t.face(PHI, k, c, j);
-        v = po + (R(0.25) * t.h) * (am[1] + am[0] + ap[1] + ap[0]);
-      }
-      my.phn[k] = v;
-      if (out) {
-        t.sP(k, lx, lane) = v;
-        if (j == t.J) t.store_prev(k, c, po);
-      }
-    }
-  }
-}
-
-// P2 phase 2: j_a at face w (the new-level sums of rows j-1..j+1 from the
-// neighbouring lanes) and the regenerated leapfrog of the face.
-template <class R, int M, bool FAST>
-QDS_HD void p2_current(Tile<R, M, false, FAST> t, int lx, int lane, bool out, const P2Lane<R, M> *L) {
-  if (!out || !(t.flags & F_AREM)) return;
-  const int w = t.x0 + lx, j = t.r0 + lane;
-  t.set_point(w);
-  C<R> jax[M], jat[M];
-  current_point(t, lx, lane, jax, jat, P2Vals<R, M>{L, t.r0});
-  const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
-#pragma unroll 1
-  for (int k = 0; k < M; k++) {
-    C<R> ex = zero<R>(), bx = zero<R>();
-    if (live) leap_point(t, 9, k, w, j, jax[k], jat[k], ex, bx);
-    t.sJ(0, k, lx, lane) = ex;
-    t.sJ(1, k, lx, lane) = bx;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Stage dispatcher.  The kernel runs every stage over all threads of the CTA
-// with a barrier in between; the host emulator runs them in the same order.
-// ---------------------------------------------------------------------------
-enum Stage { ST_LEAP0 = 0, ST_SOURCE, ST_SHIFT0, ST_PHI, ST_CURRENT, ST_LEAP1, ST_SHIFT1, N_STAGE, ST_ZERO = N_STAGE };
-
-template <class R, int M, bool SM, bool FAST = false>
-QDS_HD void run_stage(Tile<R, M, SM, FAST> t, int st, int tid, int nth) {
-  const Geo &g = t.g;
+template <class R, int M, bool FAST = false>
+QDS_HD void run_stage(Tile<R, M, FAST> t, int st) {
   const uint32_t fl = t.flags;
   const bool ax = (fl & (F_AXION | F_AREM)) != 0, ar = (fl & F_AREM) != 0;
-  // region of a stage: its halo region (fused) or the tile itself (pass mode)
-  auto region = [&](int x0_, int nx_, int r0_, int nr_, int &xa, int &nxr, int &ra, int &nrr) {
-    if (SM) { xa = x0_; nxr = nx_; ra = r0_; nrr = nr_; }
-    else { xa = 0; nxr = g.TX; ra = 0; nrr = g.TR; }
-  };
-  int xa, nxr, ra, nrr;
+  const int lx = 0, lr = 0;
+  if (!t.owned(lx, lr)) return;
   if (st == ST_ZERO) {
-    // pass mode, moving window: the rear column of every field becomes the
-    // new (empty) front column once all passes have read it
-    if (SM || !t.mw || t.x0 != 0) return;
+    if (!t.mw || t.x0 != 0) return;
     t.set_point(0);
-    for (int q = tid; q < g.TR; q += nth) {
-      const int j = t.r0 + q;
-      if (j >= t.nr) continue;
-      for (int f = 0; f < NFIELD; f++)
-        for (int k = t.k_lo; k < t.k_hi; k++) t.n[t.gidx(f, k, 0, j)] = zero<R>();
-      if (j == t.J)
-        for (int k = t.k_lo; k < t.k_hi; k++) t.n[(size_t)NFIELD * t.P + (size_t)k * t.nx + t.slot(0)] = zero<R>();
-    }
+    const int j = t.r0;
+    for (int f = 0; f < NFIELD; f++)
+      for (int k = 0; k < M; k++) t.n[t.gidx(f, k, 0, j)] = zero<R>();
+    if (j == t.J)
+      for (int k = 0; k < M; k++) t.n[(size_t)NFIELD * t.P + (size_t)k * t.nx + t.slot(0)] = zero<R>();
     return;
   }
   if (st == ST_LEAP0) {
-    region(g.a_x0(), g.a_nx(), g.a_r0(), g.a_nr(), xa, nxr, ra, nrr);
-    const int npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) {
-      const int lx = xa + q / nrr, lr = ra + q % nrr;
-      if (!SM && !t.owned(lx, lr)) continue;  // pass mode: points of the grid only
-      const int w = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(w);
-      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+    const int w = t.x0, j = t.r0;
+    t.set_point(w);
+    const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
-      for (int k = t.k_lo; k < t.k_hi; k++) {
-        C<R> ex = zero<R>(), bx = zero<R>();
-        if (live) {
-          C<R> jtf = zero<R>();
-          if (j == t.J && !t.closed) jtf = R(0.5) * (t.srcv(t.jt, k, w, j) + t.srcv(t.jt, k, w + 1, j));
-          leap_point(t, 0, k, w, j, t.srcv(t.jx, k, w, j), jtf, ex, bx);
-        }
-        t.sA(0, k, lx, lr) = ex;
-        t.sA(1, k, lx, lr) = bx;
-        if (SM && t.owned(lx, lr)) { t.store(EX, k, w, j, ex); t.store(BX, k, w, j, bx); }
+    for (int k = 0; k < M; k++) {
+      C<R> ex = zero<R>(), bx = zero<R>();
+      if (live) {
+        C<R> jtf = zero<R>();
+        if (j == t.J && !t.closed) jtf = R(0.5) * (t.srcv(t.jt, k, w, j) + t.srcv(t.jt, k, w + 1, j));
+        leap_point(t, 0, k, w, j, t.srcv(t.jx, k, w, j), jtf, ex, bx);
       }
+      t.sA(0, k, lx, lr) = ex;
+      t.sA(1, k, lx, lr) = bx;
     }
   } else if (st == ST_SOURCE) {
     if (!ax) return;
-    region(g.g_x0(), g.g_nx(), g.g_r0(), g.g_nr(), xa, nxr, ra, nrr);
-    const int npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) {
-      if (!SM && !t.owned(xa + q / nrr, ra + q % nrr)) continue;
-      t.set_point(t.x0 + xa + q / nrr);
-      source_point(t, xa + q / nrr, ra + q % nrr);
-    }
+    t.set_point(t.x0);
+    source_point(t, lx, lr);
   } else if (st == ST_SHIFT0) {
-    Faces0<R, M, SM, FAST> fs{t};
-    if (ax) region(g.t_x0(), g.t_nx(), g.t_r0(), g.t_nr(), xa, nxr, ra, nrr);
-    else { xa = 0; nxr = g.TX; ra = 0; nrr = g.TR; }
-    const int npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) {
-      const int lx = xa + q / nrr, lr = ra + q % nrr;
-      if (!SM && !t.owned(lx, lr)) continue;  // pass mode: points of the grid only
-      const int c = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(c);  // the shift reads cells c-1 .. c+1 (phi: c+2)
-      const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
-      const bool own = t.owned(lx, lr);
+    Faces0<Tile<R, M, FAST>> fs{t};
+    const int c = t.x0, j = t.r0;
+    t.set_point(c);  // the shift reads cells c-1 .. c+1 (phi: c+2)
+    const bool live = t.cell_ok(c) && j >= 0 && j < t.nr;
 #pragma unroll 1
-      for (int k = t.k_lo; k < t.k_hi; k++) {
-        C<R> tp = zero<R>(), tm = zero<R>(), up = zero<R>(), um = zero<R>();
-        C<R> ap = zero<R>(), am = zero<R>();
-        if (live) {
-          if (j < t.J || t.closed) tr_interior(t, fs, 0, k, lx, lr, tp, tm);
-          else {
-            C<R> ip, im_;
-            tr_interior(t, fs, 0, k, lx, lr - 1, ip, im_);
-            tr_outer(t, fs, 0, k, lx, R(0.5) * (ip - im_), lr, tp, tm);
-          }
-          tt_update(t, fs, 0, k, lx, lr, up, um);
-          if (ax) {
-            ap = t.cell(TAP, k, c - 1, j) + t.h * t.sG(k, lx - 1, lr);
-            am = t.cell(TAM, k, c + 1, j) + t.h * t.sG(k, lx, lr);
-          }
+    for (int k = 0; k < M; k++) {
+      C<R> tp = zero<R>(), tm = zero<R>(), up = zero<R>(), um = zero<R>();
+      C<R> ap = zero<R>(), am = zero<R>();
+      if (live) {
+        if (j < t.J || t.closed) tr_interior(t, fs, 0, k, lx, lr, tp, tm);
+        else {
+          C<R> ip, im_;
+          tr_interior(t, fs, 0, k, lx, lr - 1, ip, im_);
+          tr_outer(t, fs, 0, k, lx, R(0.5) * (ip - im_), lr, tp, tm);
         }
-        if (ax && SM) {
-          t.sT(0, k, lx, lr) = tp; t.sT(1, k, lx, lr) = tm;
-          t.sT(2, k, lx, lr) = up; t.sT(3, k, lx, lr) = um;
-          t.sT(4, k, lx, lr) = ap; t.sT(5, k, lx, lr) = am;
-        }
-        if (own) {
-          t.store(TRP, k, c, j, tp); t.store(TRM, k, c, j, tm);
-          t.store(TTP, k, c, j, up); t.store(TTM, k, c, j, um);
-          if (ax) { t.store(TAP, k, c, j, ap); t.store(TAM, k, c, j, am); }
-        }
-        if (ax && !SM) {
-          // pass mode: phi at face c (Eq. phi_update) from T_a^(n+1/2) of
-          // cells c (above) and c+1 (formed here from Gamma_a of faces c, c+1)
-          const bool flive = t.face_ok(c) && j >= 0 && j < t.nr;
-          C<R> v = zero<R>(), po = zero<R>();
-          if (flive) {
-            const C<R> ap1 = t.cell(TAP, k, c, j) + t.h * t.sG(k, lx, lr);
-            const C<R> am1 = t.cell(TAM, k, c + 2, j) + t.h * t.sG(k, lx + 1, lr);
-            po = t.face(PHI, k, c, j);
-            v = po + (R(0.25) * t.h) * (am1 + am + ap1 + ap);
-          }
-          t.sP(k, lx, lr) = v;
-          if (j == t.J) t.store_prev(k, c, po);
+        tt_update(t, fs, 0, k, lx, lr, up, um);
+        if (ax) {
+          ap = t.cell(TAP, k, c - 1, j) + t.h * t.sG(k, lx - 1, lr);
+          am = t.cell(TAM, k, c + 1, j) + t.h * t.sG(k, lx, lr);
         }
       }
-    }
-  } else if (st == ST_PHI) {
-    if (!ax || !SM) return;  // pass mode: part of ST_SHIFT0
-    region(g.p_x0(), g.p_nx(), g.p_r0(), g.p_nr(), xa, nxr, ra, nrr);
-    const int npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) {
-      const int lx = xa + q / nrr, lr = ra + q % nrr;
-      if (!SM && !t.owned(lx, lr)) continue;
-      const int w = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(w);
-      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
-#pragma unroll 1
-      for (int k = 0; k < M; k++) {
-        C<R> v = zero<R>();
-        if (live)
-          v = t.face(PHI, k, w, j) + (R(0.25) * t.h) * (t.sT(5, k, lx + 1, lr) + t.sT(5, k, lx, lr) +
-                                                       t.sT(4, k, lx + 1, lr) + t.sT(4, k, lx, lr));
-        t.sP(k, lx, lr) = v;
-        if (t.owned(lx, lr)) {
-          if (SM) t.store(PHI, k, w, j, v);
-          if (j == t.J) t.store_prev(k, w, live ? t.face(PHI, k, w, j) : zero<R>());
+      t.store(TRP, k, c, j, tp); t.store(TRM, k, c, j, tm);
+      t.store(TTP, k, c, j, up); t.store(TTM, k, c, j, um);
+      if (ax) {
+        t.store(TAP, k, c, j, ap); t.store(TAM, k, c, j, am);
+        // phi at face c (Eq. phi_update) from T_a^(n+1/2) of cells c (above)
+        // and c+1 (formed here from Gamma_a of faces c, c+1)
+        const bool flive = t.face_ok(c) && j >= 0 && j < t.nr;
+        C<R> v = zero<R>(), po = zero<R>();
+        if (flive) {
+          const C<R> ap1 = t.cell(TAP, k, c, j) + t.h * t.sG(k, lx, lr);
+          const C<R> am1 = t.cell(TAM, k, c + 2, j) + t.h * t.sG(k, lx + 1, lr);
+          po = t.face(PHI, k, c, j);
+          v = po + (R(0.25) * t.h) * (am1 + am + ap1 + ap);
         }
+        t.sP(k, lx, lr) = v;
+        if (j == t.J) t.store_prev(k, c, po);
       }
     }
   } else if (st == ST_CURRENT) {
     if (!ar) return;
-    region(g.j_x0(), g.j_nx(), g.j_r0(), g.j_nr(), xa, nxr, ra, nrr);
-    const int npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) {
-      const int lx = xa + q / nrr, lr = ra + q % nrr;
-      if (!SM && !t.owned(lx, lr)) continue;
-      const int w = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(w);
-      C<R> jax[M], jat[M];
-      current_point(t, lx, lr, jax, jat);
-      if (SM) continue;
-      // pass mode: the regenerated leapfrog (Sec. 2.2) of this face follows
-      // at once; it needs j_a,x and (outer row) j_a,theta of this point only
-      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
+    const int w = t.x0, j = t.r0;
+    t.set_point(w);
+    C<R> jax[M], jat[M];
+    current_point(t, lx, lr, jax, jat);
+    // the regenerated leapfrog (Sec. 2.2) of this face follows at once; it
+    // needs j_a,x and (outer row) j_a,theta of this point only
+    const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
 #pragma unroll 1
-      for (int k = 0; k < M; k++) {
-        C<R> ex = zero<R>(), bx = zero<R>();
-        if (live) leap_point(t, 9, k, w, j, jax[k], jat[k], ex, bx);
-        t.sJ(0, k, lx, lr) = ex;
-        t.sJ(1, k, lx, lr) = bx;
-      }
-    }
-  } else if (st == ST_LEAP1) {
-    if (!ar || !SM) return;  // pass mode: part of ST_CURRENT
-    region(g.j_x0(), g.j_nx(), g.j_r0(), g.j_nr(), xa, nxr, ra, nrr);
-    const int npt = nxr * nrr;
-    for (int q = tid; q < npt; q += nth) {
-      const int lx = xa + q / nrr, lr = ra + q % nrr;
-      if (!SM && !t.owned(lx, lr)) continue;
-      const int w = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(w);
-      const bool live = t.face_ok(w) && j >= 0 && j < t.nr;
-#pragma unroll 1
-      for (int k = 0; k < M; k++) {
-        C<R> ex = zero<R>(), bx = zero<R>();
-        if (live) leap_point(t, 9, k, w, j, t.sJ(2, k, lx, lr), t.sJ(4, k, lx, lr), ex, bx);
-        t.sJ(0, k, lx, lr) = ex;
-        t.sJ(1, k, lx, lr) = bx;
-        if (SM && t.owned(lx, lr)) { t.store(EX1, k, w, j, ex); t.store(BX1, k, w, j, bx); }
-      }
+    for (int k = 0; k < M; k++) {
+      C<R> ex = zero<R>(), bx = zero<R>();
+      if (live) leap_point(t, 9, k, w, j, jax[k], jat[k], ex, bx);
+      t.sJ(0, k, lx, lr) = ex;
+      t.sJ(1, k, lx, lr) = bx;
     }
   } else if (st == ST_SHIFT1) {
     if (!ar) return;
-    Faces1<R, M, SM, FAST> fs{t};
-    const int npt = g.TX * g.TR;
-    for (int q = tid; q < npt; q += nth) {
-      const int lx = q / g.TR, lr = q % g.TR;
-      if (!t.owned(lx, lr)) continue;
-      const int c = t.x0 + lx, j = t.r0 + lr;
-      t.set_point(c);
+    Faces1<Tile<R, M, FAST>> fs{t};
+    const int c = t.x0, j = t.r0;
+    t.set_point(c);
 #pragma unroll 1
-      for (int k = t.k_lo; k < t.k_hi; k++) {
-        C<R> tp, tm, up, um;
-        if (j < t.J || t.closed) tr_interior(t, fs, 9, k, lx, lr, tp, tm);
-        else {
-          C<R> ip, im_;
-          tr_interior(t, fs, 9, k, lx, lr - 1, ip, im_);
-          tr_outer(t, fs, 9, k, lx, R(0.5) * (ip - im_), lr, tp, tm);
-        }
-        tt_update(t, fs, 9, k, lx, lr, up, um);
-        t.store(TRP1, k, c, j, tp); t.store(TRM1, k, c, j, tm);
-        t.store(TTP1, k, c, j, up); t.store(TTM1, k, c, j, um);
+    for (int k = 0; k < M; k++) {
+      C<R> tp, tm, up, um;
+      if (j < t.J || t.closed) tr_interior(t, fs, 9, k, lx, lr, tp, tm);
+      else {
+        C<R> ip, im_;
+        tr_interior(t, fs, 9, k, lx, lr - 1, ip, im_);
+        tr_outer(t, fs, 9, k, lx, R(0.5) * (ip - im_), lr, tp, tm);
       }
+      tt_update(t, fs, 9, k, lx, lr, up, um);
+      t.store(TRP1, k, c, j, tp); t.store(TRM1, k, c, j, tm);
+      t.store(TTP1, k, c, j, up); t.store(TTM1, k, c, j, um);
     }
   }
 }

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libqds.so")
 
 AXION, AREM, MOVING_WINDOW, X_PERIODIC, R_CLOSED, FP32, SCALE_G = 1, 2, 4, 8, 16, 32, 64
-STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP, STEP_WARP_LEAP, STEP_FLAT, STEP_FLAT_MODES, STEP_QUEUE = range(8)
+STEP_DEFAULT, STEP_FLAT, STEP_MARCH = range(3)
 FIELDS = ("Trp", "Trm", "Ttp", "Ttm", "Ex", "Bx", "phi", "Tap", "Tam",
           "Trp1", "Trm1", "Ttp1", "Ttm1", "Ex1", "Bx1")
 N_FIELDS = 15
@@ -67,8 +67,8 @@ def lib():
             "qds_num_instances": (i, [H]),
             "qds_diagnostics_all": (i, [H, vp, vp]),
             "qds_set_tile": (i, [H, i, i]),
-            "qds_set_fused": (i, [H, i]),
             "qds_set_step_mode": (i, [H, i]),
+            "qds_status": (i, [H, vp]),
             "qds_step_launches": (i, [H]),
             "qds_get_tile": (i, [H, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
             "qds_free": (None, [H]),
@@ -228,40 +228,52 @@ class QDSSolver:
         _check(lib().qds_diagnostics_all(self.h, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
-    def set_fused(self, fused: bool):
-        _check(lib().qds_set_fused(self.h, int(bool(fused))))
-        self._mode = STEP_FUSED if fused else STEP_DEFAULT
+    def status(self, stream=None) -> int:
+        """Device error state (synchronises): 0, or the QDS_ERR_* code of a
+        timed-out bulk copy (4) or a non-finite value in the state (3)."""
+        return int(lib().qds_status(self.h, _stream_ptr(stream)))
 
-    def autotune(self, steps: int = 6, modes=None, stream=None) -> int:
-        """Time the pass-mode step implementations on this batch and keep
-        the fastest (the fused tile kernel is far slower and is not tried).
-        The trial steps advance the state: call before set_state."""
-        modes = modes or (STEP_FLAT, STEP_QUEUE, STEP_FLAT_MODES, STEP_STAGES, STEP_WARP_LEAP, STEP_WARP)
+    def check(self, stream=None):
+        """Raise QDSError if the device error state is set."""
+        _check(self.status(stream))
+
+    def autotune(self, steps: int = 4, candidates=None, stream=None):
+        """Time the step on this batch for the flat passes and for the
+        x-marching kernels over a set of work splits (rows per CTA, columns
+        per CTA) and keep the fastest.  The trial steps advance the state:
+        call before set_state.  Returns (mode, rows, cols)."""
+        if candidates is None:
+            candidates = [(STEP_MARCH, 0, c) for c in (64, 128, 256)]
+            candidates += [(STEP_MARCH, r, 128) for r in (32, 48)]
+            candidates += [(STEP_FLAT, 0, 0)]
         s = stream if stream is not None else torch.cuda.current_stream()
         best, best_t = None, None
         self.timings = {}
-        for m in modes:
-            self.set_step_mode(m)
-            self.step(2, stream=s)  # first launches of this mode
+        for cand in candidates:
+            mode, rows, cols = cand
+            try:
+                self.set_tile(rows, cols)
+            except QDSError:
+                continue
+            self.set_step_mode(mode)
+            self.step(2, stream=s)  # first launches of this configuration
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             self.step(steps, stream=s)
             e1.record(s)
             e1.synchronize()
             t = e0.elapsed_time(e1) / steps
-            self.timings[m] = t
+            self.timings[cand] = t
             if best_t is None or t < best_t:
-                best, best_t = m, t
-        self.set_step_mode(best)
-        self._mode = best
+                best, best_t = cand, t
+        mode, rows, cols = best
+        self.set_tile(rows, cols)
+        self.set_step_mode(mode)
         return best
 
     def step_mode_name(self) -> str:
-        names = {STEP_DEFAULT: "default", STEP_FUSED: "fused", STEP_STAGES: "stage passes",
-                 STEP_WARP: "warp-column passes", STEP_WARP_LEAP: "warp-column leapfrog + stage passes",
-                 STEP_FLAT: "stage passes over flat point ranges",
-                 STEP_FLAT_MODES: "flat stage passes, one (point, mode) per thread where modes decouple",
-                 STEP_QUEUE: "flat stage passes as persistent work-queue launches"}
+        names = {STEP_DEFAULT: "stage passes over flat point ranges (default)", STEP_FLAT: "stage passes over flat point ranges",
+                 STEP_MARCH: "x-marching kernels"}
         return names[getattr(self, "_mode", STEP_DEFAULT)]
 
     def step_launches(self) -> int:
@@ -269,15 +281,16 @@ class QDSSolver:
         return int(lib().qds_step_launches(self.h))
 
     def set_step_mode(self, mode: int):
-        """STEP_DEFAULT, STEP_FUSED, STEP_STAGES, STEP_WARP, STEP_WARP_LEAP, STEP_FLAT, STEP_FLAT_MODES
-        or STEP_QUEUE."""
+        """STEP_DEFAULT, STEP_FLAT or STEP_MARCH."""
         _check(lib().qds_set_step_mode(self.h, int(mode)))
         self._mode = int(mode)
 
-    def set_tile(self, tx, tr):
-        _check(lib().qds_set_tile(self.h, int(tx), int(tr)))
+    def set_tile(self, rows, cols):
+        """Work split of the x-marching kernels: radial rows per CTA (with the
+        halo; 0 = default) and window columns per CTA (0 = default)."""
+        _check(lib().qds_set_tile(self.h, int(rows), int(cols)))
 
     def tile(self):
         a, b, c, d = (ctypes.c_int() for _ in range(4))
         _check(lib().qds_get_tile(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
-        return dict(tx=a.value, tr=b.value, ntiles=c.value, smem=d.value)
+        return dict(rows=a.value, cols=b.value, ctas=c.value, smem=d.value)

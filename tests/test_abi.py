@@ -44,10 +44,13 @@ def _bytes(**kw):
 
 def test_state_bytes_of_valid_statements():
     up = lambda x: (x + 255) // 256 * 256
-    plane = 2 * 64 * 16
-    for flags, eb in ((0, 16), (Q.FP32, 8)):
-        # two ping-pong state copies (15 planes + phi_prev) and four scratch planes
-        assert _bytes(flags=flags) == 2 * up((15 * plane + 2 * 64) * eb) + up(4 * plane * eb)
+    for nr in (16, 17):
+        for flags, eb in ((0, 16), (Q.FP32, 8)):
+            # two ping-pong state copies (15 planes + phi_prev) and four scratch
+            # planes; in FP32 the row stride is nr rounded up to even
+            ld = nr + (nr & 1) if flags & Q.FP32 else nr
+            plane = 2 * 64 * ld
+            assert _bytes(nr=nr, flags=flags) == 2 * up((15 * plane + 2 * 64) * eb) + up(4 * plane * eb)
 
 
 @pytest.mark.parametrize("bad", [
@@ -69,10 +72,14 @@ def test_invalid_or_unstable_statements_are_rejected(bad):
 
 
 def test_largest_instance_below_the_element_limit_is_accepted():
-    """15 M nx nr + M nx < 2^31: with 4 modes and nx = 4096, nr = 8738 is
-    the largest grid that fits and 8739 the smallest that does not."""
+    """15 M nx ld + M nx < 2^31 (ld = nr, rounded up to even in FP32): with 4
+    modes and nx = 4096, nr = 8738 is the largest grid that fits and 8739
+    the smallest that does not (in FP32 too, whose stride of 8739 is 8740)."""
     assert _bytes(nx=4096, nr=8738, n_modes=4, dr=3.25) > 0
     assert _bytes(nx=4096, nr=8739, n_modes=4, dr=3.25) == 0
+    assert _bytes(nx=4096, nr=8738, n_modes=4, dr=3.25, flags=Q.FP32) > 0
+    assert _bytes(nx=4096, nr=8737, n_modes=4, dr=3.25, flags=Q.FP32) > 0
+    assert _bytes(nx=4096, nr=8739, n_modes=4, dr=3.25, flags=Q.FP32) == 0
 
 
 def test_stability_rule_matches_limits():

@@ -1,7 +1,9 @@
-"""The CUDA kernel's tile stages, compiled for the host with bounds checks on
-every global and shared-memory access (libqds_emu.so), against the FP64
-oracle: same arithmetic to rounding for every boundary mode, mode count and
-tile shape (including ragged tiles).  Runs without a GPU."""
+"""The CUDA step kernels' code, compiled for the host with bounds checks on
+the shared-memory and global accesses (libqds_emu.so), against the oracle:
+same arithmetic to rounding for every boundary mode and mode count, for the
+flat stage passes and for the x-marching kernels (bands of rows with radial
+halos, ragged segments of columns, the bulk copies' zero fill emulated).
+Runs without a GPU."""
 import ctypes
 
 import numpy as np
@@ -26,54 +28,55 @@ def emu():
     return _emu
 
 
-def run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, nsteps, TX, TR, nth=64, fused=True):
+FLAT, MARCH = 0, 1
+
+
+def run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, nsteps, mode=MARCH, rows=(24, 16), seg=7):
     dp = ctypes.POINTER(ctypes.c_double)
     out = np.zeros_like(buf)
     s = [None if a is None else np.ascontiguousarray(a, np.complex128) for a in src]
     P = lambda a: None if a is None else a.ctypes.data_as(dp)
     rc = emu().qds_emu_steps(M, P(buf), P(out), nx, nr, 1.0, dr, m_a, g, flags, *[P(a) for a in s],
-                             nsteps, TX, TR, nth, int(fused))
+                             nsteps, rows[0], rows[1], seg, mode)
     assert rc == 0
     return out
 
 
-# fused: 1 = fused tile kernel, 0 = warp-column passes, 2 = one pass per
-# stage over 8 x 32 tiles, 3 = the stage passes over flat point ranges,
-# 4 = as 3 with one (point, mode) per thread in the mode-independent passes
 @pytest.mark.parametrize("M,flags", parity_cases())
-@pytest.mark.parametrize("tile,fused", [((8, 32), 1), ((5, 3), 1), ((8, 32), 0), ((3, 4), 0), ((8, 32), 2),
-                                        ((3, 4), 2), ((8, 32), 3), ((8, 32), 4)])
-def test_emulated_kernel_matches_oracle_fp64(M, flags, tile, fused):
+@pytest.mark.parametrize("mode,rows,seg", [(FLAT, (24, 16), 7), (MARCH, (24, 16), 7), (MARCH, (64, 64), 128)])
+def test_emulated_kernels_match_oracle_fp64(M, flags, mode, rows, seg):
+    """nr = 11: one band per kernel; nx = 21 with 7-column segments gives
+    three CTAs along x, the first and last at the open (or periodic) ends."""
     nx, nr = 21, 11
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 100 + flags, M, nx, nr)
     ref = oracle_run(buf, M, nx, nr, dr, flags, 3, g=g, m_a=m_a, src=src)
-    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 3, *tile, nth=tile[0] * tile[1] if fused != 1 else 64,
-                  fused=fused)
+    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 3, mode=mode, rows=rows, seg=seg)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 1e-13, (name, e)
 
 
-@pytest.mark.parametrize("fused", [0, 3, 4])
 @pytest.mark.parametrize("M,flags", [c for c in parity_cases() if c[1] & 2])
-def test_warp_passes_span_several_row_tiles(M, flags, fused):
-    """nr = 70: P1 warps at rows 0, 31, 62 and P2 warps based at 0, 29, 59
-    (outputs from 0, 30, 60), so every seam between warps is crossed; nx = 30
-    gives interior (unchecked) and edge tiles; the flat passes (fused = 3)
-    cover 256 points per block across column boundaries."""
-    nx, nr = 30, 70
+@pytest.mark.parametrize("rows,seg", [((24, 16), 5), ((32, 24), 9), ((24, 24), 30)])
+def test_march_bands_and_segments(M, flags, rows, seg):
+    """nr = 45 odd (padded row stride in FP32), several bands per kernel
+    (first kernel: rows [0, 20), [20, 36), [36, 45) for 24 rows per CTA;
+    second: 14-row first band, 12-row bands), segments of 5, 9 and 30
+    columns over nx = 30 (a ragged last segment, one CTA for the whole x)."""
+    nx, nr = 30, 45
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 17 + flags, M, nx, nr)
     ref = oracle_run(buf, M, nx, nr, dr, flags, 2, g=g, m_a=m_a, src=src)
-    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 2, 8, 32, nth=256, fused=fused)
+    got = run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, 2, rows=rows, seg=seg)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 1e-13, (name, e)
 
 
-@pytest.mark.parametrize("fused", [1, 0, 2, 3, 4])
+@pytest.mark.parametrize("mode", [FLAT, MARCH])
 @pytest.mark.parametrize("M", [2, 3])
-def test_emulated_kernel_fp32_scaled(M, fused):
-    nx, nr = 24, 12
+@pytest.mark.parametrize("nr", [12, 13])
+def test_emulated_kernels_fp32_scaled(M, mode, nr):
+    nx = 24
     dr, g = stable_dr(M), 1e-6
     flags = 1 | 2 | 4  # axion, regenerated fields, moving window
     buf, src = random_case(7 + M, M, nx, nr)
@@ -83,6 +86,6 @@ def test_emulated_kernel_fp32_scaled(M, fused):
     buf[9 * n:15 * n] *= g * g     # regenerated fields ~ g^2
     src[3] = None
     ref = oracle_run(buf, M, nx, nr, dr, flags, 4, g=g, src=src)
-    got = run_emu(M, buf, nx, nr, dr, 0.0, g, flags | 32, src, 4, 8, 16, nth=128 if fused != 1 else 64, fused=fused)
+    got = run_emu(M, buf, nx, nr, dr, 0.0, g, flags | 32, src, 4, mode=mode, rows=(24, 16), seg=6)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 2e-6, (name, e)

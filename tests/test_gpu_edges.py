@@ -1,5 +1,5 @@
 """Edge cases of the GPU step against the oracle: the smallest grids the
-library accepts (nx = 8, nr = 4), every step implementation on them, zero
+library accepts (nx = 8, nr = 4), both step implementations on them, zero
 steps, an all-zero state (stays zero), and a batch mixing the smallest grid
 with large ragged ones."""
 import numpy as np
@@ -26,7 +26,7 @@ ALL = 1 | 2 | 4
 
 @pytest.mark.parametrize("M", [1, 2])
 @pytest.mark.parametrize("flags", [ALL, 1 | 2 | 8, 1 | 2 | 16])
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_smallest_grid_every_step_mode(M, flags, mode):
     Q = _Q()
     nx, nr = 8, 4

@@ -1,5 +1,6 @@
-"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
-the same seeded inputs.  FP64: relative L2 <= 1e-12 per field group.  FP32
+"""GPU parity: the CUDA path (through the C ABI) against the oracle on the
+same seeded inputs, for both step implementations (flat stage passes and
+the x-marching kernels).  FP64: relative L2 <= 1e-12 per field group.  FP32
 (axion and regenerated fields carried as phi/g, E1/g^2): relative L2 <= 1e-5
 for the EM fields and <= 1e-4 for the axion group and the axion-regenerated
 fields (these are driven by j_a ~ phi, so they inherit the axion's error)."""
@@ -11,13 +12,13 @@ pytestmark = pytest.mark.gpu
 
 from paper_2609_03550_b300 import inputs as I  # noqa: E402
 from paper_2609_03550_b300 import qds as Q  # noqa: E402
-from tests._helpers import (fp32_tolerance, group_errors, oracle_run, parity_cases,  # noqa: E402
+from tests._helpers import (amplitude_error, group_errors, oracle_run, parity_cases,  # noqa: E402
                             random_case, reference_and_tolerance, stable_dr)
 
 DEV = "cuda:0"
 
 
-MODES = [Q.STEP_STAGES, Q.STEP_FUSED, Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_FLAT, Q.STEP_FLAT_MODES, Q.STEP_QUEUE]
+MODES = [Q.STEP_FLAT, Q.STEP_MARCH]
 
 
 def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=None, mode=Q.STEP_DEFAULT):
@@ -25,7 +26,7 @@ def gpu_run(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, src=None, tile=No
     s = Q.QDSSolver(p, device=DEV)
     if tile:
         s.set_tile(*tile)
-        mode = Q.STEP_FUSED
+        mode = Q.STEP_MARCH
     s.set_step_mode(mode)
     s.set_state(torch.from_numpy(buf).to(DEV))
     kw = {}
@@ -52,29 +53,37 @@ def test_fp64_parity_random_states(M, flags, mode):
             assert e < 1e-12, (nsteps, name, e)
 
 
-@pytest.mark.parametrize("mode", [Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_FLAT, Q.STEP_FLAT_MODES, Q.STEP_QUEUE])
+@pytest.mark.parametrize("tile", [(24, 7), (32, 16), (48, 45), (0, 0)])
 @pytest.mark.parametrize("M,flags", [c for c in parity_cases() if c[1] & 2])
-def test_fp64_parity_warp_seams(M, flags, mode):
-    """nr = 70 puts three warps on every column (seams at rows 31/62 for the
-    first warp pass and 30/60 for the second); nx = 45 has interior tiles."""
+def test_fp64_parity_march_bands_and_segments(M, flags, tile):
+    """x-marching kernels over several bands of rows (nr = 70) and segments
+    of columns (nx = 45: 7, 16, 45 columns per CTA, ragged last segments),
+    and the default split."""
     nx, nr = 45, 70
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 31 + flags, M, nx, nr)
     ref = oracle_run(buf, M, nx, nr, dr, flags, 4, g=g, m_a=m_a, src=src)
-    got, _ = gpu_run(buf, M, nx, nr, dr, flags, 4, g=g, m_a=m_a, src=src, mode=mode)
+    got, _ = gpu_run(buf, M, nx, nr, dr, flags, 4, g=g, m_a=m_a, src=src, tile=tile)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 1e-12, (name, e)
 
 
-@pytest.mark.parametrize("tile", [(4, 8), (8, 16), (16, 8), (3, 5)])
-def test_fp64_parity_tile_shapes(tile):
-    M, nx, nr, flags = 3, 45, 27, 1 | 2 | 4
-    dr = stable_dr(M)
-    buf, src = random_case(11, M, nx, nr)
-    ref = oracle_run(buf, M, nx, nr, dr, flags, 5, g=0.2, src=src)
-    got, _ = gpu_run(buf, M, nx, nr, dr, flags, 5, g=0.2, src=src, tile=tile)
-    for name, e in group_errors(got, ref, M, nx, nr).items():
-        assert e < 1e-12, (name, e)
+@pytest.mark.parametrize("nr", [33, 64, 101])
+def test_fp32_march_odd_rows_and_bands(nr):
+    """FP32 with an odd row count (padded row stride) and bands of 24 rows."""
+    M, nx, flags = 3, 40, 1 | 2 | 4
+    dr, g = stable_dr(M), 1e-6
+    buf, src = random_case(90 + nr, M, nx, nr)
+    n = M * nx * nr
+    buf[6 * n:9 * n] *= g
+    buf[15 * n:] *= g
+    buf[9 * n:15 * n] *= g * g
+    src[3] = None
+    ref = oracle_run(buf, M, nx, nr, dr, flags, 6, g=g, src=src)
+    got, _ = gpu_run(buf, M, nx, nr, dr, flags | Q.FP32, 6, g=g, src=src, tile=(24, 9))
+    e = group_errors(got, ref, M, nx, nr)
+    print("fp32 march errors", nr, e)
+    assert e["em"] < 1e-5 and e["arem"] < 1e-4 and e["axion"] < 1e-4, e
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -92,6 +101,7 @@ def test_fp32_scaled_parity(M, mode):
     ref = oracle_run(buf, M, nx, nr, dr, flags, 10, g=g, src=src)
     got, _ = gpu_run(buf, M, nx, nr, dr, flags | Q.FP32, 10, g=g, src=src, mode=mode)
     e = group_errors(got, ref, M, nx, nr)
+    print("fp32 errors", M, mode, e)
     assert e["em"] < 1e-5 and e["arem"] < 1e-4 and e["axion"] < 1e-4, e
 
 
@@ -171,7 +181,12 @@ def test_diagnostics_match_oracle():
 @pytest.mark.parametrize("which", ["driven_wake", "two_colour"])
 def test_full_size_first_steps(which):
     """Full-size grids of the benchmark workloads, in the launch
-    configuration the benchmark uses, three steps against the oracle."""
+    configuration the benchmark uses, three steps against the oracle.  FP64:
+    1e-12 (the two-colour axion group against ten times the FP64-vs-long-
+    double distance of the oracle itself, printed).  FP32: EM fields 1e-5;
+    the axion and regenerated fields of co-propagating vacuum pulses start
+    from zero and are a small residue of products, so their error is read as
+    the amplitude error (max |difference| / max |reference|), 1e-4."""
     if which == "driven_wake":
         wl = I.driven_wake()
         flags = 0
@@ -180,18 +195,21 @@ def test_full_size_first_steps(which):
         flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
     buf = wl.initial_state()
     ref, tol = reference_and_tolerance(buf, wl.M, wl.nx, wl.nr, wl.dr, flags, 3, g=wl.g)
+    print("fp64 tolerances", tol)
     for prec in (0, Q.FP32):
         got, _ = gpu_run(buf, wl.M, wl.nx, wl.nr, wl.dr, flags | prec, 3, g=wl.g)
         e = group_errors(got, ref, wl.M, wl.nx, wl.nr)
+        print(which, "fp32" if prec else "fp64", "rel L2", e)
         if prec == 0:
             assert e["em"] < 1e-12, e
             if flags & Q.AXION:
                 assert e["axion"] < tol["axion"] and e["arem"] < tol["arem"], (e, tol)
         else:
-            t32 = fp32_tolerance(tol)
-            assert e["em"] < t32["em"], (e, t32)
+            assert e["em"] < 1e-5, e
             if flags & Q.AXION:
-                assert e["axion"] < t32["axion"] and e["arem"] < t32["arem"], (e, t32)
+                amp = amplitude_error(got, ref, wl.M, wl.nx, wl.nr)
+                print(which, "fp32 amplitude error", amp)
+                assert amp["axion"] < 1e-4 and amp["arem"] < 1e-4, amp
 
 
 def test_batched_uneven_instances_match_single_runs():
@@ -212,16 +230,16 @@ def test_batched_uneven_instances_match_single_runs():
 
 
 def test_autotune_then_parity():
-    """The autotuner times the pass-mode implementations and keeps one; the
-    solve that follows still matches the oracle."""
+    """The autotuner times the flat passes and several work splits of the
+    x-marching kernels and keeps one; the solve that follows still matches
+    the oracle."""
     M, nx, nr, flags = 3, 48, 40, 1 | 2 | 4
     dr, g = stable_dr(M), 0.2
     buf, src = random_case(5, M, nx, nr)
     p = Q.Params(nx, nr, M, dr, g=g, flags=flags)
     s = Q.QDSSolver([p, p], device=DEV)
     best = s.autotune(steps=2)
-    assert best in (Q.STEP_STAGES, Q.STEP_FLAT, Q.STEP_FLAT_MODES, Q.STEP_WARP, Q.STEP_WARP_LEAP, Q.STEP_QUEUE)
-    assert len(s.timings) == 6
+    assert best in s.timings and len(s.timings) >= 2
     for i in range(2):
         s.set_state(torch.from_numpy(buf).to(DEV), i)
     s.step(5)
