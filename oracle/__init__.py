@@ -17,6 +17,8 @@ import numpy as np
 from . import build as _build
 
 AXION, AREM, MOVING_WINDOW, X_PERIODIC, R_CLOSED = 1, 2, 4, 8, 16
+# test reading only: the outer phi row by the paper's printed three-level update
+AXION_R_PRINTED = 1024
 FIELDS = ("Trp", "Trm", "Ttp", "Ttm", "Ex", "Bx", "phi", "Tap", "Tam",
           "Trp1", "Trm1", "Ttp1", "Ttm1", "Ex1", "Bx1")
 N_FIELDS = len(FIELDS)

@@ -66,7 +66,9 @@ enum {
   ORA_AREM = 2,           /* advance the axion-regenerated fields (Sec. 2.2) */
   ORA_MOVING_WINDOW = 4,  /* window moves one cell per step                   */
   ORA_X_PERIODIC = 8,     /* periodic x (test mode for dispersion pins)       */
-  ORA_R_CLOSED = 16       /* conducting wall / Neumann axion at r = nr dr     */
+  ORA_R_CLOSED = 16,      /* conducting wall / Neumann axion at r = nr dr     */
+  ORA_AXION_R_PRINTED = 1024  /* test reading: the outer phi row by the paper's
+                                 three-level update as printed (see below)    */
 };
 
 enum { F_TRP, F_TRM, F_TTP, F_TTM, F_EX, F_BX, F_PHI, F_TAP, F_TAM,
@@ -502,6 +504,42 @@ static int step_once(const P *p, cplx *S, const cplx *jx, const cplx *jrc, const
         size_t q = (size_t)m * nx + f;
         nphiprev[q] = real_face(p, f) ? phi[ix(p, m, f, J)] : 0;
       }
+    if ((flags & ORA_AXION_R_PRINTED) && !closed) {
+      /* Test reading, used only to pin why the default reading above
+       * departs from the paper: the outermost phi row by the explicit
+       * three-level update exactly as printed (Eq. axion_r_update, Sec. 3.2),
+       *   A phi^{n+1} = -(1/dt^2 - c/(dr dt) - c/(2 r_N dt)) phi^{n-1}
+       *                 + (2/dt^2) phi^n + R^n,
+       *   A = 1/dt^2 + c/(dr dt) + c/(2 r_N dt),
+       *   R^n = c^2 (phi_{i+1} - 2 phi_i + phi_{i-1})/dx^2 - m^2 c^2 phi/r_N^2
+       *         + (2 c^2/dr^2)(phi_{N-1} - phi_N) - m_a^2 phi + g S_a,
+       * with r_N the radius of the outermost half row.  "The same update at
+       * the auxiliary half time level" is read as T_a^{+-} of that row
+       * following from phi: T_a^{+-} = d_t phi -+ d_x phi at (cell, n+1/2),
+       * centred from the faces around the cell and the levels n, n+1. */
+      const double rN = r_half(p, J);
+      const double A = 1.0 / (h * h) + 1.0 / (dr * h) + 1.0 / (2.0 * rN * h);
+      const double Bc = 1.0 / (h * h) - 1.0 / (dr * h) - 1.0 / (2.0 * rN * h);
+      for (int m = 0; m < M; m++)
+        for (int f = 0; f < nx; f++) {
+          size_t q = ix(p, m, f, J);
+          if (!real_face(p, f)) continue;
+          cplx pc = phi[q];
+          cplx lapx = (facev(p, phi, m, f + 1, J) - 2.0 * pc + facev(p, phi, m, f - 1, J)) / (h * h);
+          cplx R = lapx - (double)(m * m) / (rN * rN) * pc + (2.0 / (dr * dr)) * (phi[ix(p, m, f, J - 1)] - pc) -
+                   m_a * m_a * pc + g * Sa[q];
+          nphi[q] = (-Bc * phiprev[(size_t)m * nx + f] + (2.0 / (h * h)) * pc + R) / A;
+        }
+      for (int m = 0; m < M; m++)
+        for (int c = 0; c < nx; c++) {
+          cplx dt = 0.5 * ((facev(p, nphi, m, c - 1, J) - facev(p, phi, m, c - 1, J)) +
+                           (facev(p, nphi, m, c, J) - facev(p, phi, m, c, J))) / h;
+          cplx dx = 0.5 * ((facev(p, nphi, m, c, J) - facev(p, nphi, m, c - 1, J)) +
+                           (facev(p, phi, m, c, J) - facev(p, phi, m, c - 1, J))) / h;
+          nTap[ix(p, m, c, J)] = dt - dx;
+          nTam[ix(p, m, c, J)] = dt + dx;
+        }
+    }
     free(ghost);
   }
 

@@ -390,3 +390,140 @@ def test_closed_box_energy_has_no_drift():
     E = np.array(E)
     assert np.abs(E).max() < 0.01
     assert abs(E[-1] - E[7]) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# 11. The outer radial axion row (Sec. 3.2).  The paper's explicit three-level
+#     update of the outermost phi row (Eq. axion_r_update) is unstable with
+#     c dt = dx: its x-Laplacian runs at Courant number one, and any radial
+#     term then pushes the x-Nyquist mode out of the unit circle.  (a) For
+#     phi = (-1)^i lambda^n on the outer row, the interior row held at zero,
+#     the printed update gives
+#       A lambda^2 + (2/dt^2 + 2/dr^2 + m^2/r_N^2 + m_a^2) lambda + B = 0,
+#     A, B = 1/dt^2 +- c/(dr dt) +- c/(2 r_N dt), with a root |lambda| > 1.
+#     (b) The oracle's one-step map with that row update (test reading
+#     AXION_R_PRINTED, T_a of the row following from phi) has |lambda| > 1 at
+#     the paper's mesh dr = 5 dx, while the default reading (outgoing ghost
+#     with d_t phi half a step back, the row advanced by the interior
+#     transport) stays on the unit circle.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dr,m", [(5.0, 0), (5.0, 1), (2.0, 0), (10.0, 0)])
+def test_printed_outer_axion_row_update_has_a_growing_root(dr, m):
+    h, nr = 1.0, 40
+    rN = (nr - 0.5) * dr
+    A = 1 / h**2 + 1 / (dr * h) + 1 / (2 * rN * h)
+    B = 1 / h**2 - 1 / (dr * h) - 1 / (2 * rN * h)
+    mid = 2 / h**2 + 2 / dr**2 + m * m / rN**2
+    roots = np.roots([A, mid, B])
+    assert np.abs(roots).max() > 1.05, roots
+
+
+@pytest.mark.parametrize("nr", [4, 7])
+def test_printed_outer_axion_row_is_unstable_in_the_scheme(nr):
+    p = dict(nx=4, nr=nr, M=1, h=1.0, dr=5.0, m_a=0.0, flags=oracle.X_PERIODIC | oracle.AXION)
+    stable = np.abs(np.linalg.eigvals(_mode_matrix(p, 1, 4, nr, 0, [6, 7, 8], prev=True))).max()
+    p["flags"] |= oracle.AXION_R_PRINTED
+    printed = np.abs(np.linalg.eigvals(_mode_matrix(p, 1, 4, nr, 0, [6, 7, 8], prev=True))).max()
+    print("max |lambda|: default reading", stable, "printed update", printed)
+    assert stable < 1 + 1e-10
+    assert printed > 1.1
+
+
+# ---------------------------------------------------------------------------
+# 12. Reflection of the outer radial boundaries (Sec. 3.2, Eqs.
+#     em_r_open_bx/bt and axion_r_sommerfeld).  A radially outgoing pulse
+#     (x-uniform, so normally incident) is run on nr rows and on 2 nr rows;
+#     on the inner rows the two runs differ only by what the boundary at
+#     nr dr sends back, until the far boundary's reflection could return.
+#     The reflected amplitude must be a few per cent of the outgoing one.
+# ---------------------------------------------------------------------------
+def _radial_pulse_runs(field, m, dr=2.0, nr=40, nx=4, steps=90, r0=50.0, sigma=6.0):
+    out = []
+    for n_r in (nr, 2 * nr):
+        st = oracle.State(m + 1, nx, n_r)
+        r_half = (np.arange(n_r) + 0.5) * dr
+        prof = np.exp(-((r_half - r0) / sigma) ** 2)
+        st[field][m] = prof[None, :]
+        flags = oracle.X_PERIODIC | (oracle.AXION if field == "phi" else 0)
+        p = dict(nx=nx, nr=n_r, M=m + 1, h=1.0, dr=dr, flags=flags)
+        hist = []
+        for _ in range(steps):
+            oracle.step(p, st)
+            hist.append(st.fields[:, m, 0, :nr].copy())
+        out.append(np.array(hist))
+    return out
+
+
+# The axion condition (Eq. axion_r_sommerfeld) has no curvature term, so a
+# cylindrical pulse of width sigma is partly reflected, of order sigma/(2R):
+# 8 % at R = 80 (sigma = 6), 4 % at R = 160, where the discrete part
+# dominates (it stays at 4 % for R = 320).  The EM condition carries the
+# 1/(2r) terms (Eqs. em_r_open_bx/bt): 1.6-1.8 %, 1 % at R = 160.
+@pytest.mark.parametrize("field,m,nr,bound", [("Bx", 0, 40, 0.03), ("Bx", 1, 40, 0.03), ("phi", 0, 40, 0.1),
+                                              ("phi", 1, 40, 0.1), ("phi", 0, 80, 0.05), ("Bx", 0, 80, 0.015)])
+def test_outer_radial_boundary_reflects_little(field, m, nr, bound):
+    r0 = 50.0 if nr == 40 else 130.0
+    small, big = _radial_pulse_runs(field, m, nr=nr, r0=r0)
+    obs = slice(0, nr - 10)  # rows 20 dr and more inside the outer boundary
+    fi = {"Bx": [4, 5, 0, 1, 2, 3], "phi": [6, 7, 8]}[field]
+    diff = np.abs(small[:, fi][..., obs] - big[:, fi][..., obs]).max()
+    # amplitude of the outgoing pulse as it crosses the last 10 rows of the
+    # small box in the big run
+    ref = np.abs(big[:, fi][..., nr - 10:nr]).max()
+    print(field, m, nr, "reflected / outgoing amplitude", diff / ref)
+    assert diff / ref < bound
+
+
+# ---------------------------------------------------------------------------
+# 13. Energy diagnostic (Sec. 4.1, U = int (1/2)(|E|^2 + |B|^2) dV, and the
+#     axion energy of Sec. 4.3) against closed forms: a field uniform over the
+#     box has energy density (1/2)|F|^2 for m = 0 and (1/4)|F|^2 for m >= 1
+#     (the theta average of Re(F e^{-i m theta})^2), times the volume it
+#     occupies: a disc of radius nr dr for half-row fields (r_{j+1/2}) and of
+#     radius (nr - 1/2) dr for integer-row fields (r_j, the axis cell being the
+#     disc of radius dr/2), times the length nx dx.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("m", [0, 1, 2])
+def test_energy_diagnostic_matches_closed_forms(m):
+    M, nx, nr, dr, h = m + 1, 6, 9, 1.7, 1.0
+    L = nx * h
+    disc_half = math.pi * (nr * dr) ** 2
+    disc_int = math.pi * ((nr - 0.5) * dr) ** 2
+    dens = 0.5 if m == 0 else 0.25
+    a, b, e, f = 0.7 - 0.2j, 1.3 + 0.4j, -0.9 + 0.1j, 0.35 + 0.8j
+    if m == 0:
+        a, b, e, f = a.real, b.real, e.real, f.real
+    cases = [
+        ("Trp", a, disc_half, 0.5),   # T_r^+ alone: E_r = B_th = a/2 (half rows)
+        ("Ttm", b, disc_int, 0.5),    # T_th^- alone: E_th = -B_r = b/2 (integer rows)
+        ("Ex", e, disc_int, 1.0),     # integer rows
+        ("Bx", f, disc_half, 1.0),    # half rows
+    ]
+    for name, val, area, amp in cases:
+        st = oracle.State(M, nx, nr)
+        st[name][m] = val
+        d = oracle.diagnostics(dict(nx=nx, nr=nr, M=M, h=h, dr=dr), st, profile=True)
+        # E_r and B_th (or E_th and B_r) each carry amp * val
+        n_comp = 2 if name.startswith("T") else 1
+        want = dens * n_comp * abs(amp * val) ** 2 * area * L
+        assert abs(d["em0"] - want) <= 1e-12 * want, (name, d["em0"], want)
+        # U(x) of Sec. 4.1 counts the transverse fields only, per unit length
+        u_want = want / L if name.startswith("T") else 0.0
+        assert np.allclose(d["profile"], u_want, rtol=1e-12, atol=1e-14 * want), (name, d["profile"], u_want)
+    # axion: T_a^+ = T_a^- = t gives d_t phi = t, d_x phi = 0; phi = p with
+    # mass m_a adds (1/2) m_a^2 |p|^2 (m = 0); half rows
+    t, pv, ma = 0.6 + 0.3j, 0.8 - 0.5j, 0.37
+    if m == 0:
+        t, pv = t.real, pv.real
+    st = oracle.State(M, nx, nr)
+    st["Tap"][m] = t
+    st["Tam"][m] = t
+    d = oracle.diagnostics(dict(nx=nx, nr=nr, M=M, h=h, dr=dr, m_a=ma), st)
+    want = dens * abs(t) ** 2 * disc_half * L
+    assert abs(d["axion"] - want) <= 1e-12 * want, (d["axion"], want)
+    if m == 0:
+        st = oracle.State(M, nx, nr)
+        st["phi"][0] = pv
+        d = oracle.diagnostics(dict(nx=nx, nr=nr, M=M, h=h, dr=dr, m_a=ma), st)
+        want = dens * ma * ma * abs(pv) ** 2 * disc_half * L
+        assert abs(d["axion"] - want) <= 1e-12 * want, (d["axion"], want)
