@@ -4,9 +4,11 @@ Workload (default): the batched vacuum two-colour scan - 512 independent
 EM + axion + axion-regenerated-field solves of uneven size (nx 512..4096,
 nr 32..256, 2..4 modes, from seed 2), FP32 with the axion and regenerated
 fields carried as phi/g and E1/g^2, moving window.  One "step" advances every
-instance by one time step (one launch per mode count).  Inputs (72 GB of
-state) are far larger than L2.  The FP64 plain path is timed on the same
-workload; the FP64 CPU oracle is timed on a bounded sample on the host cores.
+instance by one time step.  The state (36 GB in FP32) is far larger than L2.
+The FP64 plain path is timed on the same workload, and FP32 is compared with
+FP64 over the full 1000 steps on a sample of the instances; the FP64 CPU
+oracle is timed on a bounded sample on the host cores.  With N GPUs the 512
+instances are split into N disjoint subsets of equal cost (strong scaling).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl qds|reference]
 """
@@ -120,6 +122,7 @@ def build_solver(wls, flags, device, autotune=False):
     from paper_2609_03550_b300 import qds as Q
     params = [Q.Params(w.nx, w.nr, w.M, w.dr, g=w.g, m_a=w.m_a, flags=flags) for w in wls]
     s = Q.QDSSolver(params, device=device)
+    s.timings = {}
     if autotune:
         s.autotune()  # before the initial state is set: the trial steps advance the state
     for i, w in enumerate(wls):
@@ -137,6 +140,38 @@ def time_steps(s, K, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3
+
+
+def accuracy(wls, flags, device, steps):
+    """FP32 against FP64 on the GPU after ``steps`` steps of the given
+    instances (the FP64 GPU path matches the oracle to 1e-12 in the tests):
+    relative L2 of the EM fields and amplitude errors (max |diff| / max |FP64|)
+    of the axion and regenerated groups, worst over the instances."""
+    import numpy as np
+    import torch
+    from paper_2609_03550_b300 import qds as Q
+    s64 = build_solver(wls, flags, device)
+    s32 = build_solver(wls, flags | Q.FP32, device)
+    s64.step(steps)
+    s32.step(steps)
+    torch.cuda.synchronize()
+    worst = {"em_rel_l2": 0.0, "axion_rel_l2": 0.0, "arem_rel_l2": 0.0, "axion_amplitude": 0.0,
+             "arem_amplitude": 0.0}
+    for i, w in enumerate(wls):
+        a = s32.get_state(i).cpu().numpy()
+        b = s64.get_state(i).cpu().numpy()
+        n = w.M * w.nx * w.nr
+        for name, lo, hi in (("em", 0, 6), ("axion", 6, 9), ("arem", 9, 15)):
+            d, r = a[lo * n:hi * n] - b[lo * n:hi * n], b[lo * n:hi * n]
+            worst[f"{name}_rel_l2"] = max(worst[f"{name}_rel_l2"], float(np.linalg.norm(d) / np.linalg.norm(r)))
+            if name != "em":
+                worst[f"{name}_amplitude"] = max(worst[f"{name}_amplitude"],
+                                                 float(np.abs(d).max() / np.abs(r).max()))
+    del s32, s64
+    torch.cuda.empty_cache()
+    worst.update({"steps": steps, "instances": [w.name for w in wls], "against": "FP64 on the GPU",
+                  "bounds": {"em_rel_l2": 1e-5, "axion_amplitude": 1e-4, "arem_amplitude": 1e-4}})
+    return worst
 
 
 def cpu_baseline(wls, flags, budget_s):
@@ -250,7 +285,7 @@ def run_reference(args):
 
 def run_qds(args):
     import torch
-    from paper_2609_03550_b300.ranks import Ranks, job_throughput
+    from paper_2609_03550_b300.ranks import Ranks, job_throughput, shard
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
@@ -259,7 +294,10 @@ def run_qds(args):
 
     from paper_2609_03550_b300 import inputs as I
     from paper_2609_03550_b300 import qds as Q
-    wls = I.batched_scan()[: args.instances]  # every rank runs its own scan (weak scaling)
+    scan = I.batched_scan()[: args.instances]
+    total_units = sum(w.cell_modes() for w in scan)
+    mine = shard([w.cell_modes() for w in scan], world)[rank]  # this rank's instances
+    wls = [scan[i] for i in mine]
     units = sum(w.cell_modes() for w in wls)
     flags = Q.AXION | Q.AREM | Q.MOVING_WINDOW
     stream = torch.cuda.current_stream(device)
@@ -268,17 +306,22 @@ def run_qds(args):
     s = build_solver(wls, flags | Q.FP32, device, autotune=not args.no_autotune)
     tile = s.tile()
     tile["step_mode"] = s.step_mode_name()
+    tile["autotune_ms_per_step"] = {f"{['default', 'flat', 'march'][m]} rows={r} cols={c}": round(t, 3)
+                                    for (m, r, c), t in s.timings.items()}
     launches_per_step = s.step_launches()
     s.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
-    barrier()
-    t32 = time_steps(s, args.steps, stream)
+    reps = []
+    for _ in range(args.repeats):
+        barrier()
+        reps.append(max_over_ranks(time_steps(s, args.steps, stream)))
     barrier()
     clk = clocks.stop()
-    t32 = max_over_ranks(t32)
+    t32 = statistics.median(reps)
     step32 = t32 / args.steps
+    status = s.status()
 
     # ---------------- end to end through the public API ----------------
     # per step: advance every instance, compute every instance's energies
@@ -299,6 +342,13 @@ def run_qds(args):
     del s
     torch.cuda.empty_cache()
 
+    # ---------------- accuracy of FP32 against FP64 ----------------
+    acc = None
+    if not args.no_accuracy:
+        sample = [w for w in wls if w.name in {f"scan_{i}" for i in range(args.accuracy_instances)}]
+        if sample:
+            acc = accuracy(sample, flags, device, sample[0].steps)
+
     # ---------------- FP64 plain on the same workload ----------------
     fp64 = None
     if not args.no_fp64:
@@ -307,10 +357,12 @@ def run_qds(args):
         barrier()
         t64 = max_over_ranks(time_steps(s64, args.fp64_steps, stream))
         step64 = t64 / args.fp64_steps
-        fp64 = {"value": world * units / step64, "unit": UNIT, "ms_per_step": 1e3 * step64,
-                "steps": args.fp64_steps, "dtype": "f64",
+        fp64 = {"value": job_throughput(total_units, step64), "unit": UNIT, "ms_per_step": 1e3 * step64,
+                "steps": args.fp64_steps, "dtype": "f64", "step_mode": s64.step_mode_name(),
                 "hbm_gbs_algorithmic": units * BYTES_PER_UNIT["f64"] / step64 / 1e9,
-                "fp32_speedup": step64 / step32}
+                "fp32_speedup": step64 / step32,
+                "fp32_accuracy_at_this_speedup": None if acc is None else
+                {k: acc[k] for k in ("em_rel_l2", "axion_amplitude", "arem_amplitude")}}
         del s64
         torch.cuda.empty_cache()
 
@@ -329,25 +381,30 @@ def run_qds(args):
     if world == 1 and not args.no_cpu:
         cpu = cpu_baseline(wls, flags, args.cpu_seconds)
     out = {
-        "metric": METRIC, "value": job_throughput(units, world, step32), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_throughput(total_units, step32), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step32,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "batched_vacuum_two_colour_scan_512_seed2" if len(wls) == 512
-                   else f"batched_vacuum_two_colour_scan_first{len(wls)}_seed2", "instances": len(wls),
-                   "cell_modes_per_step": units, "modes": "2..4", "nx": "513..4085", "nr": "32..254",
-                   "precision": "FP32, phi/g and E1/g^2", "parallelism": f"instances, {world} GPU(s)",
+        "config": {"workload": "batched_vacuum_two_colour_scan_512_seed2" if len(scan) == 512
+                   else f"batched_vacuum_two_colour_scan_first{len(scan)}_seed2", "instances": len(scan),
+                   "cell_modes_per_step": total_units, "modes": "2..4", "nx": "513..4085", "nr": "32..254",
+                   "precision": "FP32, phi/g and E1/g^2", "parallelism": f"instances split over {world} GPU(s)",
                    "l2": f"inputs larger than L2 ({units * BYTES_PER_UNIT['f32'] / 2e9:.1f} GB FP32 state per GPU)",
+                   "timing": f"median of {args.repeats} timed runs of {args.steps} steps (ms per step: "
+                             + ", ".join(f"{1e3 * t / args.steps:.2f}" for t in reps) + ")",
                    "tile": tile},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "the pass kernels of one step, all mode counts (the step reads and writes "
-                               "the state once in algorithmic terms)",
+                     "kernel": "the kernels of one step, all mode counts (the step reads and writes the state "
+                               "once in algorithmic terms)",
                      "bytes_per_unit": BYTES_PER_UNIT["f32"], "peak_kind": peak_kind},
+        "accuracy": acc,
+        "device_status": status,
         "fp64_plain": fp64,
-        "e2e": {"value": world * units * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": 0,
+        "e2e": {"value": total_units * args.steps / te2e, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(diag_host.numel() * 8), "finite": e2e_finite,
-                "per_step": "step + diagnostics of all instances + device-to-host read"},
+                "per_step": "step + energies of all instances + device-to-host read (the vacuum scan has no "
+                            "per-step inputs)"},
         "gpu_launches": args.steps * launches_per_step,
         "adjoint": adj,
         "clocks": clk,
@@ -370,6 +427,10 @@ def main():
     ap.add_argument("--instances", type=int, default=512, help="first N instances (profiling runs only)")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default step mode (profiling runs)")
+    ap.add_argument("--repeats", type=int, default=5, help="timed runs of --steps steps (the median is reported)")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--accuracy-instances", type=int, default=8,
+                    help="FP32 vs FP64 over the full run on the scan's first N instances")
     ap.add_argument("--adjoint-steps", type=int, default=8000)
     ap.add_argument("--adjoint-every", type=int, default=90)
     args = ap.parse_args()

@@ -160,7 +160,8 @@ int qds_step_launches(const qds_handle *h);
 
 /* Work split of QDS_STEP_MARCH (the autotuner's knobs): rows = radial rows
  * per CTA including the halo (24..256, rounded down to a multiple of 8, at
- * most 256 / n_modes; 0 = the default that fits two CTAs per SM), cols =
+ * most 256 / n_modes and at most what fits in 227 KB of shared memory;
+ * 0 = the default that fits two CTAs per SM), cols =
  * window columns per CTA (>= 4; 0 = 128).  qds_get_tile reports the rows of
  * the first kernel of the first mode count, the columns, the CTAs of one
  * step and that kernel's shared memory in bytes. */
@@ -172,6 +173,15 @@ int qds_get_tile(qds_handle *h, int *rows, int *cols, int *ntiles, int *smem_byt
  * they store; the energy reductions flag a non-finite energy).  Synchronises
  * stream.  qds_diagnostics returns the same codes. */
 int qds_status(qds_handle *h, void *stream);
+
+/* Test hook for the failure path: with on != 0 every x-marching CTA of the
+ * following steps withholds its first bulk copy, so that its bounded wait
+ * on that column runs out (about a second); the CTA then sets the timeout
+ * bit, lets its other copies land and exits, and qds_status reports
+ * QDS_ERR_TIMEOUT.  The fields of those steps are not valid.  on = 0
+ * restores normal operation (qds_set_state clears the error bits).
+ * Asynchronous on stream. */
+int qds_test_withhold_copy(qds_handle *h, int on, void *stream);
 
 void qds_free(qds_handle *h);
 const char *qds_last_error(void);

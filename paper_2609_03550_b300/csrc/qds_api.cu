@@ -373,6 +373,8 @@ int build_march(qds_handle *h) {
       G.d_items[kind] = nullptr;
       int RB = h->rows_override > 0 ? h->rows_override : default_rows(h->fp32, kind, G.M);
       RB = std::min(RB, std::min(256 / G.M, h->fp32 ? 256 : 128)) / 8 * 8;
+      // a requested row count larger than fits in shared memory is clamped
+      while (RB > 8 && march_smem(h->fp32, kind, G.M, RB) > 227 * 1024) RB -= 8;
       const int halo = kind == 0 ? kHalo1 : kHalo2;
       if (RB < 2 * halo + 8) return fail(QDS_ERR_INVALID_ARG, "march rows per CTA too small");
       G.rows[kind] = RB;
@@ -730,6 +732,13 @@ int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream) {
 int qds_status(qds_handle *h, void *stream) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
   return read_status(h, (cudaStream_t)stream);
+}
+
+int qds_test_withhold_copy(qds_handle *h, int on, void *stream) {
+  if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
+  set_test_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(h->d_ctrl, on ? 1u : 0u);
+  CU(cudaGetLastError());
+  return QDS_OK;
 }
 
 int qds_diagnostics_i(qds_handle *h, int i, double *out_host, double *profile_dev, void *stream) {

@@ -12,7 +12,7 @@ namespace qds {
 struct Ctrl {
   unsigned long long step;  // steps taken since the last state import
   unsigned int err;         // device-side error flags (kErr*)
-  unsigned int pad;
+  unsigned int test;        // test hook: bit 0 withholds the first bulk copy of each x-marching CTA
 };
 
 // Per-instance prefactors of the energies (diag_final_all_kernel).
@@ -88,6 +88,10 @@ static __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {
 
 static __global__ void reset_kernel(Ctrl *ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) { ctrl->step = 0; ctrl->err = 0; }
+}
+
+static __global__ void set_test_kernel(Ctrl *ctrl, unsigned int bits) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->test = bits;
 }
 
 // Canonical complex128 layout <-> working storage (precision, row stride,

@@ -468,8 +468,12 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const Inst<R> *__restrict
     march_issue<R, M, KIND>(mm, par, sm + s2 * geo.slot, it.rb0, march_coord(c, t.nx, t.s, t.per), &bar[s2], bytes,
                             geo.RB);
   };
+  // (test hook: with bit 0 of ctrl->test set the first column is never
+  // fetched, so that its bounded wait runs out)
+  const bool withhold = (ctrl->test & 1u) != 0;
   if (tid == 0)
-    for (int c = L0; c <= C1 && c < L0 + 3; c++) issue(c);
+    for (int c = L0; c <= C1 && c < L0 + 3; c++)
+      if (!(withhold && c == L0)) issue(c);
   bool bad = false;  // a non-finite value was stored
   for (int L = L0; L <= L1; L++) {
     // column L (if any) has landed; a copy that did not complete within the
@@ -485,7 +489,8 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const Inst<R> *__restrict
       if (tid == 0) {
         atomicOr(&ctrl->err, kErrTimeout);
         for (int c = L; c <= C1 && c < L + 3; c++)
-          mbar_wait(&bar[(c + 4 * kRing) % kRing], (unsigned)(((c - L0) / kRing) & 1));
+          if (!(withhold && c == L0))
+            mbar_wait(&bar[(c + 4 * kRing) % kRing], (unsigned)(((c - L0) / kRing) & 1));
       }
       __syncthreads();
       return;

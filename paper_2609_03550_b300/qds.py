@@ -69,6 +69,7 @@ def lib():
             "qds_set_tile": (i, [H, i, i]),
             "qds_set_step_mode": (i, [H, i]),
             "qds_status": (i, [H, vp]),
+            "qds_test_withhold_copy": (i, [H, i, vp]),
             "qds_step_launches": (i, [H]),
             "qds_get_tile": (i, [H, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
             "qds_free": (None, [H]),
@@ -232,6 +233,11 @@ class QDSSolver:
         """Device error state (synchronises): 0, or the QDS_ERR_* code of a
         timed-out bulk copy (4) or a non-finite value in the state (3)."""
         return int(lib().qds_status(self.h, _stream_ptr(stream)))
+
+    def test_withhold_copy(self, on: bool, stream=None):
+        """Test hook: the x-marching CTAs withhold their first bulk copy, so
+        that the bounded wait runs out and qds_status reports a timeout."""
+        _check(lib().qds_test_withhold_copy(self.h, int(bool(on)), _stream_ptr(stream)))
 
     def check(self, stream=None):
         """Raise QDSError if the device error state is set."""

@@ -1,11 +1,12 @@
 """Rank plumbing of the multi-GPU benchmark.
 
-The batched scan shards by instance: every rank advances its own independent
-solves (weak scaling: the work per GPU is fixed as the rank count grows), so
-the data path has no collective.  Only a barrier around the timed region and
-the maximum of the per-rank times cross ranks; the whole-job throughput is
-the units of all ranks divided by that maximum.  Ranks are read from the
-torchrun environment (RANK, WORLD_SIZE, LOCAL_RANK, MASTER_ADDR/PORT).
+The batched scan shards by instance: the independent solves of one scan are
+split into disjoint subsets of nearly equal cost, one per rank (strong
+scaling: the job is fixed and each GPU takes 1/N of it), so the data path
+has no collective.  Only a barrier around the timed region and the maximum
+of the per-rank times cross ranks; the whole-job throughput is the units of
+the whole scan divided by that maximum.  Ranks are read from the torchrun
+environment (RANK, WORLD_SIZE, LOCAL_RANK, MASTER_ADDR/PORT).
 """
 from __future__ import annotations
 
@@ -48,6 +49,20 @@ class Ranks:
             self.dist = None
 
 
-def job_throughput(units_per_rank: float, world: int, t_max: float) -> float:
-    """Whole-job units per second: every rank's units over the slowest rank's time."""
-    return world * units_per_rank / t_max
+def shard(costs, world: int):
+    """Split items of the given costs into ``world`` disjoint subsets of
+    nearly equal total cost (longest first, each to the lightest subset);
+    returns the item indices of each subset, in increasing order."""
+    loads = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda k: (-costs[k], k)):
+        r = min(range(world), key=lambda q: (loads[q], q))
+        parts[r].append(i)
+        loads[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
+def job_throughput(total_units: float, t_max: float) -> float:
+    """Whole-job units per second: the units of all ranks over the slowest
+    rank's time."""
+    return total_units / t_max

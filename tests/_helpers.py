@@ -1,4 +1,6 @@
 """Shared test helpers (no method arithmetic)."""
+import math
+
 import numpy as np
 
 import oracle
@@ -67,6 +69,28 @@ def reference_and_tolerance(buf, M, nx, nr, dr, flags, nsteps, g=0.0, m_a=0.0, s
     r64 = oracle_run(buf, M, nx, nr, dr, flags, nsteps, g=g, m_a=m_a, src=src, extended=False)
     floor = group_errors(r64, ref, M, nx, nr)
     return ref, {k: max(base, 10.0 * v) for k, v in floor.items()}
+
+
+def phase_matched_scales(wl, T):
+    """Amplitudes the two-colour pair of workload wl would drive in T time
+    units if phase matched (manufactured resonance of Sec. 2.2: a source
+    S0 cos(kx - wt) grows phi as g S0 t / (2 w)): phi ~ g A1 A2 T / (2 dw)
+    with A1, A2 the peak pulse fields and dw = w1 - w2, and the regenerated
+    fields, driven by j_a ~ g A1 dw phi, ~ g A1 dw phi T / 2."""
+    l1, l2 = wl.lasers[0], wl.lasers[1]
+    w1, w2 = 2 * math.pi / l1.lam, 2 * math.pi / l2.lam
+    A1, A2 = l1.a0 * w1, l2.a0 * w2
+    phi = wl.g * A1 * A2 * T / (2 * (w1 - w2))
+    return phi, wl.g * A1 * (w1 - w2) * phi * T / 2
+
+
+def scaled_errors(got, ref, wl, T):
+    """Max |got - ref| of phi and of the regenerated fields over their
+    phase-matched scales (phase_matched_scales)."""
+    n = wl.M * wl.nx * wl.nr
+    s_phi, s_e1 = phase_matched_scales(wl, T)
+    return (float(np.abs(got[6 * n:7 * n] - ref[6 * n:7 * n]).max() / s_phi),
+            float(np.abs(got[9 * n:15 * n] - ref[9 * n:15 * n]).max() / s_e1))
 
 
 def amplitude_error(got, ref, M, nx, nr):

@@ -74,3 +74,55 @@ def test_batch_with_smallest_and_ragged_grids():
         got = s.get_state(i).cpu().numpy()
         for name, e in group_errors(got, ref, M, nx, nr).items():
             assert e < 1e-12, (i, name, e)
+
+
+def test_nonfinite_state_is_reported():
+    """A NaN current makes the state non-finite: the x-marching kernels flag
+    it at once (qds_status), the flat passes through the energy reduction
+    (qds_diagnostics); a new state clears the flag."""
+    Q = _Q()
+    M, nx, nr = 2, 40, 12
+    for mode in (Q.STEP_MARCH, Q.STEP_FLAT):
+        p = Q.Params(nx, nr, M, stable_dr(M), g=0.5, flags=ALL)
+        s = Q.QDSSolver(p, device=DEV)
+        s.set_step_mode(mode)
+        buf, _ = random_case(4, M, nx, nr)
+        s.set_state(torch.from_numpy(buf).to(DEV))
+        s.step(2)
+        assert s.status() == 0
+        jx = torch.zeros((M, nx, nr), dtype=torch.complex128, device=DEV)
+        jx[0, 20, 3] = float("nan")
+        s.step(1, jx=jx)
+        if mode == Q.STEP_MARCH:
+            assert s.status() == 3  # QDS_ERR_NONFINITE
+        with pytest.raises(Q.QDSError, match="non-finite"):
+            s.diagnostics()
+        assert s.status() == 3
+        s.set_state(torch.from_numpy(buf).to(DEV))
+        s.step(2)
+        assert s.status() == 0
+        assert np.isfinite(s.diagnostics()["em0"])
+
+
+def test_bulk_copy_wait_runs_out_and_reports_a_timeout():
+    """The bounded wait of the x-marching kernels: with the test hook the
+    first column of every CTA is never fetched; the wait runs out, the CTA
+    sets the timeout bit and exits, qds_status reports QDS_ERR_TIMEOUT, and
+    the context stays usable (the next solve matches the oracle)."""
+    Q = _Q()
+    M, nx, nr, flags = 2, 24, 10, ALL
+    p = Q.Params(nx, nr, M, stable_dr(M), g=0.3, flags=flags)
+    s = Q.QDSSolver(p, device=DEV)
+    s.set_step_mode(Q.STEP_MARCH)
+    buf, _ = random_case(6, M, nx, nr)
+    s.set_state(torch.from_numpy(buf).to(DEV))
+    s.test_withhold_copy(True)
+    s.step(1)
+    assert s.status() == 4  # QDS_ERR_TIMEOUT
+    s.test_withhold_copy(False)
+    s.set_state(torch.from_numpy(buf).to(DEV))
+    s.step(3)
+    assert s.status() == 0
+    ref = oracle_run(buf, M, nx, nr, stable_dr(M), flags, 3, g=0.3)
+    for name, e in group_errors(s.get_state().cpu().numpy(), ref, M, nx, nr).items():
+        assert e < 1e-12, (name, e)
