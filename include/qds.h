@@ -110,12 +110,25 @@ int qds_set_state(qds_handle *h, const void *src_dev, void *stream);
 /* Export the canonical complex128 state (device pointer), asynchronous. */
 int qds_get_state(qds_handle *h, void *dst_dev, void *stream);
 
-/* Advance nsteps steps with constant sources (src may be NULL); calls of
- * >= 16 steps replay a captured CUDA graph.  Asynchronous on stream: a batch
- * with several mode counts runs each mode count's kernels on a stream of the
- * handle, forked from and joined back to `stream` by events, so the call is
- * ordered on `stream` like a single launch. */
+/* Advance nsteps steps; calls of >= 16 steps replay a captured CUDA graph.
+ * src != NULL sets the sources of every instance for this and later calls
+ * to these arrays, the same every step (all pointers NULL: no sources; a
+ * batch takes only that, its sources are set per instance); src == NULL
+ * keeps the sources set before (qds_set_sources_i or an earlier call).
+ * Asynchronous on stream: a batch with several mode counts runs each mode
+ * count's kernels on a stream of the handle, forked from and joined back to
+ * `stream` by events, so the call is ordered on `stream` like a single
+ * launch. */
 int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream);
+
+/* Sources of instance i for the following qds_step calls (src NULL: none).
+ * Step k of a call (k = 0, 1, ...) reads every array of src advanced by
+ * k * stride elements (complex values of the working precision; stride 0:
+ * the same arrays every step), so that a call of n steps can take n steps
+ * of a driven run at once: with stride M*nx*nr the arrays are [n][M][nx][nr].
+ * The arrays must stay valid until the stream has executed those steps.
+ * Uploads the descriptor (synchronises stream). */
+int qds_set_sources_i(qds_handle *h, int i, const qds_sources *src, long long stride, void *stream);
 
 /* Energies into out_host[4] = {EM energy, axion energy, regenerated EM
  * energy, int (E0.E1 + B0.B1) dV} (mode-weighted volume integrals, FP64,

@@ -67,7 +67,14 @@ def _params_with_g(p: Q.Params, g: float) -> Q.Params:
 
 def _advance(solver, spec, n0, count, keep=None):
     """Advance the solver ``count`` steps from step index n0; if ``keep`` is
-    a list, append the canonical state before every step."""
+    a list, append the canonical state before every step.  Without ``keep``
+    and with a source object that can fill a block of steps (``fill``), the
+    block runs as one call with per-step sources (graph replays)."""
+    if keep is None and spec.sources is not None and hasattr(spec.sources, "fill"):
+        bufs = spec.sources.fill(n0, count)
+        solver.set_sources(0, *bufs, per_step=True)
+        solver.step(count)
+        return
     for n in range(n0, n0 + count):
         if keep is not None:
             keep.append(solver.get_state())

@@ -206,9 +206,9 @@ struct qds_handle {
   int mode = QDS_STEP_DEFAULT;  // step implementation (qds_set_step_mode)
   int seg = 0;                  // march: columns per CTA (0: default)
   int rows_override = 0;        // march: rows per CTA (0: default)
-  // graph cache: key (jx, jr, jt, sext, nsteps, stream)
-  std::map<std::tuple<const void *, const void *, const void *, const void *, int, void *>, cudaGraphExec_t> graphs;
-  const void *cur_src[4] = {nullptr, nullptr, nullptr, nullptr};
+  // graph cache: key (steps per graph, stream); the kernels read the source
+  // pointers from the device descriptors at run time
+  std::map<std::tuple<int, void *>, cudaGraphExec_t> graphs;
 };
 
 namespace {
@@ -241,15 +241,36 @@ void fill_inst(qds_handle *h, int i, const qds_params &p, void *base) {
   h->h_inst[i].assign((char *)&I, (char *)&I + sizeof I);
 }
 
+// Sources of instance i (NULL clears), stride elements apart from step to
+// step of a qds_step call (0: the same arrays every step).
 template <class R>
-void set_sources(qds_handle *h, const qds_sources *src) {
-  for (int i = 0; i < h->n_inst; i++) {
-    Inst<R> *I = reinterpret_cast<Inst<R> *>(h->h_inst[i].data());
-    I->jx = src ? (const C<R> *)src->jx : nullptr;
-    I->jr = src ? (const C<R> *)src->jr : nullptr;
-    I->jt = src ? (const C<R> *)src->jth : nullptr;
-    I->sext = src ? (const C<R> *)src->s_ext : nullptr;
+void set_sources_i(qds_handle *h, int i, const qds_sources *src, long long stride) {
+  Inst<R> *I = reinterpret_cast<Inst<R> *>(h->h_inst[i].data());
+  I->jx = src ? (const C<R> *)src->jx : nullptr;
+  I->jr = src ? (const C<R> *)src->jr : nullptr;
+  I->jt = src ? (const C<R> *)src->jth : nullptr;
+  I->sext = src ? (const C<R> *)src->s_ext : nullptr;
+  I->sstride = stride;
+}
+
+bool sources_equal(const qds_handle *h, int i, const qds_sources *src, long long stride) {
+  const void *s4[4] = {src ? src->jx : nullptr, src ? src->jr : nullptr, src ? src->jth : nullptr,
+                       src ? src->s_ext : nullptr};
+  if (h->fp32) {
+    const Inst<float> *I = reinterpret_cast<const Inst<float> *>(h->h_inst[i].data());
+    return I->jx == s4[0] && I->jr == s4[1] && I->jt == s4[2] && I->sext == s4[3] && I->sstride == stride;
   }
+  const Inst<double> *I = reinterpret_cast<const Inst<double> *>(h->h_inst[i].data());
+  return I->jx == s4[0] && I->jr == s4[1] && I->jt == s4[2] && I->sext == s4[3] && I->sstride == stride;
+}
+
+bool any_strided(const qds_handle *h) {
+  for (int i = 0; i < h->n_inst; i++) {
+    const long long s = h->fp32 ? reinterpret_cast<const Inst<float> *>(h->h_inst[i].data())->sstride
+                                : reinterpret_cast<const Inst<double> *>(h->h_inst[i].data())->sstride;
+    if (s) return true;
+  }
+  return false;
 }
 
 size_t inst_size(const qds_handle *h) { return h->fp32 ? sizeof(Inst<float>) : sizeof(Inst<double>); }
@@ -680,21 +701,40 @@ int qds_get_state_i(qds_handle *h, int i, void *dst, void *stream) {
 
 int qds_get_state(qds_handle *h, void *dst, void *stream) { return qds_get_state_i(h, 0, dst, stream); }
 
+int qds_set_sources_i(qds_handle *h, int i, const qds_sources *src, long long stride, void *stream) {
+  if (!h || i < 0 || i >= h->n_inst) return fail(QDS_ERR_INVALID_ARG, "bad handle or instance");
+  if (stride < 0) return fail(QDS_ERR_INVALID_ARG, "negative source stride");
+  if (sources_equal(h, i, src, stride)) return QDS_OK;
+  if (h->fp32) set_sources_i<float>(h, i, src, stride);
+  else set_sources_i<double>(h, i, src, stride);
+  return upload_inst(h, (cudaStream_t)stream);
+}
+
 int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream) {
   if (!h) return fail(QDS_ERR_INVALID_ARG, "NULL handle");
   if (nsteps < 0) return fail(QDS_ERR_INVALID_ARG, "nsteps < 0");
   if (nsteps == 0) return QDS_OK;
-  if (src && h->n_inst != 1 && (src->jx || src->jr || src->jth || src->s_ext))
-    return fail(QDS_ERR_UNSUPPORTED, "sources are per instance; batched handles take none");
   cudaStream_t st = (cudaStream_t)stream;
-  const void *s4[4] = {src ? src->jx : nullptr, src ? src->jr : nullptr, src ? src->jth : nullptr,
-                       src ? src->s_ext : nullptr};
-  if (std::memcmp(s4, h->cur_src, sizeof s4) != 0) {
-    if (h->fp32) set_sources<float>(h, src);
-    else set_sources<double>(h, src);
-    int rc = upload_inst(h, st);
-    if (rc) return rc;
-    std::memcpy(h->cur_src, s4, sizeof s4);
+  if (src) {
+    // constant sources for this call (every instance of a batch: none)
+    const bool any = src->jx || src->jr || src->jth || src->s_ext;
+    if (any && h->n_inst != 1)
+      return fail(QDS_ERR_UNSUPPORTED, "a batch takes per-instance sources (qds_set_sources_i)");
+    bool same = true;
+    for (int i = 0; i < h->n_inst; i++) same = same && sources_equal(h, i, any ? src : nullptr, 0);
+    if (!same) {
+      for (int i = 0; i < h->n_inst; i++) {
+        if (h->fp32) set_sources_i<float>(h, i, any ? src : nullptr, 0);
+        else set_sources_i<double>(h, i, any ? src : nullptr, 0);
+      }
+      int rc = upload_inst(h, st);
+      if (rc) return rc;
+    }
+  }
+  // per-step sources: the steps of this call count from here
+  if (any_strided(h)) {
+    src_base_kernel<<<1, 32, 0, st>>>(h->d_ctrl);
+    CU(cudaGetLastError());
   }
   // Multi-step calls replay a captured graph of G steps.
   const int G = 16;
@@ -703,7 +743,7 @@ int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream) {
     if (e != cudaSuccess) return fail(QDS_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     return QDS_OK;
   }
-  auto key = std::make_tuple(s4[0], s4[1], s4[2], s4[3], G, (void *)st);
+  auto key = std::make_tuple(G, (void *)st);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
     cudaStream_t cs;

@@ -98,6 +98,7 @@ struct Inst {
   C<R> *state[2];        // ping-pong bases: 15 planes, then phi_prev
   C<R> *scratch;         // pass mode: Gamma_a, j_a,x, j_a,r, j_a,th planes
   const C<R> *jx, *jr, *jt, *sext;  // optional sources [M][nx][nr]
+  long long sstride;                // elements between the sources of consecutive steps (0: the same every step)
 };
 
 // Row stride of the working layout for precision R.

@@ -32,8 +32,7 @@ void emu_flat_step(EmuState<R, M> &S, const Inst<R> &I, int n, uint32_t flags) {
   const int nx = S.nx, nr = S.nr;
   const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0, mw = (flags & F_MOVING_WINDOW) != 0;
   const bool per_ = (flags & F_X_PERIODIC) != 0;
-  const int order[] = {ST_LEAP0, ST_SOURCE, ST_SHIFT0, ST_CURRENT, ST_SHIFT1, ST_ZERO};
-  for (int st : order) {
+  for (int st = 0; st < N_STAGE; st++) {
     if (st == ST_SOURCE && !ax) continue;
     if ((st == ST_CURRENT || st == ST_SHIFT1) && !ar) continue;
     if (st == ST_ZERO && !mw) continue;

@@ -10,10 +10,19 @@
 namespace qds {
 
 struct Ctrl {
-  unsigned long long step;  // steps taken since the last state import
-  unsigned int err;         // device-side error flags (kErr*)
-  unsigned int test;        // test hook: bit 0 withholds the first bulk copy of each x-marching CTA
+  unsigned long long step;      // steps taken since the last state import
+  unsigned int err;             // device-side error flags (kErr*)
+  unsigned int test;            // test hook: bit 0 withholds the first bulk copy of each x-marching CTA
+  unsigned long long src_base;  // step count when the current qds_step call began
 };
+
+// Sources of the current step: the descriptor's arrays advanced by the
+// steps taken in this call times the per-step stride.
+template <class R>
+__device__ __forceinline__ const C<R> *step_src(const C<R> *a, const Inst<R> &I, const Ctrl *ctrl) {
+  if (!a || I.sstride == 0) return a;
+  return a + (long long)(ctrl->step - ctrl->src_base) * I.sstride;
+}
 
 // Per-instance prefactors of the energies (diag_final_all_kernel).
 struct Scal4 {
@@ -28,9 +37,14 @@ constexpr unsigned kErrNonfinite = 2u;  // a NaN or Inf reached the state
 // Pass-mode view of the point (x0 = td.y, r0 = td.z) of instance td.x at
 // step n.
 template <class R, int M, bool FAST>
-__device__ __forceinline__ Tile<R, M, FAST> pass_tile(const Inst<R> &I, int4 td, unsigned long long n) {
+__device__ __forceinline__ Tile<R, M, FAST> pass_tile(const Inst<R> &I, int4 td, const Ctrl *ctrl) {
+  const unsigned long long n = ctrl->step;
   Tile<R, M, FAST> t;
   t.bind(I, &I);
+  t.jx = step_src(I.jx, I, ctrl);
+  t.jr = step_src(I.jr, I, ctrl);
+  t.jt = step_src(I.jt, I, ctrl);
+  t.sext = step_src(I.sext, I, ctrl);
   t.nx = I.nx;
   t.nr = I.nr;
   t.ld = I.ld;
@@ -66,7 +80,7 @@ __device__ __forceinline__ void flat_point(const Inst<R> *__restrict__ insts, in
   const Inst<R> &I = insts[td.x];
   const int q = td.y + (int)threadIdx.x;
   const int w = q / I.nr, j = q - w * I.nr;
-  Tile<R, M, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl->step);
+  Tile<R, M, FAST> t = pass_tile<R, M, FAST>(I, make_int4(td.x, w, j, 0), ctrl);
   run_stage<R, M, FAST>(t, ST);
 }
 
@@ -88,6 +102,10 @@ static __global__ void advance_kernel(Ctrl *ctrl, int nsteps) {
 
 static __global__ void reset_kernel(Ctrl *ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) { ctrl->step = 0; ctrl->err = 0; }
+}
+
+static __global__ void src_base_kernel(Ctrl *ctrl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->src_base = ctrl->step;
 }
 
 static __global__ void set_test_kernel(Ctrl *ctrl, unsigned int bits) {

@@ -425,7 +425,10 @@ __global__ void __launch_bounds__(256, 2) march_kernel(const Inst<R> *__restrict
   const unsigned long long nstep = ctrl->step;
   const int par = (int)(nstep & 1ull);
   MarchTile<R, M, KIND> t;
-  t.jx = I.jx; t.jr = I.jr; t.jt = I.jt; t.sext = I.sext;
+  t.jx = step_src(I.jx, I, ctrl);
+  t.jr = step_src(I.jr, I, ctrl);
+  t.jt = step_src(I.jt, I, ctrl);
+  t.sext = step_src(I.sext, I, ctrl);
   t.gs = I.gs; t.gj = I.gj; t.ma2 = I.ma2;
   t.flags = I.flags;
   t.nx = I.nx; t.nr = I.nr; t.J = I.nr - 1; t.ld = I.ld;

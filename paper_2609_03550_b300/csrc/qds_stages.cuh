@@ -807,7 +807,7 @@ QDS_HD void run_stage(Tile<R, M, FAST> t, int st) {
     const int w = t.x0, j = t.r0;
     t.set_point(w);
     C<R> jax[M], jat[M];
-    current_point(t, lx, lr, jax, jat);
+    current_point(t, lx, lr, jax, jat, TileNewVals<Tile<R, M, FAST>>{t, lx});
     // the regenerated leapfrog (Sec. 2.2) of this face follows at once; it
     // needs j_a,x and (outer row) j_a,theta of this point only
     const bool live = t.face_ok(w) && j >= 0 && j < t.nr;

@@ -288,7 +288,7 @@ class DeviceBunchSources:
         self.noise = torch.empty((3, 2, wl.M, wl.nx, wl.nr), dtype=torch.float64, device=device)
         self.bunch64 = self.bunch.to(torch.complex128)
 
-    def __call__(self, step):
+    def _draw(self, step, out):
         torch = self.torch
         self.gen.manual_seed(self.seed * 1_000_003 + int(step))
         self.noise.uniform_(-1.0, 1.0, generator=self.gen)
@@ -297,5 +297,20 @@ class DeviceBunchSources:
             z = torch.complex(self.amp * self.noise[c, 0], self.amp * self.noise[c, 1])
             if c == 0:
                 z[0] += self.bunch64[0]
-            self.buf[c].copy_(z)
+            out[c].copy_(z)
+
+    def __call__(self, step):
+        self._draw(step, self.buf)
         return tuple(self.buf)
+
+    def fill(self, n0, count):
+        """The currents of steps n0 .. n0+count-1 (the values __call__ gives)
+        as three tensors [count, M, nx, nr], in buffers kept for reuse."""
+        torch = self.torch
+        blk = getattr(self, "_blk", None)
+        if blk is None or blk[0].shape[0] < count:
+            blk = self._blk = [torch.empty((count, self.M, self.nx, self.nr), dtype=self.dtype, device=self.device)
+                               for _ in range(3)]
+        for k in range(count):
+            self._draw(n0 + k, [b[k] for b in blk])
+        return tuple(b[:count] for b in blk)

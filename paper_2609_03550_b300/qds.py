@@ -62,6 +62,7 @@ def lib():
             "qds_set_state_i": (i, [H, i, vp, vp]),
             "qds_get_state_i": (i, [H, i, vp, vp]),
             "qds_step": (i, [H, ctypes.POINTER(_Sources), i, vp]),
+            "qds_set_sources_i": (i, [H, i, ctypes.POINTER(_Sources), ctypes.c_longlong, vp]),
             "qds_diagnostics": (i, [H, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_diagnostics_i": (i, [H, i, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_num_instances": (i, [H]),
@@ -171,15 +172,43 @@ class QDSSolver:
         _check(lib().qds_get_state_i(self.h, i, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
         return out
 
+    def _src_ptr(self, t):
+        if t is None:
+            return None
+        assert t.is_cuda and t.dtype == self.rdtype and t.is_contiguous()
+        return t.data_ptr()
+
     def step(self, nsteps=1, jx=None, jr=None, jth=None, s_ext=None, stream=None):
-        def ptr(t):
-            if t is None:
-                return None
-            assert t.is_cuda and t.dtype == self.rdtype and t.is_contiguous()
-            return t.data_ptr()
-        src = _Sources(ptr(jx), ptr(jr), ptr(jth), ptr(s_ext))
+        """Advance ``nsteps`` steps.  Sources given here (device tensors
+        [M, nx, nr] in the working precision) are used for every step of the
+        call; with none given, the sources set by ``set_sources`` stay in
+        effect if there are any, else the step runs without sources."""
+        given = any(t is not None for t in (jx, jr, jth, s_ext))
+        if not given and getattr(self, "_per_instance", False):
+            _check(lib().qds_step(self.h, None, int(nsteps), _stream_ptr(stream)))
+            return
+        self._per_instance = False
+        src = _Sources(self._src_ptr(jx), self._src_ptr(jr), self._src_ptr(jth), self._src_ptr(s_ext))
         self._src_keep = (jx, jr, jth, s_ext)
         _check(lib().qds_step(self.h, ctypes.byref(src), int(nsteps), _stream_ptr(stream)))
+
+    def set_sources(self, i=0, jx=None, jr=None, jth=None, s_ext=None, per_step=False, stream=None):
+        """Sources of instance ``i`` for the following ``step`` calls made
+        without sources.  ``per_step=False``: tensors [M, nx, nr], the same
+        every step; ``per_step=True``: tensors [n, M, nx, nr] whose slice k
+        drives step k of each later call (calls of at most n steps)."""
+        p = self.params[i]
+        plane = p.n_modes * p.nx * p.nr
+        for t in (jx, jr, jth, s_ext):
+            if t is not None:
+                assert t.numel() % plane == 0 and (per_step or t.numel() == plane)
+        src = _Sources(self._src_ptr(jx), self._src_ptr(jr), self._src_ptr(jth), self._src_ptr(s_ext))
+        keep = getattr(self, "_inst_src_keep", {})
+        keep[i] = (jx, jr, jth, s_ext)
+        self._inst_src_keep = keep
+        self._per_instance = True
+        _check(lib().qds_set_sources_i(self.h, int(i), ctypes.byref(src), plane if per_step else 0,
+                                       _stream_ptr(stream)))
 
     def adjoint_step(self, fwd, lam, i: int = 0, jx=None, jth=None, s_ext=None, dLdg=None, stream=None):
         """One transposed step (qds_adjoint_step): ``fwd`` is the canonical

@@ -43,7 +43,8 @@ def run_emu(M, buf, nx, nr, dr, m_a, g, flags, src, nsteps, mode=MARCH, rows=(24
 
 
 @pytest.mark.parametrize("M,flags", parity_cases())
-@pytest.mark.parametrize("mode,rows,seg", [(FLAT, (24, 16), 7), (MARCH, (24, 16), 7), (MARCH, (64, 64), 128)])
+@pytest.mark.parametrize("mode,rows,seg", [(FLAT, (24, 16), 7), (MARCH, (24, 16), 7),
+                                           (MARCH, (64, 64), 128)])
 def test_emulated_kernels_match_oracle_fp64(M, flags, mode, rows, seg):
     """nr = 11: one band per kernel; nx = 21 with 7-column segments gives
     three CTAs along x, the first and last at the open (or periodic) ends."""
