@@ -158,11 +158,13 @@ int qds_diagnostics_all(qds_handle *h, double *out_dev, void *stream);
  *                     point per thread over flat ranges of 256 points,
  *                     intermediates in the new state and scratch planes;
  *   QDS_STEP_MARCH    two x-marching kernels per mode count: each CTA walks
- *                     a band of rows (all modes) along x, the old state
- *                     arriving column by column in a shared-memory ring by
- *                     bulk tensor copies; the first kernel advances the EM
- *                     field and the axion and writes j_a, the second the
- *                     axion-regenerated field.
+ *                     a band of rows (all modes, one thread per row and
+ *                     mode) along x, the old state arriving column by
+ *                     column in a shared-memory ring by bulk tensor copies,
+ *                     two columns ahead; the first kernel advances the EM
+ *                     field and the axion and writes j_a (one extra warp
+ *                     forms the outer half row's boundary values), the
+ *                     second the axion-regenerated field.
  * Changing the mode drops the captured graphs. */
 #define QDS_STEP_DEFAULT 0
 #define QDS_STEP_FLAT 1
@@ -171,13 +173,12 @@ int qds_set_step_mode(qds_handle *h, int mode);
 /* Kernel launches of one step in the current mode (0 for a NULL handle). */
 int qds_step_launches(const qds_handle *h);
 
-/* Work split of QDS_STEP_MARCH (the autotuner's knobs): rows = radial rows
- * per CTA including the halo (24..256, rounded down to a multiple of 8, at
- * most 256 / n_modes and at most what fits in 227 KB of shared memory;
- * 0 = the default that fits two CTAs per SM), cols =
- * window columns per CTA (>= 4; 0 = 128).  qds_get_tile reports the rows of
- * the first kernel of the first mode count, the columns, the CTAs of one
- * step and that kernel's shared memory in bytes. */
+/* Work split of QDS_STEP_MARCH (the autotuner's knobs): rows = ring rows
+ * per CTA including the radial halo, 64 or 32 in FP32 and 32 in FP64 (a
+ * request is rounded down to one of these, at least 32; 0 = 64 in FP32),
+ * cols = window columns per CTA (>= 4; 0 = 128).  qds_get_tile reports the
+ * rows of the first kernel of the first mode count, the columns, the CTAs of
+ * one step and that kernel's shared memory in bytes. */
 int qds_set_tile(qds_handle *h, int rows, int cols);
 int qds_get_tile(qds_handle *h, int *rows, int *cols, int *ntiles, int *smem_bytes);
 

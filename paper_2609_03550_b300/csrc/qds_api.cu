@@ -90,21 +90,12 @@ size_t instance_bytes(const qds_params &p) {
 // ---------------------------------------------------------------------------
 // x-marching launch plan
 // ---------------------------------------------------------------------------
-// Shared memory of one CTA, in bytes, for band rows RB.
-int march_smem(bool fp32, int kind, int M, int RB) {
-  return fp32 ? march_geo<float>(kind, M, RB).bytes : march_geo<double>(kind, M, RB).bytes;
-}
-
-// Default rows per CTA: the largest multiple of 8 (at most 256/M threads,
-// 128 rows in FP64 for the copy box) whose shared memory lets two CTAs share
-// an SM.
-int default_rows(bool fp32, int kind, int M) {
-  const int cap_thr = 256 / M;
-  const int cap = std::min(cap_thr, fp32 ? 256 : 128);
-  int best = 8;
-  for (int RB = 8; RB <= cap; RB += 8)
-    if (march_smem(fp32, kind, M, RB) <= 110 * 1024) best = RB;
-  return best;
+// Ring rows per CTA the kernels are compiled for: 32 and 64 in FP32, 32 in
+// FP64 (a warp is then 32 rows of one mode).  A request is rounded down to
+// one of these; 0 gives the default, 64 in FP32.
+int march_rows(bool fp32, int req) {
+  if (!fp32) return 32;
+  return req == 0 || req >= 64 ? 64 : 32;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -144,21 +135,16 @@ int encode_map(CUtensorMap *out, void *base, bool fp32, int M, int nx, int nr, i
   return QDS_OK;
 }
 
-// Work items of one kernel kind for one instance: bands of rows (the first
-// band starts at row 0 with no halo below) times segments of columns.
+// Work items of one kernel kind for one instance: bands of rows (see
+// march_bands) times segments of columns.
 void march_items(std::vector<MarchItem> &out, int inst, int nx, int nr, int RB, int halo, int seg) {
-  const int first = RB - halo;
-  const int tr = RB - 2 * halo;
-  for (int r0 = 0; r0 < nr;) {
-    const int r1 = std::min(nr, r0 == 0 ? first : r0 + tr);
-    const int rb0 = r0 == 0 ? 0 : r0 - halo;
+  march_bands(nr, RB, halo, [&](int r0, int r1, int rb0) {
     for (int xa = 0; xa < nx; xa += seg) {
       MarchItem it{};
       it.inst = inst; it.r0 = r0; it.r1 = r1; it.rb0 = rb0; it.xa = xa; it.xb = std::min(nx, xa + seg);
       out.push_back(it);
     }
-    r0 = r1;
-  }
+  });
 }
 
 }  // namespace
@@ -295,27 +281,43 @@ cudaError_t launch_flat(qds_handle *h, const qds_handle::Group &G, cudaStream_t 
   return cudaGetLastError();
 }
 
-template <class R, int M, int KIND>
-cudaError_t launch_march(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
-  const MarchGeo &g = G.geo[KIND];
-  march_kernel<R, M, KIND><<<G.nitems[KIND], M * g.RB, g.bytes, st>>>((const Inst<R> *)h->d_inst, h->d_maps,
-                                                                     G.d_items[KIND], h->d_ctrl, g);
+template <class R, int M, int RB, int KIND>
+cudaError_t launch_march_rb(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  march_kernel<R, M, RB, KIND><<<G.nitems[KIND], march_threads<M, RB, KIND>(), G.geo[KIND].bytes, st>>>(
+      (const Inst<R> *)h->d_inst, h->d_maps, G.d_items[KIND], h->d_ctrl);
   return cudaGetLastError();
 }
 
-template <class R, int M>
-cudaError_t allow_march_smem_t(int b0, int b1) {
-  cudaError_t e = cudaFuncSetAttribute(march_kernel<R, M, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(march_kernel<R, M, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b1);
+template <class R, int M, int KIND>
+cudaError_t launch_march(qds_handle *h, const qds_handle::Group &G, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (G.rows[KIND] == 64) return launch_march_rb<R, M, 64, KIND>(h, G, st);
+  }
+  return launch_march_rb<R, M, 32, KIND>(h, G, st);
 }
 
-cudaError_t allow_march_smem(bool fp32, int M, int b0, int b1) {
+template <class R, int M, int RB>
+cudaError_t allow_march_smem_rb() {
+  const int b0 = march_geo<R>(0, M, RB).bytes, b1 = march_geo<R>(1, M, RB).bytes;
+  cudaError_t e = cudaFuncSetAttribute(march_kernel<R, M, RB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, b0);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(march_kernel<R, M, RB, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, b1);
+}
+
+template <int M>
+cudaError_t allow_march_smem_m(bool fp32) {
+  if (!fp32) return allow_march_smem_rb<double, M, 32>();
+  cudaError_t e = allow_march_smem_rb<float, M, 32>();
+  if (e != cudaSuccess) return e;
+  return allow_march_smem_rb<float, M, 64>();
+}
+
+cudaError_t allow_march_smem(bool fp32, int M) {
   switch (M) {
-    case 1: return fp32 ? allow_march_smem_t<float, 1>(b0, b1) : allow_march_smem_t<double, 1>(b0, b1);
-    case 2: return fp32 ? allow_march_smem_t<float, 2>(b0, b1) : allow_march_smem_t<double, 2>(b0, b1);
-    case 3: return fp32 ? allow_march_smem_t<float, 3>(b0, b1) : allow_march_smem_t<double, 3>(b0, b1);
-    case 4: return fp32 ? allow_march_smem_t<float, 4>(b0, b1) : allow_march_smem_t<double, 4>(b0, b1);
+    case 1: return allow_march_smem_m<1>(fp32);
+    case 2: return allow_march_smem_m<2>(fp32);
+    case 3: return allow_march_smem_m<3>(fp32);
+    case 4: return allow_march_smem_m<4>(fp32);
   }
   return cudaErrorInvalidValue;
 }
@@ -392,12 +394,8 @@ int build_march(qds_handle *h) {
     for (int kind = 0; kind < 2; kind++) {
       cudaFree(G.d_items[kind]);
       G.d_items[kind] = nullptr;
-      int RB = h->rows_override > 0 ? h->rows_override : default_rows(h->fp32, kind, G.M);
-      RB = std::min(RB, std::min(256 / G.M, h->fp32 ? 256 : 128)) / 8 * 8;
-      // a requested row count larger than fits in shared memory is clamped
-      while (RB > 8 && march_smem(h->fp32, kind, G.M, RB) > 227 * 1024) RB -= 8;
+      const int RB = march_rows(h->fp32, h->rows_override);
       const int halo = kind == 0 ? kHalo1 : kHalo2;
-      if (RB < 2 * halo + 8) return fail(QDS_ERR_INVALID_ARG, "march rows per CTA too small");
       G.rows[kind] = RB;
       G.geo[kind] = h->fp32 ? march_geo<float>(kind, G.M, RB) : march_geo<double>(kind, G.M, RB);
       if (G.geo[kind].bytes > 227 * 1024) return fail(QDS_ERR_UNSUPPORTED, "march tile does not fit in shared memory");
@@ -409,7 +407,7 @@ int build_march(qds_handle *h) {
       CU(cudaMalloc(&G.d_items[kind], sizeof(MarchItem) * std::max<size_t>(1, items.size())));
       CU(cudaMemcpy(G.d_items[kind], items.data(), sizeof(MarchItem) * items.size(), cudaMemcpyHostToDevice));
     }
-    CU(allow_march_smem(h->fp32, G.M, G.geo[0].bytes, G.geo[1].bytes));
+    CU(allow_march_smem(h->fp32, G.M));
   }
   // tensor maps of every instance (box rows of its group)
   std::vector<MarchMaps> maps(h->n_inst);

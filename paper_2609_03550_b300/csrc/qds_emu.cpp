@@ -9,6 +9,7 @@
 // checked on the CPU before the kernels run on a GPU; it is a separate
 // library (libqds_emu.so) that the product path never loads.
 #define QDS_EMU 1
+#include <array>
 #include <cstring>
 #include <vector>
 
@@ -85,85 +86,103 @@ void emu_copy_box(const EmuState<R, M> &S, const C<R> *base, int f0, int nbox, i
 }
 
 // One x-marching kernel (KIND 0: EM + axion + j_a, 1: regenerated EM) over
-// all its work items, CTA by CTA, every stage over all threads of the CTA
+// all its work items, CTA by CTA, every phase over all threads of the CTA
 // before the next (the kernel's barriers), the ring filled as the bulk
-// copies would fill it.
-template <class R, int M, int KIND>
-void emu_march_kernel(EmuState<R, M> &S, const Inst<R> &I, int n, uint32_t flags, int RB, int seg) {
+// copies would fill it.  The shared memory is poisoned with NaN (with NaN
+// guard regions on both sides), so that a read of anything no copy or phase
+// wrote shows up in the result.
+template <class R, int M, int RB, int KIND>
+void emu_march_kernel(EmuState<R, M> &S, const Inst<R> &I0, int n, uint32_t flags, int seg) {
+  using Sh = MarchShape<R, M, RB, KIND>;
   const int nx = S.nx, nr = S.nr;
   const MarchGeo geo = march_geo<R>(KIND, M, RB);
   const int halo = KIND == 0 ? kHalo1 : kHalo2;
-  std::vector<C<R>> sm(geo.off_bar / sizeof(C<R>) + 1);
-  const bool ax = (flags & (F_AXION | F_AREM)) != 0, ar = (flags & F_AREM) != 0;
-  // work items as the host library builds them
+  const size_t guard = 8192;
+  std::vector<C<R>> smv(geo.off_bar / sizeof(C<R>) + 1 + 2 * guard);
+  C<R> *sm = smv.data() + guard;
+  const bool ar = (flags & F_AREM) != 0;
+  Inst<R> I = I0;
+  I.state[0] = S.buf[0].data();
+  I.state[1] = S.buf[1].data();
+  I.scratch = S.scratch.data();
   std::vector<MarchItem> items;
-  {
-    const int first = RB - halo, tr = RB - 2 * halo;
-    for (int r0 = 0; r0 < nr;) {
-      const int r1 = std::min(nr, r0 == 0 ? first : r0 + tr);
-      const int rb0 = r0 == 0 ? 0 : r0 - halo;
-      for (int xa = 0; xa < nx; xa += seg) {
-        MarchItem it{};
-        it.inst = 0; it.r0 = r0; it.r1 = r1; it.rb0 = rb0; it.xa = xa; it.xb = std::min(nx, xa + seg);
-        items.push_back(it);
-      }
-      r0 = r1;
+  march_bands(nr, RB, halo, [&](int r0, int r1, int rb0) {
+    for (int xa = 0; xa < nx; xa += seg) {
+      MarchItem it{};
+      it.inst = 0; it.r0 = r0; it.r1 = r1; it.rb0 = rb0; it.xa = xa; it.xb = std::min(nx, xa + seg);
+      items.push_back(it);
     }
-  }
+  });
   const int nth = M * RB;
+  std::vector<MarchCtx<R, M, RB, KIND>> ctx(nth);
+  std::vector<K1Regs<R>> regs(nth);
+  std::vector<std::array<K2Hist<R>, 2>> hist(nth);
   for (const MarchItem &it : items) {
-    MarchTile<R, M, KIND> t;
-    t.jx = I.jx; t.jr = I.jr; t.jt = I.jt; t.sext = I.sext;
-    t.gs = I.gs; t.gj = I.gj; t.ma2 = I.ma2;
-    t.flags = flags;
-    t.nx = nx; t.nr = nr; t.J = nr - 1; t.ld = S.ld;
-    t.x0 = 0; t.r0 = 0;
-    t.per = (flags & F_X_PERIODIC) != 0;
-    t.closed = (flags & F_R_CLOSED) != 0;
-    t.mw = (flags & F_MOVING_WINDOW) != 0;
-    t.s = t.mw ? n % nx : 0;
-    t.P = S.P;
-    t.o = S.buf[n & 1].data();
-    t.n = S.buf[(n & 1) ^ 1].data();
-    t.scr = S.scratch.data();
-    t.h = I.h; t.dr = I.dr; t.ih = I.inv_h; t.idr = I.inv_dr;
-    // the kernel zeroes the intermediate planes; the ring holds whatever the
-    // shared memory held (poisoned here, so that a read of a slot no copy
-    // filled shows up in the result)
-    for (size_t q = 0; q < sm.size(); q++) sm[q] = (int)q < geo.off_a ? mk<R>((R)NAN, (R)NAN) : zero<R>();
-    t.ring = sm.data();
-    t.sa = sm.data() + geo.off_a;
-    t.sg = sm.data() + geo.off_g;
-    t.st = sm.data() + geo.off_t;
-    t.sp = sm.data() + geo.off_p;
-    t.RB = RB; t.rb0 = it.rb0; t.SS = geo.slot;
-    t.xa = it.xa; t.xb = it.xb; t.b_r0 = it.r0; t.b_r1 = it.r1;
-    t.sm_len = (int)sm.size();
-    const int L0 = march_first(KIND, it.xa), L1 = march_last(KIND, it.xb), C1 = march_last_col(KIND, it.xb);
-    auto load = [&](int c) {
-      C<R> *slot = sm.data() + ((c + 4 * kRing) % kRing) * geo.slot;
-      const int coord = march_coord(c, nx, t.s, t.per);
+    for (auto &v : smv) v = mk<R>((R)NAN, (R)NAN);
+    for (int tid = 0; tid < nth; tid++) {
+      march_ctx<R, M, RB, KIND>(ctx[tid], I, it, sm, (unsigned long long)n, tid);
+      ctx[tid].jx = I.jx; ctx[tid].jr = I.jr; ctx[tid].jt = I.jt; ctx[tid].sext = I.sext;
+      ctx[tid].state_len = S.E;
+      regs[tid].gam_prev = regs[tid].gam = regs[tid].tap_prev = regs[tid].tam_prev = zero<R>();
+      regs[tid].bad = false;
+      const C<R> nan = mk<R>((R)NAN, (R)NAN);
+      for (int q = 0; q < 2; q++) hist[tid][q] = K2Hist<R>{nan, nan, nan, nan, nan, nan, nan, nan, nan, nan};
+    }
+    const MarchCtx<R, M, RB, KIND> &c0 = ctx[0];
+    const int L0 = c0.L0, L1 = march_last(KIND, it.xb), C1 = march_last_col(KIND, it.xb);
+    auto load = [&](int col) {
+      C<R> *slot = sm + ((col - L0) % Sh::NS) * Sh::SS;
+      const int coord = march_coord(col, nx, c0.s, c0.per);
       if (KIND == 0) {
-        emu_copy_box<R, M>(S, t.o, 0, 9, coord, it.rb0, RB, slot);
+        emu_copy_box<R, M>(S, c0.o, 0, 9, coord, it.rb0, RB, slot);
       } else {
-        emu_copy_box<R, M>(S, t.o, TRP1, 6, coord, it.rb0, RB, slot);
+        emu_copy_box<R, M>(S, c0.o, TRP1, 6, coord, it.rb0, RB, slot);
         emu_copy_box<R, M>(S, S.scratch.data(), 1, 3, coord, it.rb0, RB, slot + 6 * M * RB);
       }
     };
-    // the copies land when the kernel issues them (three ahead, then one per
-    // iteration after the first phase), which is no later than they are read
-    for (int c = L0; c <= C1 && c < L0 + 3; c++) load(c);
+    // the copies land when the kernel issues them (three ahead, then one
+    // per iteration after its last phase), no later than they are read
+    for (int col = L0; col <= C1 && col < L0 + 3; col++) load(col);
+    bool bad = false;
     for (int L = L0; L <= L1; L++) {
+      for (int tid = 0; tid < nth; tid++) ctx[tid].iter(L);
       if constexpr (KIND == 0) {
-        for (int tid = 0; tid < nth; tid++) m1_phase1<R, M>(t, L, ar, tid, nth);
-        if (L + 3 <= C1) load(L + 3);
-        for (int tid = 0; tid < nth; tid++) m1_phase2<R, M>(t, L, ax, tid, nth);
+        // the boundary warp (lane k: the outer half row of mode k) works in
+        // the same phases as the main threads; its writes do not overlap theirs
+        for (int tid = 0; tid < nth; tid++) k1_p1<R, M, RB>(ctx[tid], L);
+        for (int k = 0; k < M; k++) {
+          const int t = k * RB + (nr - 1 - it.rb0);
+          if (nr - 1 - it.rb0 < RB && outer_active<R, M, RB>(ctx[t])) outer_p1<R, M, RB>(ctx[t], L);
+        }
+        for (int tid = 0; tid < nth; tid++) k1_p2<R, M, RB>(ctx[tid], L, ar);
+        for (int tid = 0; tid < nth; tid++) k1_p3<R, M, RB>(ctx[tid], L, regs[tid]);
+        for (int k = 0; k < M; k++) {
+          const int t = k * RB + (nr - 1 - it.rb0);
+          if (nr - 1 - it.rb0 < RB && outer_active<R, M, RB>(ctx[t])) (void)outer_p3<R, M, RB>(ctx[t], L);
+        }
       } else {
-        for (int tid = 0; tid < nth; tid++) m2_phase<R, M>(t, L, tid, nth);
-        if (L + 3 <= C1) load(L + 3);
+        for (int tid = 0; tid < nth; tid++) k2_p1<R, M, RB>(ctx[tid], L);
+        for (int tid = 0; tid < nth; tid++) {
+          K2Hist<R>(&h)[2] = *reinterpret_cast<K2Hist<R>(*)[2]>(hist[tid].data());
+          k2_p2<R, M, RB>(ctx[tid], L, h, bad);
+        }
       }
+      if (L + 3 <= C1) load(L + 3);
     }
   }
+}
+
+// The ring heights the kernels are compiled for.
+template <class R, int M, int KIND>
+bool emu_march_rb(EmuState<R, M> &S, const Inst<R> &I, int n, uint32_t flags, int RB, int seg) {
+  switch (RB) {
+    case 8: emu_march_kernel<R, M, 8, KIND>(S, I, n, flags, seg); return true;
+    case 16: emu_march_kernel<R, M, 16, KIND>(S, I, n, flags, seg); return true;
+    case 24: emu_march_kernel<R, M, 24, KIND>(S, I, n, flags, seg); return true;
+    case 32: emu_march_kernel<R, M, 32, KIND>(S, I, n, flags, seg); return true;
+    case 64: emu_march_kernel<R, M, 64, KIND>(S, I, n, flags, seg); return true;
+  }
+  return false;
 }
 
 // mode 0: flat stage passes; mode 1: the x-marching kernels with rows per
@@ -221,8 +240,8 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
     if (mode == 0) {
       emu_flat_step<R, M>(S, I, n, flags);
     } else {
-      emu_march_kernel<R, M, 0>(S, I, n, flags, RB1, seg);
-      if (ar) emu_march_kernel<R, M, 1>(S, I, n, flags, RB2, seg);
+      if (!emu_march_rb<R, M, 0>(S, I, n, flags, RB1, seg)) std::abort();
+      if (ar && !emu_march_rb<R, M, 1>(S, I, n, flags, RB2, seg)) std::abort();
     }
   }
   // export in window order
@@ -273,7 +292,8 @@ extern "C" int qds_emu_steps(int M, const double *canon, double *out, int nx, in
                              double m_a, double g, uint32_t flags, const double *jx, const double *jr,
                              const double *jt, const double *sext, int nsteps, int RB1, int RB2, int seg,
                              int mode) {
-  if (RB1 < 2 * kHalo1 + 8 || RB2 < 2 * kHalo2 + 8 || RB1 % 8 || RB2 % 8 || seg < 1) return 2;
+  auto ok_rb = [](int rb) { return rb == 8 || rb == 16 || rb == 24 || rb == 32 || rb == 64; };
+  if (!ok_rb(RB1) || !ok_rb(RB2) || seg < 1) return 2;
   if (flags & F_FP32)
     return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode);
   return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode);

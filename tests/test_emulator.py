@@ -58,12 +58,14 @@ def test_emulated_kernels_match_oracle_fp64(M, flags, mode, rows, seg):
 
 
 @pytest.mark.parametrize("M,flags", [c for c in parity_cases() if c[1] & 2])
-@pytest.mark.parametrize("rows,seg", [((24, 16), 5), ((32, 24), 9), ((24, 24), 30)])
+@pytest.mark.parametrize("rows,seg", [((24, 16), 5), ((32, 24), 9), ((24, 24), 30), ((8, 8), 4), ((16, 8), 1)])
 def test_march_bands_and_segments(M, flags, rows, seg):
     """nr = 45 odd (padded row stride in FP32), several bands per kernel
-    (first kernel: rows [0, 20), [20, 36), [36, 45) for 24 rows per CTA;
-    second: 14-row first band, 12-row bands), segments of 5, 9 and 30
-    columns over nx = 30 (a ragged last segment, one CTA for the whole x)."""
+    (first kernel with 24 ring rows: owned rows [0, 21), [21, 39), [39, 45),
+    each later band's ring starting 3-4 rows below it at an even row; the
+    smallest rings, 8 rows, give bands of one or two rows), segments of
+    1, 4, 5, 9 and 30 columns over nx = 30 (a ragged last segment, one CTA
+    for the whole x)."""
     nx, nr = 30, 45
     dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
     buf, src = random_case(M * 17 + flags, M, nx, nr)
