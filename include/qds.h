@@ -130,6 +130,23 @@ int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream);
  * Uploads the descriptor (synchronises stream). */
 int qds_set_sources_i(qds_handle *h, int i, const qds_sources *src, long long stride, void *stream);
 
+/* Laser injection at x_min (Sec. 4.1 injects its vacuum pulse through the
+ * boundary; Eq. em_x_open sets the inflow characteristics to zero there):
+ * for the following qds_step calls the exterior cell behind x_min holds the
+ * inflow T_r^+ = E_r + B_theta (tr_plus_dev) and T_theta^- = E_theta - B_r
+ * (tth_minus_dev) of the EM field at time n, so that the shift carries them
+ * into cell 0 at step n -> n+1 (the outgoing T_r^-, T_theta^+ and all other
+ * fields stay zero outside; the axion and the regenerated field are not
+ * injected).  Arrays: [M][nr] complex values of the working precision
+ * (device), physical variables; step k of a call reads them advanced by
+ * k * stride elements (stride 0: the same every step; M*nr: [n][M][nr]).
+ * NULL for either array gives zero inflow for it; both NULL restores the
+ * open boundary.  Open x only (QDS_X_PERIODIC: QDS_ERR_INVALID_ARG).  The
+ * arrays must stay valid until the stream has executed those steps.
+ * Uploads the descriptor (synchronises stream). */
+int qds_set_inflow_i(qds_handle *h, int i, const void *tr_plus_dev, const void *tth_minus_dev, long long stride,
+                     void *stream);
+
 /* Energies into out_host[4] = {EM energy, axion energy, regenerated EM
  * energy, int (E0.E1 + B0.B1) dV} (mode-weighted volume integrals, FP64,
  * compensated sums); if profile_dev is non-NULL (device, nx doubles) also the

@@ -39,6 +39,8 @@ def lib(extended=False):
         L.ora_step.restype = ctypes.c_int
         L.ora_step_n.argtypes = L.ora_step.argtypes + [ctypes.c_int]
         L.ora_step_n.restype = ctypes.c_int
+        L.ora_step_inflow.argtypes = L.ora_step.argtypes + [dp, dp, ctypes.c_longlong, ctypes.c_int]
+        L.ora_step_inflow.restype = ctypes.c_int
         L.ora_diagnostics.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, dp, dp, dp]
@@ -82,17 +84,27 @@ class State:
         return State(self.M, self.nx, self.nr, self.buf)
 
 
-def step(p, st, jx=None, jr=None, jt=None, s_ext=None, nsteps=1, extended=False):
+def step(p, st, jx=None, jr=None, jt=None, s_ext=None, nsteps=1, extended=False, inflow=None):
     """Advance ``st`` in place by ``nsteps`` steps with constant sources.
 
     ``p``: dict with nx, nr, M, h, dr, m_a, g, flags.  Sources are complex128
-    arrays [M, nx, nr] at the native staggered positions (or None).  With
+    arrays [M, nx, nr] at the native staggered positions (or None).
+    ``inflow``: laser injection at x_min, a pair (T_r^+, T_th^-) of the
+    exterior cell behind x_min, each [M, nr] (the same every step) or
+    [nsteps, M, nr] (step by step); None keeps the open boundary.  With
     ``extended`` the steps run in long double (state rounded to complex128
     only on return)."""
     L = lib(extended)
     srcs = [None if a is None else np.ascontiguousarray(a, np.complex128) for a in (jx, jr, jt, s_ext)]
-    rc = L.ora_step_n(p["nx"], p["nr"], p["M"], p["h"], p["dr"], p.get("m_a", 0.0), p.get("g", 0.0),
-                      p.get("flags", 0), _ptr(st.buf), *[_ptr(a) for a in srcs], int(nsteps))
+    ins, istride = [None, None], 0
+    if inflow is not None:
+        ins = [np.ascontiguousarray(a, np.complex128) for a in inflow]
+        shape = (p["M"], p["nr"])
+        assert ins[0].shape == ins[1].shape and ins[0].shape in (shape, (nsteps,) + shape)
+        istride = 0 if ins[0].ndim == 2 else p["M"] * p["nr"]
+    rc = L.ora_step_inflow(p["nx"], p["nr"], p["M"], p["h"], p["dr"], p.get("m_a", 0.0), p.get("g", 0.0),
+                           p.get("flags", 0), _ptr(st.buf), *[_ptr(a) for a in srcs], _ptr(ins[0]),
+                           _ptr(ins[1]), istride, int(nsteps))
     if rc != 0:
         raise RuntimeError(f"ora_step failed: {rc}")
     return st

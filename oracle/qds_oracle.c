@@ -79,6 +79,9 @@ typedef struct {
   double h, dr, m_a, g;
   int flags;
   size_t plane; /* M*nx*nr */
+  /* laser injection at x_min (NULL: none): the inflow characteristics
+   * T_r^+ and T_th^- of the exterior cell -1 at time n, [M][nr] each */
+  const cplx *in_rp, *in_tm;
 } P;
 
 static inline size_t ix(const P *p, int m, int i, int j) {
@@ -92,6 +95,14 @@ static inline cplx cellv(const P *p, const cplx *a, int m, int i, int j) {
   if (periodic(p)) i = (i % p->nx + p->nx) % p->nx;
   else if (i < 0 || i >= p->nx) return 0;
   return a[ix(p, m, i, j)];
+}
+/* The exterior cell -1 behind x_min as seen by the shift into cell 0: the
+ * open boundary of Eq. em_x_open has T_r^+ = T_th^- = 0 there; with laser
+ * injection those two inflow characteristics take the prescribed values
+ * (the outgoing T_r^-, T_th^+ stay zero outside). */
+static inline cplx cell_in(const P *p, const cplx *a, const cplx *inflow, int m, int i, int j) {
+  if (!periodic(p) && i == -1 && inflow) return inflow[(size_t)m * p->nr + j];
+  return cellv(p, a, m, i, j);
 }
 static inline int real_face(const P *p, int f) {
   if (periodic(p)) return 1;
@@ -287,7 +298,7 @@ static void em_step(const P *p, const cplx *Trp, const cplx *Trm,
               cplx Pr = (ex_hi - facev(p, nEx, m, f, j)) / dr;
               src = (s == 0) ? Gr + Pr : Gr - Pr;
             }
-            if (s == 0) nTrp[ix(p, m, c, j)] = cellv(p, Trp, m, c - 1, j) + h * src;
+            if (s == 0) nTrp[ix(p, m, c, j)] = cell_in(p, Trp, p->in_rp, m, c - 1, j) + h * src;
             else nTrm[ix(p, m, c, j)] = cellv(p, Trm, m, c + 1, j) + h * src;
           }
         }
@@ -314,7 +325,7 @@ static void em_step(const P *p, const cplx *Trp, const cplx *Trm,
             src = (s == 0) ? Gt + Pt : Gt - Pt;
           }
           if (s == 0) nTtp[ix(p, m, c, j)] = cellv(p, Ttp, m, c + 1, j) + h * src;
-          else nTtm[ix(p, m, c, j)] = cellv(p, Ttm, m, c - 1, j) + h * src;
+          else nTtm[ix(p, m, c, j)] = cell_in(p, Ttm, p->in_tm, m, c - 1, j) + h * src;
         }
       }
     }
@@ -336,11 +347,13 @@ static void em_step(const P *p, const cplx *Trp, const cplx *Trm,
           Gr_l = -I * (double)m * facev(p, nBx, m, c - 1, J) / rh - facev(p, jr, m, c - 1, J);
         if (real_face(p, c))
           Gr_r = -I * (double)m * facev(p, nBx, m, c, J) / rh - facev(p, jr, m, c, J);
-        cplx Tp = cellv(p, Trp, m, c - 1, J) + h * Gr_l;
+        cplx Tp = cell_in(p, Trp, p->in_rp, m, c - 1, J) + h * Gr_l;
         cplx Tm = cellv(p, Trm, m, c + 1, J) + h * Gr_r;
         cplx Er_new = 0.5 * (Tp + Tm);
 
         cplx Er_l = 0.5 * (cellv(p, t->Er, m, c - 1, J - 1) + cellv(p, t->Er, m, c - 1, J));
+        if (c == 0 && !periodic(p) && p->in_rp) /* E_r = (T_r^+ + T_r^-)/2 of the exterior cell */
+          Er_l = 0.25 * (p->in_rp[(size_t)m * nr + J - 1] + p->in_rp[(size_t)m * nr + J]);
         cplx Er_r = 0.5 * (cellv(p, t->Er, m, c + 1, J - 1) + cellv(p, t->Er, m, c + 1, J));
         cplx dxEr = (Er_r - Er_l) / (2.0 * h);
         cplx Bth = 0.5 * (cellv(p, t->Bt, m, c, J - 1) + cellv(p, t->Bt, m, c, J));
@@ -658,7 +671,9 @@ static int step_once(const P *p, cplx *S, const cplx *jx, const cplx *jrc, const
     /* ---- AREM: the duplicate QDS step on (E1, B1) driven by j_a. ---- */
     Transverse t1 = {tmp, tmp + pl, tmp + 2 * pl, tmp + 3 * pl}; /* reuse t0 storage */
     reconstruct(p, fld(S, p, F_TRP1), fld(S, p, F_TRM1), fld(S, p, F_TTP1), fld(S, p, F_TTM1), &t1);
-    em_step(p, fld(S, p, F_TRP1), fld(S, p, F_TRM1), fld(S, p, F_TTP1), fld(S, p, F_TTM1),
+    P p1 = *p; /* the laser is injected into the EM field only */
+    p1.in_rp = p1.in_tm = NULL;
+    em_step(&p1, fld(S, p, F_TRP1), fld(S, p, F_TRM1), fld(S, p, F_TTP1), fld(S, p, F_TTM1),
             fld(S, p, F_EX1), fld(S, p, F_BX1), jax, jar, jat,
             fld(N, p, F_TRP1), fld(N, p, F_TRM1), fld(N, p, F_TTP1), fld(N, p, F_TTM1),
             fld(N, p, F_EX1), fld(N, p, F_BX1), &t1);
@@ -700,25 +715,44 @@ static cplx *to_cplx(const double *d, size_t n) {
   return z;
 }
 
-/* nsteps steps with constant sources; the state is held in the working
- * precision between the steps of one call. */
-int ora_step_n(int nx, int nr, int M, double h, double dr, double m_a, double g,
-               int flags, double *state_d, const double *jx_d, const double *jr_d,
-               const double *jt_d, const double *sext_d, int nsteps) {
-  if (nx < 4 || nr < 4 || M < 1 || M > 8 || nsteps < 0) return -1;
-  P pp = {nx, nr, M, h, dr, m_a, g, flags, (size_t)M * nx * nr};
+/* nsteps steps with constant sources and, optionally, laser injection at
+ * x_min: the inflow T_r^+, T_th^- of step n at in_rp_d / in_tm_d + n * istride
+ * complex elements ([M][nr] each; istride 0: the same every step).  The state
+ * is held in the working precision between the steps of one call. */
+int ora_step_inflow(int nx, int nr, int M, double h, double dr, double m_a, double g,
+                    int flags, double *state_d, const double *jx_d, const double *jr_d,
+                    const double *jt_d, const double *sext_d, const double *in_rp_d,
+                    const double *in_tm_d, long long istride, int nsteps) {
+  if (nx < 4 || nr < 4 || M < 1 || M > 8 || nsteps < 0 || istride < 0) return -1;
+  P pp = {nx, nr, M, h, dr, m_a, g, flags, (size_t)M * nx * nr, NULL, NULL};
   const size_t ns = (size_t)N_FIELDS * pp.plane + (size_t)M * nx;
   cplx *S = to_cplx(state_d, ns);
   cplx *jx = to_cplx(jx_d, pp.plane), *jr = to_cplx(jr_d, pp.plane);
   cplx *jt = to_cplx(jt_d, pp.plane), *se = to_cplx(sext_d, pp.plane);
+  const size_t nin = (size_t)M * nr;
   int rc = 0;
-  for (int n = 0; n < nsteps && rc == 0; n++) rc = step_once(&pp, S, jx, jr, jt, se);
+  for (int n = 0; n < nsteps && rc == 0; n++) {
+    cplx *irp = in_rp_d ? to_cplx(in_rp_d + 2 * (size_t)n * istride, nin) : NULL;
+    cplx *itm = in_tm_d ? to_cplx(in_tm_d + 2 * (size_t)n * istride, nin) : NULL;
+    pp.in_rp = irp;
+    pp.in_tm = itm;
+    rc = step_once(&pp, S, jx, jr, jt, se);
+    free(irp);
+    free(itm);
+  }
   for (size_t q = 0; q < ns; q++) {
     state_d[2 * q] = (double)RE(S[q]);
     state_d[2 * q + 1] = (double)IM(S[q]);
   }
   free(S); free(jx); free(jr); free(jt); free(se);
   return rc;
+}
+
+int ora_step_n(int nx, int nr, int M, double h, double dr, double m_a, double g,
+               int flags, double *state_d, const double *jx_d, const double *jr_d,
+               const double *jt_d, const double *sext_d, int nsteps) {
+  return ora_step_inflow(nx, nr, M, h, dr, m_a, g, flags, state_d, jx_d, jr_d, jt_d, sext_d, NULL, NULL, 0,
+                         nsteps);
 }
 
 int ora_step(int nx, int nr, int M, double h, double dr, double m_a, double g,

@@ -252,11 +252,26 @@ bool sources_equal(const qds_handle *h, int i, const qds_sources *src, long long
 
 bool any_strided(const qds_handle *h) {
   for (int i = 0; i < h->n_inst; i++) {
-    const long long s = h->fp32 ? reinterpret_cast<const Inst<float> *>(h->h_inst[i].data())->sstride
-                                : reinterpret_cast<const Inst<double> *>(h->h_inst[i].data())->sstride;
-    if (s) return true;
+    long long s, si;
+    if (h->fp32) {
+      const Inst<float> *I = reinterpret_cast<const Inst<float> *>(h->h_inst[i].data());
+      s = I->sstride; si = I->istride;
+    } else {
+      const Inst<double> *I = reinterpret_cast<const Inst<double> *>(h->h_inst[i].data());
+      s = I->sstride; si = I->istride;
+    }
+    if (s || si) return true;
   }
   return false;
+}
+
+// Injection arrays of instance i (NULL: none).
+template <class R>
+void set_inflow_i(qds_handle *h, int i, const void *tr_plus, const void *tth_minus, long long stride) {
+  Inst<R> *I = reinterpret_cast<Inst<R> *>(h->h_inst[i].data());
+  I->in_rp = (const C<R> *)tr_plus;
+  I->in_tm = (const C<R> *)tth_minus;
+  I->istride = stride;
 }
 
 size_t inst_size(const qds_handle *h) { return h->fp32 ? sizeof(Inst<float>) : sizeof(Inst<double>); }
@@ -705,6 +720,17 @@ int qds_set_sources_i(qds_handle *h, int i, const qds_sources *src, long long st
   if (sources_equal(h, i, src, stride)) return QDS_OK;
   if (h->fp32) set_sources_i<float>(h, i, src, stride);
   else set_sources_i<double>(h, i, src, stride);
+  return upload_inst(h, (cudaStream_t)stream);
+}
+
+int qds_set_inflow_i(qds_handle *h, int i, const void *tr_plus_dev, const void *tth_minus_dev, long long stride,
+                     void *stream) {
+  if (!h || i < 0 || i >= h->n_inst) return fail(QDS_ERR_INVALID_ARG, "bad handle or instance");
+  if (stride < 0) return fail(QDS_ERR_INVALID_ARG, "negative inflow stride");
+  if ((tr_plus_dev || tth_minus_dev) && (h->params[i].flags & QDS_X_PERIODIC))
+    return fail(QDS_ERR_INVALID_ARG, "injection at x_min needs an open x boundary");
+  if (h->fp32) set_inflow_i<float>(h, i, tr_plus_dev, tth_minus_dev, stride);
+  else set_inflow_i<double>(h, i, tr_plus_dev, tth_minus_dev, stride);
   return upload_inst(h, (cudaStream_t)stream);
 }
 

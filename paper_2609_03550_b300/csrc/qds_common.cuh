@@ -99,6 +99,11 @@ struct Inst {
   C<R> *scratch;         // pass mode: Gamma_a, j_a,x, j_a,r, j_a,th planes
   const C<R> *jx, *jr, *jt, *sext;  // optional sources [M][nx][nr]
   long long sstride;                // elements between the sources of consecutive steps (0: the same every step)
+  // optional laser injection at x_min: the inflow T_r^+, T_th^- of the
+  // exterior cell behind x_min, [M][nr] each, istride elements apart from
+  // step to step (0: the same every step)
+  const C<R> *in_rp, *in_tm;
+  long long istride;
 };
 
 // Row stride of the working layout for precision R.

@@ -122,6 +122,7 @@ void emu_march_kernel(EmuState<R, M> &S, const Inst<R> &I0, int n, uint32_t flag
     for (int tid = 0; tid < nth; tid++) {
       march_ctx<R, M, RB, KIND>(ctx[tid], I, it, sm, (unsigned long long)n, tid);
       ctx[tid].jx = I.jx; ctx[tid].jr = I.jr; ctx[tid].jt = I.jt; ctx[tid].sext = I.sext;
+      ctx[tid].in_rp = I.in_rp; ctx[tid].in_tm = I.in_tm;
       ctx[tid].state_len = S.E;
       regs[tid].gam_prev = regs[tid].gam = regs[tid].tap_prev = regs[tid].tam_prev = zero<R>();
       regs[tid].bad = false;
@@ -149,6 +150,7 @@ void emu_march_kernel(EmuState<R, M> &S, const Inst<R> &I0, int n, uint32_t flag
       if constexpr (KIND == 0) {
         // the boundary warp (lane k: the outer half row of mode k) works in
         // the same phases as the main threads; its writes do not overlap theirs
+        for (int tid = 0; tid < nth; tid++) k1_inflow<R, M, RB>(ctx[tid], L);
         for (int tid = 0; tid < nth; tid++) k1_p1<R, M, RB>(ctx[tid], L);
         for (int k = 0; k < M; k++) {
           const int t = k * RB + (nr - 1 - it.rb0);
@@ -190,7 +192,8 @@ bool emu_march_rb(EmuState<R, M> &S, const Inst<R> &I, int n, uint32_t flags, in
 template <class R, int M>
 void emu_steps(const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
                uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext,
-               int nsteps, int RB1, int RB2, int seg, int mode) {
+               const double *in_rp, const double *in_tm, long long istride, int nsteps, int RB1, int RB2, int seg,
+               int mode) {
   EmuState<R, M> S;
   S.nx = nx; S.nr = nr; S.ld = row_stride<R>(nr);
   const int ld = S.ld;
@@ -236,7 +239,17 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
   I.sext = sext ? sj[3].data() : nullptr;
   S.scratch.assign(4 * P, mk<R>((R)1e30, (R)1e30));
   const bool ar = (flags & F_AREM) != 0;
+  const size_t nin = (size_t)M * nr;
+  std::vector<C<R>> irp(nin), itm(nin);
   for (int n = 0; n < nsteps; n++) {
+    // injection at x_min of step n (istride complex elements per step)
+    I.in_rp = I.in_tm = nullptr;
+    for (size_t q = 0; q < nin; q++) {
+      if (in_rp) irp[q] = mk<R>((R)in_rp[2 * (n * istride + q)], (R)in_rp[2 * (n * istride + q) + 1]);
+      if (in_tm) itm[q] = mk<R>((R)in_tm[2 * (n * istride + q)], (R)in_tm[2 * (n * istride + q) + 1]);
+    }
+    if (in_rp) I.in_rp = irp.data();
+    if (in_tm) I.in_tm = itm.data();
     if (mode == 0) {
       emu_flat_step<R, M>(S, I, n, flags);
     } else {
@@ -273,30 +286,44 @@ void emu_steps(const double *canon, double *out, int nx, int nr, double h, doubl
 
 template <class R>
 int dispatch(int M, const double *canon, double *out, int nx, int nr, double h, double dr, double m_a, double g,
-             uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext, int nsteps,
-             int RB1, int RB2, int seg, int mode) {
-  switch (M) {
-    case 1: emu_steps<R, 1>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
-    case 2: emu_steps<R, 2>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
-    case 3: emu_steps<R, 3>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
-    case 4: emu_steps<R, 4>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode); return 0;
-  }
+             uint32_t flags, const double *jx, const double *jr, const double *jt, const double *sext,
+             const double *in_rp, const double *in_tm, long long istride, int nsteps, int RB1, int RB2, int seg,
+             int mode) {
+#define QDS_EMU_CASE(MM)                                                                                 \
+  case MM:                                                                                               \
+    emu_steps<R, MM>(canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, in_rp, in_tm, istride, \
+                     nsteps, RB1, RB2, seg, mode);                                                       \
+    return 0;
+  switch (M) { QDS_EMU_CASE(1) QDS_EMU_CASE(2) QDS_EMU_CASE(3) QDS_EMU_CASE(4) }
+#undef QDS_EMU_CASE
   return 1;
 }
 
 }  // namespace
 
 // mode 0: flat stage passes; 1: x-marching kernels (rows RB1, RB2 per CTA,
-// seg columns per CTA).
+// seg columns per CTA).  in_rp / in_tm: laser injection at x_min ([M][nr]
+// complex per step, istride complex elements apart; may be NULL).
+extern "C" int qds_emu_steps_inflow(int M, const double *canon, double *out, int nx, int nr, double h, double dr,
+                                    double m_a, double g, uint32_t flags, const double *jx, const double *jr,
+                                    const double *jt, const double *sext, const double *in_rp,
+                                    const double *in_tm, long long istride, int nsteps, int RB1, int RB2, int seg,
+                                    int mode) {
+  auto ok_rb = [](int rb) { return rb == 8 || rb == 16 || rb == 24 || rb == 32 || rb == 64; };
+  if (!ok_rb(RB1) || !ok_rb(RB2) || seg < 1 || istride < 0) return 2;
+  if (flags & F_FP32)
+    return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, in_rp, in_tm, istride,
+                           nsteps, RB1, RB2, seg, mode);
+  return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, in_rp, in_tm, istride,
+                          nsteps, RB1, RB2, seg, mode);
+}
+
 extern "C" int qds_emu_steps(int M, const double *canon, double *out, int nx, int nr, double h, double dr,
                              double m_a, double g, uint32_t flags, const double *jx, const double *jr,
                              const double *jt, const double *sext, int nsteps, int RB1, int RB2, int seg,
                              int mode) {
-  auto ok_rb = [](int rb) { return rb == 8 || rb == 16 || rb == 24 || rb == 32 || rb == 64; };
-  if (!ok_rb(RB1) || !ok_rb(RB2) || seg < 1) return 2;
-  if (flags & F_FP32)
-    return dispatch<float>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode);
-  return dispatch<double>(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nsteps, RB1, RB2, seg, mode);
+  return qds_emu_steps_inflow(M, canon, out, nx, nr, h, dr, m_a, g, flags, jx, jr, jt, sext, nullptr, nullptr, 0,
+                              nsteps, RB1, RB2, seg, mode);
 }
 
 // ---------------------------------------------------------------------------

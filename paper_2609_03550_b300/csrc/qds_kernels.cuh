@@ -24,6 +24,13 @@ __device__ __forceinline__ const C<R> *step_src(const C<R> *a, const Inst<R> &I,
   return a + (long long)(ctrl->step - ctrl->src_base) * I.sstride;
 }
 
+// Injection arrays of the current step (null when not injecting).
+template <class R>
+__device__ __forceinline__ const C<R> *step_inflow(const C<R> *a, const Inst<R> &I, const Ctrl *ctrl) {
+  if (!a || I.istride == 0) return a;
+  return a + (long long)(ctrl->step - ctrl->src_base) * I.istride;
+}
+
 // Per-instance prefactors of the energies (diag_final_all_kernel).
 struct Scal4 {
   double x, y, z, w;
@@ -45,6 +52,8 @@ __device__ __forceinline__ Tile<R, M, FAST> pass_tile(const Inst<R> &I, int4 td,
   t.jr = step_src(I.jr, I, ctrl);
   t.jt = step_src(I.jt, I, ctrl);
   t.sext = step_src(I.sext, I, ctrl);
+  t.in_rp = step_inflow(I.in_rp, I, ctrl);
+  t.in_tm = step_inflow(I.in_tm, I, ctrl);
   t.nx = I.nx;
   t.nr = I.nr;
   t.ld = I.ld;

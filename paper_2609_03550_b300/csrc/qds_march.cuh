@@ -164,6 +164,7 @@ struct MarchCtx : MarchShape<R, M, RB_, KIND> {
   size_t P;                         // elements per field (M planes)
   R h, dr, ih, idr, ma2, gs, gj;
   const C<R> *jx, *jr, *jt, *sext;  // this step's sources [M][nx][nr] in window order (may be null)
+  const C<R> *in_rp, *in_tm;        // this step's injection at x_min, [M][nr] (may be null)
   const C<R> *o;                    // old state (global; phi_prev)
   C<R> *n;                          // new state (global)
   C<R> *scr;                        // scratch planes (global; j_a in planes 1..3)
@@ -532,6 +533,21 @@ QDS_HD C<R> conv3(int m, const C<R> (&A)[3][M], const C<R> (&B)[3][M]) {
     }
   }
   return mk<R>(R(0.5) * ((sr[0] + sr[1]) + sr[2]), R(0.5) * ((si[0] + si[1]) + si[2]));
+}
+
+// ---------------------------------------------------------------------------
+// Laser injection at x_min: the ring slot of window column -1 (read as zeros
+// by the bulk copy: the open boundary of Eq. em_x_open) takes the injected
+// inflow T_r^+ and T_th^- of the EM field on the thread's row, before the
+// shift into cell 0 reads it (two iterations later).
+// ---------------------------------------------------------------------------
+template <class R, int M, int RB>
+QDS_HD void k1_inflow(const MarchCtx<R, M, RB, 0> &c, int L) {
+  if (L != -1 || c.per || c.j >= c.nr || (!c.in_rp && !c.in_tm)) return;
+  C<R> *p = const_cast<C<R> *>(c.rc[0]);
+  const size_t q = (size_t)c.k * c.nr + c.j;
+  p[0] = c.in_rp ? ldg(c.in_rp + q) : zero<R>();
+  p[3 * M * RB] = c.in_tm ? ldg(c.in_tm + q) : zero<R>();
 }
 
 // ---------------------------------------------------------------------------
@@ -1198,6 +1214,8 @@ __global__ void __launch_bounds__(march_threads<M, RB, KIND>(), KIND == 1 ? 2 : 
   c.jr = step_src(I.jr, I, ctrl);
   c.jt = step_src(I.jt, I, ctrl);
   c.sext = step_src(I.sext, I, ctrl);
+  c.in_rp = step_inflow(I.in_rp, I, ctrl);
+  c.in_tm = step_inflow(I.in_tm, I, ctrl);
   constexpr int NS = Sh::NS;
   constexpr int BAR = ((KIND == 0 ? Sh::O_ST + Sh::PL : Sh::O_AF) * (int)sizeof(C<R>) + 15) / 16 * 16;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smraw + BAR);
@@ -1237,6 +1255,7 @@ __global__ void __launch_bounds__(march_threads<M, RB, KIND>(), KIND == 1 ? 2 : 
     const bool ok = L > C1 || mbar_wait(&bar[(L - L0) % NS], (unsigned)(((L - L0) / NS) & 1));
     if (ok) {
       if constexpr (KIND == 0) {
+        if (!bwarp) k1_inflow<R, M, RB>(c, L);
         if (!bwarp) k1_p1<R, M, RB>(c, L);
         else if (bact) outer_p1<R, M, RB>(c, L);
       } else {

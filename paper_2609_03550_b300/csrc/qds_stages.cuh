@@ -64,11 +64,13 @@ struct Tile {
   // values of the descriptor used per point, held in registers (loads
   // through I could not be hoisted past the stores of a pass)
   const C<R> *jx, *jr, *jt, *sext;
+  const C<R> *in_rp, *in_tm;  // injection at x_min (may be null)
   R gs, gj, ma2;
   uint32_t flags;
   QDS_HD void bind(const Inst<R> &d, const Inst<R> *dev) {
     I = dev;
     jx = d.jx; jr = d.jr; jt = d.jt; sext = d.sext;
+    in_rp = d.in_rp; in_tm = d.in_tm;
     gs = d.gs; gj = d.gj; ma2 = d.ma2;
     flags = d.flags;
   }
@@ -129,7 +131,16 @@ struct Tile {
 #endif
       return ldg(o + eidx(field, k, sl, j));
     }
-    if (sl < 0 || (unsigned)j >= (unsigned)nr) return zero<R>();
+    if ((unsigned)j >= (unsigned)nr) return zero<R>();
+    if (sl < 0) {
+      // the exterior cell behind x_min: zero (open boundary, Eq. em_x_open),
+      // or the injected inflow T_r^+ / T_th^- of the EM field
+      if (w == -1 && !per) {
+        if (field == TRP && in_rp) return ldg(in_rp + (size_t)k * nr + j);
+        if (field == TTM && in_tm) return ldg(in_tm + (size_t)k * nr + j);
+      }
+      return zero<R>();
+    }
 #if defined(QDS_EMU)
     QDS_CHECK(eidx(field, k, sl, j) < state_len, "cell read");
 #endif

@@ -85,6 +85,28 @@ def add_lasers(buf, M, nx, nr, dr, lasers, x_offset=0.0):
     return buf
 
 
+def laser_inflow(lasers, M, nr, dr, nsteps, h=1.0):
+    """Inflow arrays for injecting forward m = 1 pulses at x_min
+    (qds_set_inflow_i): T_r^+ and T_theta^- of the exterior cell behind x_min
+    at steps 0..nsteps-1, each [nsteps, M, nr] complex128.  A pulse given
+    with its centre x0 < 0 (window coordinates, behind the box) enters as a
+    forward wave would: the value at step n is its initial profile at
+    x = -1 - n h (the c dt = dx shift), i.e. the field on the plane x_min
+    without the diffraction it would undergo before reaching it."""
+    in_rp = np.zeros((nsteps, M, nr), np.complex128)
+    in_tm = np.zeros((nsteps, M, nr), np.complex128)
+    if M < 2:
+        return in_rp, in_tm
+    x = (-1.0 - h * np.arange(nsteps))[:, None]
+    r_half = ((np.arange(nr) + 0.5) * dr)[None, :]
+    r_int = (np.arange(nr) * dr)[None, :]
+    for L in lasers:
+        p = 1.0 if L.pol == "y" else 1j
+        in_rp[:, 1] += 2.0 * p * L.amplitude(x, r_half)
+        in_tm[:, 1] += -2j * p * L.amplitude(x, r_int)
+    return in_rp, in_tm
+
+
 def random_state(rng, M, nx, nr, scale=1.0, axis_consistent=True):
     """Random complex state for tiny-grid parity checks.  Mode 0 is kept real
     (the m = 0 fields of a real field are real).  With ``axis_consistent`` the

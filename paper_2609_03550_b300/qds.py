@@ -63,6 +63,7 @@ def lib():
             "qds_get_state_i": (i, [H, i, vp, vp]),
             "qds_step": (i, [H, ctypes.POINTER(_Sources), i, vp]),
             "qds_set_sources_i": (i, [H, i, ctypes.POINTER(_Sources), ctypes.c_longlong, vp]),
+            "qds_set_inflow_i": (i, [H, i, vp, vp, ctypes.c_longlong, vp]),
             "qds_diagnostics": (i, [H, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_diagnostics_i": (i, [H, i, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_num_instances": (i, [H]),
@@ -209,6 +210,23 @@ class QDSSolver:
         self._per_instance = True
         _check(lib().qds_set_sources_i(self.h, int(i), ctypes.byref(src), plane if per_step else 0,
                                        _stream_ptr(stream)))
+
+    def set_inflow(self, i=0, tr_plus=None, tth_minus=None, per_step=False, stream=None):
+        """Laser injection at x_min of instance ``i`` for the following
+        ``step`` calls (qds_set_inflow_i): the inflow T_r^+ and T_theta^- of
+        the exterior cell behind x_min, tensors [M, nr] (the same every step)
+        or [n, M, nr] (slice k drives step k of each later call, per_step);
+        None gives zero inflow (both None: the open boundary)."""
+        p = self.params[i]
+        plane = p.n_modes * p.nr
+        for t in (tr_plus, tth_minus):
+            if t is not None:
+                assert t.numel() % plane == 0 and (per_step or t.numel() == plane)
+        keep = getattr(self, "_inflow_keep", {})
+        keep[i] = (tr_plus, tth_minus)
+        self._inflow_keep = keep
+        _check(lib().qds_set_inflow_i(self.h, int(i), self._src_ptr(tr_plus), self._src_ptr(tth_minus),
+                                      plane if per_step else 0, _stream_ptr(stream)))
 
     def adjoint_step(self, fwd, lam, i: int = 0, jx=None, jth=None, s_ext=None, dLdg=None, stream=None):
         """One transposed step (qds_adjoint_step): ``fwd`` is the canonical

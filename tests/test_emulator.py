@@ -92,3 +92,48 @@ def test_emulated_kernels_fp32_scaled(M, mode, nr):
     got = run_emu(M, buf, nx, nr, dr, 0.0, g, flags | 32, src, 4, mode=mode, rows=(24, 16), seg=6)
     for name, e in group_errors(got, ref, M, nx, nr).items():
         assert e < 2e-6, (name, e)
+
+
+def run_emu_inflow(M, buf, nx, nr, dr, m_a, g, flags, src, inflow, nsteps, mode=MARCH, rows=(24, 16), seg=7):
+    L = emu()
+    dp = ctypes.POINTER(ctypes.c_double)
+    if not hasattr(L, "_inflow_set"):
+        L.qds_emu_steps_inflow.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
+                                           dp, dp, dp, dp, dp, dp, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L._inflow_set = True
+    out = np.zeros_like(buf)
+    s = [None if a is None else np.ascontiguousarray(a, np.complex128) for a in src]
+    ins = [np.ascontiguousarray(a, np.complex128) for a in inflow]
+    P = lambda a: None if a is None else a.ctypes.data_as(dp)
+    rc = L.qds_emu_steps_inflow(M, P(buf), P(out), nx, nr, 1.0, dr, m_a, g, flags, *[P(a) for a in s],
+                                P(ins[0]), P(ins[1]), M * nr, nsteps, rows[0], rows[1], seg, mode)
+    assert rc == 0
+    return out
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 4])
+@pytest.mark.parametrize("flags", [0, 1 | 2, 1 | 2 | 4, 1 | 2 | 16])
+@pytest.mark.parametrize("mode,rows,seg", [(FLAT, (24, 16), 7), (MARCH, (16, 8), 5), (MARCH, (64, 64), 64)])
+def test_injection_at_xmin_matches_oracle(M, flags, mode, rows, seg):
+    """Laser injection at x_min (a different inflow T_r^+, T_th^- every step)
+    on random states with sources: the flat passes and the x-marching
+    kernels (several bands, ragged segments) against the oracle."""
+    nx, nr, N = 23, 19, 4
+    dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
+    buf, src = random_case(M * 7 + flags + 3, M, nx, nr)
+    rng = np.random.default_rng(M + 100 * flags)
+    inflow = [rng.standard_normal((N, M, nr)) + 1j * rng.standard_normal((N, M, nr)) for _ in range(2)]
+    ref = oracle_run_inflow(buf, M, nx, nr, dr, flags, N, g, m_a, src, inflow)
+    got = run_emu_inflow(M, buf, nx, nr, dr, m_a, g, flags, src, inflow, N, mode=mode, rows=rows, seg=seg)
+    for name, e in group_errors(got, ref, M, nx, nr).items():
+        assert e < 1e-13, (name, e)
+
+
+def oracle_run_inflow(buf, M, nx, nr, dr, flags, nsteps, g, m_a, src, inflow):
+    import oracle
+    st = oracle.State(M, nx, nr, buf)
+    oracle.step(dict(nx=nx, nr=nr, M=M, h=1.0, dr=dr, g=g, m_a=m_a, flags=flags & 31), st, *src,
+                nsteps=nsteps, extended=True, inflow=inflow)
+    return st.buf

@@ -301,3 +301,33 @@ def test_per_step_sources_in_one_call_match_step_by_step(mode):
                     *[srcs[0][c][k].cpu().numpy() for c in range(3)], extended=True)
     for name, e in group_errors(ref[0], st.buf, M, nx, nr).items():
         assert e < 1e-12, (name, e)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("M,flags", [(1, 0), (2, 3), (3, 7), (4, 19), (2, 7)])
+def test_fp64_parity_with_injection_at_xmin(M, flags, mode):
+    """Laser injection at x_min with a different inflow every step (one call
+    of N steps reading [N, M, nr] slices), random state and sources: against
+    the oracle's injection (Eq. em_x_open with prescribed inflow)."""
+    import oracle
+    nx, nr, N = 37, 21, 20  # 20 steps: one captured graph of 16 steps and 4 single launches
+    dr, m_a, g = stable_dr(M, 0.1), 0.1, 0.3
+    buf, src = random_case(M * 13 + flags, M, nx, nr)
+    rng = np.random.default_rng(M + flags)
+    inflow = [rng.standard_normal((N, M, nr)) + 1j * rng.standard_normal((N, M, nr)) for _ in range(2)]
+    st = oracle.State(M, nx, nr, buf)
+    oracle.step(dict(nx=nx, nr=nr, M=M, h=1.0, dr=dr, g=g, m_a=m_a, flags=flags), st, *src, nsteps=N,
+                extended=True, inflow=inflow)
+    p = Q.Params(nx, nr, M, dr, g=g, m_a=m_a, flags=flags)
+    s = Q.QDSSolver(p, device=DEV)
+    s.set_step_mode(mode)
+    s.set_state(torch.from_numpy(buf).to(DEV))
+    srcs = [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in src]
+    s.set_sources(0, *srcs)
+    tin = [torch.from_numpy(np.ascontiguousarray(a)).to(DEV) for a in inflow]
+    s.set_inflow(0, tin[0], tin[1], per_step=True)
+    s.step(N)
+    torch.cuda.synchronize()
+    got = s.get_state().cpu().numpy()
+    for name, e in group_errors(got, st.buf, M, nx, nr).items():
+        assert e < 1e-12, (name, e)

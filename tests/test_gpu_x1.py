@@ -82,3 +82,52 @@ def test_x2_resolution_scan_approaches_the_paraxial_value():
     print("dx = lambda/20:", e20, "dx = lambda/40:", e40)
     assert abs(e40 - gold["qds_vg_error_lambda40"]) < gold["tolerance"]
     assert gold["paraxial_vg_error"] - gold["tolerance"] < e40 <= e20 + 1e-7
+
+
+def _vg_error_injected(ppw, mode):
+    """As _vg_error, but the pulse enters through x_min (qds_set_inflow_i,
+    the inflow characteristics of Eq. em_x_open prescribed) into an empty
+    box that stays put; the centroid is fitted over the same interval."""
+    lam = float(ppw)
+    dr, w0 = lam / 2, 10 * lam
+    steps = 300 * ppw + int(62.5 * lam)
+    nx, nr = steps + 40 * ppw, 50
+    x0 = -20 * lam                      # pulse centre behind x_min at t = 0
+    fit_start = 62.5 * lam - x0         # the centroid has moved 62.5 lambda past x = 0
+    L = I.Laser(1.0, lam, w0, 10 * lam, x0, "y")
+    n_in = int(40 * lam)                # the envelope is below 1e-15 of its peak after this
+    in_rp, in_tm = I.laser_inflow([L], 2, nr, dr, n_in)
+    s = Q.QDSSolver(Q.Params(nx, nr, 2, dr, flags=0), device=DEV)
+    s.set_step_mode(mode)
+    s.set_state(torch.zeros(I.state_size(2, nx, nr), dtype=torch.complex128, device=DEV))
+    t_rp = torch.from_numpy(in_rp).to(DEV)
+    t_tm = torch.from_numpy(in_tm).to(DEV)
+    s.set_inflow(0, t_rp, t_tm, per_step=True)
+    s.step(n_in)                        # one call of n_in steps reads slice k at step k
+    s.set_inflow(0, None, None)
+    x = np.arange(nx)
+    every = 25 * ppw // 10
+    ts, xs = [], []
+    n = n_in
+    while True:
+        if n % every == 0 and n >= fit_start:
+            U = s.diagnostics(profile=True)["profile"].cpu().numpy()
+            xs.append((x * U).sum() / U.sum())
+            ts.append(n)
+        if n >= steps:
+            break
+        k = min(every - n % every, steps - n)
+        s.step(k)
+        n += k
+    vg = np.polyfit(np.array(ts, float), np.array(xs), 1)[0]
+    return 1.0 - vg
+
+
+@pytest.mark.parametrize("mode", [Q.STEP_FLAT, Q.STEP_MARCH])
+def test_x1_with_the_pulse_injected_at_xmin(mode):
+    """NEXT-2: the paper injects its vacuum pulse through the boundary; the
+    injected pulse reproduces |v_g/c - 1| = 2.61e-4 at dx = lambda/10."""
+    gold = _golden()
+    err = _vg_error_injected(10, mode)
+    print("injected, dx = lambda/10: |v_g/c - 1| =", err)
+    assert abs(err - gold["qds_vg_error"]) < gold["tolerance"]

@@ -527,3 +527,45 @@ def test_energy_diagnostic_matches_closed_forms(m):
         d = oracle.diagnostics(dict(nx=nx, nr=nr, M=M, h=h, dr=dr, m_a=ma), st)
         want = dens * ma * ma * abs(pv) ** 2 * disc_half * L
         assert abs(d["axion"] - want) <= 1e-12 * want, (d["axion"], want)
+
+
+# ---------------------------------------------------------------------------
+# Laser injection at x_min (the inflow characteristics of Eq. em_x_open take
+# prescribed values instead of zero).  An r-independent m = 1 forward plane
+# wave fed in through x_min enters the box exactly: the value injected at
+# step n sits in cell c after step n + 1 + c (the c dt = dx shift, Sec. 2.1;
+# all Gamma / Phi vanish for this wave), and nothing else appears.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("pol", ["y", "z"])
+def test_injected_plane_wave_enters_exactly(pol):
+    M, nx, nr, N = 2, 48, 40, 9
+    p = dict(nx=nx, nr=nr, M=M, h=1.0, dr=2.0, flags=0)
+    st = oracle.State(M, nx, nr)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    pf = 1.0 if pol == "y" else 1j
+    in_rp = np.zeros((N, M, nr), np.complex128)
+    in_tm = np.zeros((N, M, nr), np.complex128)
+    in_rp[:, 1, :] = 2 * pf * f[:, None]
+    in_tm[:, 1, :] = -2j * pf * f[:, None]
+    oracle.step(p, st, nsteps=N, inflow=(in_rp, in_tm))
+    rows = slice(0, nr - 3 * N)  # rows not yet reached by the outer-boundary signal
+    want = np.zeros(nx, np.complex128)
+    want[:N] = f[::-1]           # cell c holds the value injected at step N - 1 - c
+    assert np.array_equal(st["Trp"][1][:, rows], 2 * pf * want[:, None].repeat(nr, 1)[:, rows])
+    assert np.array_equal(st["Ttm"][1][:, rows], -2j * pf * want[:, None].repeat(nr, 1)[:, rows])
+    assert not np.any(st["Trm"][1][:, rows]) and not np.any(st["Ttp"][1][:, rows])
+    assert not np.any(st["Ex"][:, :, rows]) and not np.any(st["Bx"][:, :, rows])
+    assert not np.any(st.fields[:, 0])  # m = 0 untouched
+
+
+def test_zero_inflow_is_the_open_boundary():
+    M, nx, nr = 3, 21, 11
+    from tests._helpers import random_case, stable_dr
+    buf, src = random_case(41, M, nx, nr)
+    p = dict(nx=nx, nr=nr, M=M, h=1.0, dr=stable_dr(M), m_a=0.1, g=0.3, flags=oracle.AXION | oracle.AREM)
+    a, b = oracle.State(M, nx, nr, buf), oracle.State(M, nx, nr, buf)
+    oracle.step(p, a, *src, nsteps=3)
+    z = np.zeros((M, nr), np.complex128)
+    oracle.step(p, b, *src, nsteps=3, inflow=(z, z))
+    assert np.array_equal(a.buf, b.buf)
