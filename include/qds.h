@@ -218,6 +218,29 @@ void qds_free(qds_handle *h);
 const char *qds_last_error(void);
 
 /* ---------------------------------------------------------------------------
+ * Mode products for many retained modes (Sec. 3.3).  For npts points:
+ *   out[m][q] = sum_{p < npairs} w[p] C_m{A_p[.][q], B_p[.][q]},  m < n_modes,
+ * C_m the mode convolution of Eq. mode_convolution (the form of the axion
+ * source, Eqs. source_mode_zero/_m, and of the axion current, Eqs.
+ * jax/jar/jat_mode; w folds their signs and halves).  method:
+ *   QDS_MODES_DIRECT  the convolution sums, O(n_modes^2) per point;
+ *   QDS_MODES_THETA   the theta-grid procedure of Sec. 3.3: every field
+ *                     sampled on N angles by an FFT of its mode vector, the
+ *                     products summed over the pairs pointwise, projected
+ *                     back by one more FFT; N the power of two >= 3 n_modes
+ *                     - 2 (qds_mode_products_theta_points), the fewest angles
+ *                     that leave the retained modes free of aliasing.  Exact
+ *                     for real fields (real m = 0 components).
+ * a_dev, b_dev: [npairs][n_modes][npts], out_dev: [n_modes][npts], complex
+ * device arrays (complex64 if fp32 else complex128); w_host: npairs doubles.
+ * 1 <= n_modes <= 64, 1 <= npairs <= 4.  Asynchronous on stream. */
+#define QDS_MODES_DIRECT 0
+#define QDS_MODES_THETA 1
+int qds_mode_products(int n_modes, int npts, int npairs, const void *a_dev, const void *b_dev, const double *w_host,
+                      void *out_dev, int method, int fp32, void *stream);
+int qds_mode_products_theta_points(int n_modes);
+
+/* ---------------------------------------------------------------------------
  * Adjoint (transpose) of one step of the EM group and the axion (Sec. 2;
  * the transpose of the +x transport shift is the -x shift).  For a real
  * functional L of the state the adjoint of a complex value z is

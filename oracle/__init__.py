@@ -47,6 +47,11 @@ def lib(extended=False):
         L.ora_diagnostics.restype = ctypes.c_int
         L.ora_mode_conv.argtypes = [ctypes.c_int, dp, dp, dp]
         L.ora_mode_conv.restype = None
+        L.ora_mode_products.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+        L.ora_mode_products.restype = ctypes.c_int
+        L.ora_mode_products_theta.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp,
+                                              dp, dp]
+        L.ora_mode_products_theta.restype = ctypes.c_int
         L.ora_set_threads.argtypes = [ctypes.c_int]
         L.ora_set_threads.restype = ctypes.c_int
         _libs[extended] = L
@@ -131,6 +136,26 @@ def mode_conv(A, B):
     B = np.ascontiguousarray(B, np.complex128)
     out = np.zeros(A.size, np.complex128)
     lib().ora_mode_conv(A.size, _ptr(A), _ptr(B), _ptr(out))
+    return out
+
+
+def mode_products(A, B, w, ntheta=None):
+    """sum_p w[p] C_m{A[p], B[p]} at every point (Sec. 3.3): A, B complex
+    [npairs, M, npts], w [npairs]; returns [M, npts].  ntheta None: the
+    convolution sums (Eq. mode_convolution); else the theta-grid procedure
+    with ntheta angles (plain DFT sums)."""
+    A = np.ascontiguousarray(A, np.complex128)
+    B = np.ascontiguousarray(B, np.complex128)
+    w = np.ascontiguousarray(w, np.float64)
+    npairs, M, npts = A.shape
+    out = np.zeros((M, npts), np.complex128)
+    wp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if ntheta is None:
+        rc = lib().ora_mode_products(M, npairs, npts, _ptr(A), _ptr(B), wp, _ptr(out))
+    else:
+        rc = lib().ora_mode_products_theta(M, npairs, npts, int(ntheta), _ptr(A), _ptr(B), wp, _ptr(out))
+    if rc != 0:
+        raise RuntimeError(f"mode products failed: {rc}")
     return out
 
 

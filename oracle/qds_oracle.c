@@ -169,6 +169,72 @@ void ora_mode_conv(int M, const double *A, const double *B, double *out) {
 }
 
 /* ------------------------------------------------------------------------
+ * Mode products of many retained modes at many points (Sec. 3.3): for each
+ * point q, out^(m) = sum_p w_p C_m{A_p, B_p}, m = 0..M-1.  A, B: [npairs][M]
+ * [npts] complex, out: [M][npts].
+ *   ora_mode_products: the convolution sums of Eq. mode_convolution;
+ *   ora_mode_products_theta: the theta-grid procedure of Sec. 3.3 with
+ *   ntheta equally spaced angles theta_s = 2 pi s / ntheta: each field
+ *   F(theta_s) = Re sum_k F^(k) e^{-i k theta_s} (Eq. fourier_decomp), the
+ *   products summed over the pairs pointwise, projected back by
+ *   C_m = (2 / ntheta) sum_s P(theta_s) e^{i m theta_s}, halved for m = 0.
+ *   Plain DFT sums (no FFT): the reference for the transform-based kernels.
+ * ---------------------------------------------------------------------- */
+static cplx load_c(const double *a, size_t q) { return a[2 * q] + I * a[2 * q + 1]; }
+
+int ora_mode_products(int M, int npairs, int npts, const double *A, const double *B, const double *w,
+                      double *out) {
+  if (M < 1 || npairs < 1 || npts < 0) return -1;
+  cplx *a = malloc(sizeof(cplx) * M), *b = malloc(sizeof(cplx) * M);
+  if (!a || !b) { free(a); free(b); return -2; }
+  for (int q = 0; q < npts; q++)
+    for (int m = 0; m < M; m++) {
+      cplx s = 0;
+      for (int p = 0; p < npairs; p++) {
+        for (int k = 0; k < M; k++) {
+          a[k] = load_c(A, ((size_t)p * M + k) * npts + q);
+          b[k] = load_c(B, ((size_t)p * M + k) * npts + q);
+        }
+        s += w[p] * mode_conv(M, m, a, b);
+      }
+      out[2 * ((size_t)m * npts + q)] = (double)RE(s);
+      out[2 * ((size_t)m * npts + q) + 1] = (double)IM(s);
+    }
+  free(a); free(b);
+  return 0;
+}
+
+int ora_mode_products_theta(int M, int npairs, int npts, int ntheta, const double *A, const double *B,
+                            const double *w, double *out) {
+  if (M < 1 || npairs < 1 || npts < 0 || ntheta < 1) return -1;
+  for (int q = 0; q < npts; q++) {
+    for (int m = 0; m < M; m++) {
+      cplx c = 0;
+      for (int s_ = 0; s_ < ntheta; s_++) {
+        const double th = 2.0 * 3.14159265358979323846 * s_ / ntheta;
+        double P = 0;
+        for (int p = 0; p < npairs; p++) {
+          double fa = 0, fb = 0;
+          for (int k = 0; k < M; k++) {
+            const cplx ak = load_c(A, ((size_t)p * M + k) * npts + q);
+            const cplx bk = load_c(B, ((size_t)p * M + k) * npts + q);
+            fa += (double)RE(ak * cexp(-I * (double)k * th));
+            fb += (double)RE(bk * cexp(-I * (double)k * th));
+          }
+          P += w[p] * fa * fb;
+        }
+        c += P * cexp(I * (double)m * th);
+      }
+      c *= 2.0 / ntheta;
+      if (m == 0) c *= 0.5;
+      out[2 * ((size_t)m * npts + q)] = (double)RE(c);
+      out[2 * ((size_t)m * npts + q) + 1] = (double)IM(c);
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------
  * Transverse field reconstruction (Eq. reconstruct_fields):
  *   E_r = (T_r^+ + T_r^-)/2, B_th = (T_r^+ - T_r^-)/2c,
  *   E_th = (T_th^+ + T_th^-)/2, B_r = (T_th^+ - T_th^-)/2c.

@@ -64,6 +64,8 @@ def lib():
             "qds_step": (i, [H, ctypes.POINTER(_Sources), i, vp]),
             "qds_set_sources_i": (i, [H, i, ctypes.POINTER(_Sources), ctypes.c_longlong, vp]),
             "qds_set_inflow_i": (i, [H, i, vp, vp, ctypes.c_longlong, vp]),
+            "qds_mode_products": (i, [i, i, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp, i, i, vp]),
+            "qds_mode_products_theta_points": (i, [i]),
             "qds_diagnostics": (i, [H, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_diagnostics_i": (i, [H, i, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_num_instances": (i, [H]),
@@ -347,3 +349,23 @@ class QDSSolver:
         a, b, c, d = (ctypes.c_int() for _ in range(4))
         _check(lib().qds_get_tile(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
         return dict(rows=a.value, cols=b.value, ctas=c.value, smem=d.value)
+
+
+MODES_DIRECT, MODES_THETA = 0, 1
+
+
+def mode_products(A, B, w, method=MODES_DIRECT, out=None, stream=None):
+    """sum_p w[p] C_m{A[p], B[p]} at every point (qds_mode_products): A, B
+    complex64 or complex128 CUDA tensors [npairs, M, npts], w a sequence of
+    npairs floats; returns [M, npts] (or fills ``out``).  method
+    MODES_DIRECT: the convolution sums; MODES_THETA: the theta-grid
+    procedure with FFTs (Sec. 3.3)."""
+    assert A.shape == B.shape and A.dim() == 3 and A.dtype == B.dtype and A.is_cuda
+    assert A.dtype in (torch.complex64, torch.complex128) and A.is_contiguous() and B.is_contiguous()
+    npairs, M, npts = A.shape
+    if out is None:
+        out = torch.empty((M, npts), dtype=A.dtype, device=A.device)
+    wa = (ctypes.c_double * npairs)(*[float(x) for x in w])
+    _check(lib().qds_mode_products(M, npts, npairs, A.data_ptr(), B.data_ptr(), wa, out.data_ptr(), int(method),
+                                   1 if A.dtype == torch.complex64 else 0, _stream_ptr(stream)))
+    return out

@@ -569,3 +569,35 @@ def test_zero_inflow_is_the_open_boundary():
     z = np.zeros((M, nr), np.complex128)
     oracle.step(p, b, *src, nsteps=3, inflow=(z, z))
     assert np.array_equal(a.buf, b.buf)
+
+
+# ---------------------------------------------------------------------------
+# The theta-grid procedure of Sec. 3.3 (fields sampled on ntheta angles,
+# products taken pointwise, projected back) reproduces the convolution sums
+# of Eq. mode_convolution exactly when ntheta >= 3M - 2: the product of two
+# fields with modes up to M - 1 has modes up to 2M - 2, and a mode q lands on
+# a retained mode m < M only if |q - m| is a multiple of ntheta, which needs
+# ntheta <= 3M - 3.  The bound is sharp: one angle fewer aliases.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 7, 12])
+def test_theta_grid_products_match_the_convolution_sums(M):
+    rng = np.random.default_rng(70 + M)
+    npairs, npts = 3, 5
+    A = rng.standard_normal((npairs, M, npts)) + 1j * rng.standard_normal((npairs, M, npts))
+    B = rng.standard_normal((npairs, M, npts)) + 1j * rng.standard_normal((npairs, M, npts))
+    A[:, 0] = A[:, 0].real  # real fields: the m = 0 components are real (Eq. fourier_decomp)
+    B[:, 0] = B[:, 0].real
+    w = np.array([1.0, 0.5, -0.5])
+    direct = oracle.mode_products(A, B, w)
+    nt = max(1, 3 * M - 2)
+    theta = oracle.mode_products(A, B, w, ntheta=nt)
+    scale = np.abs(direct).max()
+    assert np.abs(theta - direct).max() < 1e-13 * scale
+    if M >= 2:
+        alias = oracle.mode_products(A, B, w, ntheta=nt - 1)
+        assert np.abs(alias - direct).max() > 1e-3 * scale
+    # and the sums equal the per-pair Eq. mode_convolution of the step
+    if M <= 8:
+        q = 2
+        one = sum(w[p] * oracle.mode_conv(A[p, :, q], B[p, :, q]) for p in range(npairs))
+        assert np.allclose(direct[:, q], one, rtol=0, atol=1e-13 * scale)
