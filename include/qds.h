@@ -262,6 +262,39 @@ int qds_mode_products_theta_points(int n_modes);
  * needs QDS_AXION.  Runs in the handle's precision (QDS_FP32: complex64
  * arithmetic, results widened to complex128).  Asynchronous on stream. */
 size_t qds_adjoint_work_bytes(const qds_handle *h, int i);
+/* The same transpose without conversions, for the adjoint's
+ * checkpoint-and-recompute in the working precision:
+ * fwd_working_dev: a working snapshot of instance i (qds_save_working) taken
+ *   fwd_step steps after the state import, at the START of the step (its
+ *   EM planes are read; working row stride and window offset).
+ * lam_in_dev / lam_out_dev: the adjoint of the state after / before the step
+ *   in the canonical layout of qds_set_state but in the working precision
+ *   (complex64 with QDS_FP32, else complex128), physical variables; distinct
+ *   buffers (lam_out is written in full).
+ * work_dev: >= qds_adjoint_work_bytes_w(h, i) bytes, 256-byte aligned.
+ * Otherwise as qds_adjoint_step.  Asynchronous on stream. */
+size_t qds_adjoint_work_bytes_w(const qds_handle *h, int i);
+int qds_adjoint_step_w(qds_handle *h, int i, const qds_sources *src, const void *fwd_working_dev,
+                       unsigned long long fwd_step, const void *lam_in_dev, void *lam_out_dev, void *work_dev,
+                       size_t work_bytes, double *dLdg_dev, void *stream);
+
+/* Working snapshots, the checkpoints of the adjoint's recompute (the paper
+ * defines no adjoint; these serve qds_adjoint_step_w): the state of instance
+ * i as the kernels hold it (working precision, 1/g-scaled axion and
+ * regenerated groups in FP32, padded row stride, ring offset of the moving
+ * window), qds_working_bytes(h, i) bytes.
+ * qds_steps_taken: steps since the last qds_set_state / qds_restore_working
+ *   (the host's count of the qds_step calls; it fixes the window offset).
+ * qds_save_working: copies the current state into dst_dev (asynchronous);
+ *   with bytes < qds_working_bytes only the first bytes (the EM group's six
+ *   plane sets, 6 n_modes nx ld elements, lead the state).
+ * qds_restore_working: makes a snapshot taken `step` steps after the import
+ *   the current state again and sets the step count to `step` (a handle of
+ *   one instance; clears the device error bits).  Asynchronous on stream. */
+size_t qds_working_bytes(const qds_handle *h, int i);
+unsigned long long qds_steps_taken(const qds_handle *h);
+int qds_save_working(qds_handle *h, int i, void *dst_dev, size_t bytes, void *stream);
+int qds_restore_working(qds_handle *h, const void *src_dev, size_t bytes, unsigned long long step, void *stream);
 int qds_adjoint_step(qds_handle *h, int i, const qds_sources *src, const void *fwd_state_dev,
                      void *adj_state_dev, void *work_dev, size_t work_bytes, double *dLdg_dev, void *stream);
 

@@ -5,10 +5,11 @@ physical variables) and the coupling g to the state after ``spec.nsteps``
 steps, as a ``torch.autograd.Function``.  Its backward pass is the
 hand-written transpose of the step (``qds_adjoint_step``) with
 checkpoint-and-recompute: the forward keeps the state every ``spec.every``
-steps (about sqrt(N) of them), and the backward re-runs each segment from
-its checkpoint, keeping that segment's states, and then applies the
-transposed steps to it in reverse order.  Memory: (N / every + every)
-canonical states.
+steps (about sqrt(N) of them) as working snapshots, and the backward re-runs
+each segment from its checkpoint, keeping the EM planes of that segment's
+states, and then applies the transposed steps to it in reverse order in the
+working precision.  Memory: N / every working states and ``every`` EM-plane
+copies.
 
 The adjoint covers the EM group and the axion: the regenerated fields never
 feed back into them, so the gradient is exact for functionals of the EM
@@ -65,30 +66,32 @@ def _params_with_g(p: Q.Params, g: float) -> Q.Params:
     return Q.Params(p.nx, p.nr, p.n_modes, p.dr, dx=p.dx, m_a=p.m_a, g=float(g), flags=p.flags, omega0=p.omega0)
 
 
-def _advance(solver, spec, n0, count, keep=None):
-    """Advance the solver ``count`` steps from step index n0; if ``keep`` is
-    a list, append the canonical state before every step.  Without ``keep``
-    and with a source object that can fill a block of steps (``fill``), the
-    block runs as one call with per-step sources (graph replays)."""
-    if keep is None and spec.sources is not None and hasattr(spec.sources, "fill"):
+def _advance(solver, spec, n0, count):
+    """Advance the solver ``count`` steps from step index n0.  With a source
+    object that can fill a block of steps (``fill``), the block runs as one
+    call with per-step sources (graph replays)."""
+    if spec.sources is None:
+        solver.step(count)
+        return
+    if hasattr(spec.sources, "fill"):
         bufs = spec.sources.fill(n0, count)
         solver.set_sources(0, *bufs, per_step=True)
         solver.step(count)
         return
     for n in range(n0, n0 + count):
-        if keep is not None:
-            keep.append(solver.get_state())
-        if spec.sources is None:
-            if keep is None:
-                solver.step(n0 + count - n)
-                return
-            solver.step(1)
-        else:
-            jx, jr, jt = spec.sources(n)
-            solver.step(1, jx=jx, jr=jr, jth=jt)
+        jx, jr, jt = spec.sources(n)
+        solver.step(1, jx=jx, jr=jr, jth=jt)
 
 
 class _Run(torch.autograd.Function):
+    """Forward: checkpoints are working snapshots (the state as the kernels
+    hold it, qds_save_working).  Backward: per segment, the checkpoint is
+    restored, the segment re-run keeping the EM planes of the state before
+    every step (all the transposed step reads), and the transposed steps
+    (qds_adjoint_step_w) run in reverse on the adjoint held in the working
+    precision, two buffers in turn: no conversion to complex128 between
+    steps."""
+
     @staticmethod
     def forward(ctx, state0, g, spec: RunSpec):
         p = _params_with_g(spec.params, float(g.detach().cpu()))
@@ -98,7 +101,9 @@ class _Run(torch.autograd.Function):
         solver.set_state(state0.detach().contiguous())
         n = 0
         while n < spec.nsteps:
-            ckpts.append((n, solver.get_state()))
+            snap, taken = solver.save_working()
+            assert taken == n
+            ckpts.append((n, snap))
             cnt = min(K, spec.nsteps - n)
             _advance(solver, spec, n, cnt)
             n += cnt
@@ -110,25 +115,40 @@ class _Run(torch.autograd.Function):
     def backward(ctx, lam_out):
         spec, solver, ckpts = ctx.spec, ctx.solver, ctx.ckpts
         p = spec.params
-        lam = lam_out.detach().to(torch.complex128).contiguous().clone()
         plane = p.n_modes * p.nx * p.nr
-        if bool((lam[9 * plane:N_FIELDS * plane] != 0).any()):
+        lam128 = lam_out.detach().to(torch.complex128).contiguous()
+        if bool((lam128[9 * plane:N_FIELDS * plane] != 0).any()):
             raise Q.QDSError("the adjoint covers the EM fields and the axion; "
                              "the loss must not depend on the regenerated fields")
+        lam = lam128.to(solver.rdtype).contiguous()
+        lam_b = torch.empty_like(lam)
         dg = torch.zeros(1, dtype=torch.float64, device=lam.device)
+        K = spec.interval()
+        em_bytes = solver.working_bytes(0, em_only=True)
+        pool = [torch.empty(em_bytes, dtype=torch.uint8, device=lam.device) for _ in range(K)]
+        block = spec.sources is not None and hasattr(spec.sources, "fill")
         for n0, ck in reversed(ckpts):
-            cnt = min(spec.interval(), spec.nsteps - n0)
-            states = []
-            solver.set_state(ck)
-            _advance(solver, spec, n0, cnt, keep=states)
+            cnt = min(K, spec.nsteps - n0)
+            solver.restore_working(ck, n0)
+            # the segment's currents, drawn once for the re-run and the transpose
+            blk = spec.sources.fill(n0, cnt) if block else None
+
+            def src(k):
+                if spec.sources is None:
+                    return None, None, None
+                if blk is not None:
+                    return blk[0][k], blk[1][k], blk[2][k]
+                return spec.sources(n0 + k)
+            for k in range(cnt):
+                solver.save_working(out=pool[k], em_only=True)
+                jx, jr, jt = src(k)
+                solver.step(1, jx=jx, jr=jr, jth=jt)
             for k in range(cnt - 1, -1, -1):
-                jx = jt = None
-                if spec.sources is not None:
-                    jx, _, jt = spec.sources(n0 + k)
-                solver.adjoint_step(states[k], lam, jx=jx, jth=jt, dLdg=dg)
-            del states
+                jx, _, jt = src(k)
+                solver.adjoint_step_w(pool[k], n0 + k, lam, lam_b, jx=jx, jth=jt, dLdg=dg)
+                lam, lam_b = lam_b, lam
         ctx.ckpts = None
-        return lam, dg.reshape(()).to(torch.float64), None
+        return lam.to(torch.complex128), dg.reshape(()).to(torch.float64), None
 
 
 def run_qds(state0: torch.Tensor, g: torch.Tensor, spec: RunSpec) -> torch.Tensor:

@@ -21,6 +21,7 @@ using namespace qds;
 // defined in qds_api.cu
 void qds_internal_set_error(const std::string &m);
 int qds_internal_params(const qds_handle *h, int i, qds_params *out);
+int qds_internal_layout(const qds_handle *h, int i, int *ld);
 
 namespace {
 
@@ -103,18 +104,22 @@ cudaError_t launch_all(Adj<R, M> a, int blocks, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// F: the forward state at the start of the step, with row stride ld and
+// ring offset s (the canonical layout: ld = nr, s = 0; a working snapshot:
+// the handle's row stride and the window's offset at that step).
 template <class R, int M>
 Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_inst, const C<R> *F,
-                   const C<R> *LN, C<R> *LO, C<R> *SB, double *dg) {
+                   const C<R> *LN, C<R> *LO, C<R> *SB, double *dg, int ld = 0, int s = 0) {
   Adj<R, M> a;
   std::memset(&a, 0, sizeof a);
   const int nx = p.nx, nr = p.nr;
   const size_t P = plane_elems(M, nx, nr);
+  if (ld == 0) ld = nr;
   Tile<R, M, false> &t = a.f;
   t.bind(h_inst, d_inst);
-  t.nx = nx; t.nr = nr; t.ld = nr; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = 0;
+  t.nx = nx; t.nr = nr; t.ld = ld; t.J = nr - 1; t.x0 = 0; t.r0 = 0; t.s = s;
   t.per = false; t.closed = false; t.mw = false;
-  t.P = P; t.o = F; t.n = nullptr;
+  t.P = plane_elems(M, nx, ld); t.o = F; t.n = nullptr;
   t.h = (R)p.dx; t.dr = (R)p.dr; t.ih = (R)(1.0 / p.dx); t.idr = (R)(1.0 / p.dr);
   t.scr = nullptr;
   t.cw = -(1 << 28);  // each point sets the column cache (adjoint_kernel)
@@ -189,7 +194,81 @@ int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *
   return QDS_OK;
 }
 
+// The transposed step in the working precision without conversions: the
+// forward state is a working snapshot (qds_save_working) taken `step` steps
+// after the state import, lam_in / lam_out canonical arrays of the working
+// precision (distinct buffers).  Work: the descriptor and the scratch planes.
+size_t work_w_bytes(const qds_params &p, size_t elem) {
+  return up256(sizeof(Inst<double>)) + up256((size_t)N_SB * plane_elems(p.n_modes, p.nx, p.nr) * elem);
+}
+
+template <class R>
+int adjoint_w(const qds_params &p, int ld, const qds_sources *src, const void *fwd, unsigned long long step,
+              const void *lam_in, void *lam_out, void *work, size_t work_bytes, double *dg, cudaStream_t st) {
+  if (work_bytes < work_w_bytes(p, sizeof(C<R>))) return fail_ad(QDS_ERR_INVALID_ARG, "adjoint work buffer too small");
+  if (reinterpret_cast<uintptr_t>(work) % 256) return fail_ad(QDS_ERR_INVALID_ARG, "adjoint work buffer must be 256-byte aligned");
+  if (lam_in == lam_out) return fail_ad(QDS_ERR_INVALID_ARG, "lam_in and lam_out must be distinct buffers");
+  const int M = p.n_modes, nx = p.nx, nr = p.nr;
+  char *b = static_cast<char *>(work);
+  Inst<R> I;
+  std::memset(&I, 0, sizeof I);
+  I.nx = nx; I.nr = nr; I.ld = ld; I.M = M; I.flags = p.flags;
+  I.h = (R)p.dx; I.dr = (R)p.dr; I.inv_h = (R)(1.0 / p.dx); I.inv_dr = (R)(1.0 / p.dr);
+  I.ma2 = (R)(p.m_a * p.m_a);
+  I.gs = (R)p.g; I.gj = (R)p.g;
+  if (src) {
+    I.jx = (const C<R> *)src->jx;
+    I.jt = (const C<R> *)src->jth;
+    I.sext = (const C<R> *)src->s_ext;
+  }
+  cudaError_t e = cudaMemcpyAsync(b, &I, sizeof I, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint descriptor: ") + cudaGetErrorString(e));
+  C<R> *SB = reinterpret_cast<C<R> *>(b + up256(sizeof(Inst<double>)));
+  const Inst<R> *d_inst = reinterpret_cast<const Inst<R> *>(b);
+  const C<R> *F = static_cast<const C<R> *>(fwd);
+  const C<R> *LN = static_cast<const C<R> *>(lam_in);
+  C<R> *LO = static_cast<C<R> *>(lam_out);
+  const int s = (p.flags & QDS_MOVING_WINDOW) ? (int)(step % (unsigned long long)nx) : 0;
+  const int blocks = (int)((size_t(nx) * nr + kThr - 1) / kThr);
+  switch (M) {
+    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
+    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
+    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
+    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
+    default: e = cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
+  return QDS_OK;
+}
+
 }  // namespace
+
+extern "C" size_t qds_adjoint_work_bytes_w(const qds_handle *h, int i) {
+  qds_params p;
+  if (qds_internal_params(h, i, &p)) return 0;
+  return work_w_bytes(p, (p.flags & QDS_FP32) ? sizeof(C<float>) : sizeof(C<double>));
+}
+
+extern "C" int qds_adjoint_step_w(qds_handle *h, int i, const qds_sources *src, const void *fwd_working_dev,
+                                  unsigned long long fwd_step, const void *lam_in_dev, void *lam_out_dev,
+                                  void *work_dev, size_t work_bytes, double *dLdg_dev, void *stream) {
+  qds_params p;
+  int rc = qds_internal_params(h, i, &p);
+  if (rc) return rc;
+  int ld = 0;
+  if ((rc = qds_internal_layout(h, i, &ld))) return rc;
+  if (!fwd_working_dev || !lam_in_dev || !lam_out_dev || !work_dev)
+    return fail_ad(QDS_ERR_INVALID_ARG, "NULL state, adjoint or work pointer");
+  if (p.flags & (QDS_X_PERIODIC | QDS_R_CLOSED))
+    return fail_ad(QDS_ERR_UNSUPPORTED, "the adjoint covers open boundaries only");
+  if (!(p.flags & QDS_AXION)) return fail_ad(QDS_ERR_UNSUPPORTED, "the adjoint step needs QDS_AXION");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.flags & QDS_FP32)
+    return adjoint_w<float>(p, ld, src, fwd_working_dev, fwd_step, lam_in_dev, lam_out_dev, work_dev, work_bytes,
+                            dLdg_dev, st);
+  return adjoint_w<double>(p, ld, src, fwd_working_dev, fwd_step, lam_in_dev, lam_out_dev, work_dev, work_bytes,
+                           dLdg_dev, st);
+}
 
 extern "C" size_t qds_adjoint_work_bytes(const qds_handle *h, int i) {
   qds_params p;

@@ -190,6 +190,7 @@ struct qds_handle {
   cudaEvent_t fork = nullptr;
   std::vector<std::vector<char>> h_inst;  // host copy of the descriptors (per instance)
   int mode = QDS_STEP_DEFAULT;  // step implementation (qds_set_step_mode)
+  unsigned long long host_step = 0;  // mirror of the device step counter (steps since the last state import)
   int seg = 0;                  // march: columns per CTA (0: default)
   int rows_override = 0;        // march: rows per CTA (0: default)
   // graph cache: key (steps per graph, stream); the kernels read the source
@@ -579,6 +580,13 @@ __attribute__((visibility("hidden"))) int qds_internal_params(const qds_handle *
   return QDS_OK;
 }
 
+// Row stride of instance i's working layout, for the adjoint translation unit.
+__attribute__((visibility("hidden"))) int qds_internal_layout(const qds_handle *h, int i, int *ld) {
+  if (!h || i < 0 || i >= h->n_inst) return fail(QDS_ERR_INVALID_ARG, "bad handle or instance");
+  *ld = row_ld(h->params[i]);
+  return QDS_OK;
+}
+
 extern "C" {
 
 const char *qds_last_error(void) { return g_err.c_str(); }
@@ -688,6 +696,7 @@ int qds_set_state_i(qds_handle *h, int i, const void *src, void *stream) {
   CU(cudaGetLastError());
   reset_kernel<<<1, 32, 0, st>>>(h->d_ctrl);
   CU(cudaGetLastError());
+  h->host_step = 0;
   return QDS_OK;
 }
 
@@ -755,6 +764,7 @@ int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream) {
       if (rc) return rc;
     }
   }
+  h->host_step += (unsigned long long)nsteps;
   // per-step sources: the steps of this call count from here
   if (any_strided(h)) {
     src_base_kernel<<<1, 32, 0, st>>>(h->d_ctrl);
@@ -790,6 +800,35 @@ int qds_step(qds_handle *h, const qds_sources *src, int nsteps, void *stream) {
     cudaError_t e = launch_steps(h, rem, st);
     if (e != cudaSuccess) return fail(QDS_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
   }
+  return QDS_OK;
+}
+
+size_t qds_working_bytes(const qds_handle *h, int i) {
+  if (!h || i < 0 || i >= h->n_inst) return 0;
+  return half_bytes(h->params[i]);
+}
+
+unsigned long long qds_steps_taken(const qds_handle *h) { return h ? h->host_step : 0; }
+
+int qds_save_working(qds_handle *h, int i, void *dst_dev, size_t bytes, void *stream) {
+  if (!h || !dst_dev || i < 0 || i >= h->n_inst) return fail(QDS_ERR_INVALID_ARG, "bad handle, instance or destination");
+  const size_t hb = half_bytes(h->params[i]);
+  const size_t n = bytes < hb ? bytes : hb;  // a prefix (the EM planes lead) or the whole state
+  const char *src = h->state + h->inst_off[i] + (h->host_step & 1ull) * hb;
+  CU(cudaMemcpyAsync(dst_dev, src, n, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return QDS_OK;
+}
+
+int qds_restore_working(qds_handle *h, const void *src_dev, size_t bytes, unsigned long long step, void *stream) {
+  if (!h || !src_dev) return fail(QDS_ERR_INVALID_ARG, "bad handle or source");
+  if (h->n_inst != 1) return fail(QDS_ERR_UNSUPPORTED, "restoring a working snapshot needs a single-instance handle");
+  const size_t hb = half_bytes(h->params[0]);
+  if (bytes < hb) return fail(QDS_ERR_INVALID_ARG, "working snapshot buffer too small (qds_working_bytes)");
+  cudaStream_t st = (cudaStream_t)stream;
+  CU(cudaMemcpyAsync(h->state + h->inst_off[0] + (step & 1ull) * hb, src_dev, hb, cudaMemcpyDeviceToDevice, st));
+  set_step_kernel<<<1, 32, 0, st>>>(h->d_ctrl, step);
+  CU(cudaGetLastError());
+  h->host_step = step;
   return QDS_OK;
 }
 

@@ -113,6 +113,11 @@ static __global__ void reset_kernel(Ctrl *ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) { ctrl->step = 0; ctrl->err = 0; }
 }
 
+// restore the step counter with a working snapshot (clears the error bits)
+static __global__ void set_step_kernel(Ctrl *ctrl, unsigned long long step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) { ctrl->step = step; ctrl->err = 0; }
+}
+
 static __global__ void src_base_kernel(Ctrl *ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) ctrl->src_base = ctrl->step;
 }

@@ -80,6 +80,13 @@ def lib():
             "qds_last_error": (ctypes.c_char_p, []),
             "qds_advance_noalloc": (i, [P, vp, vp, vp, sz, i, vp]),
             "qds_adjoint_work_bytes": (sz, [H, i]),
+            "qds_adjoint_work_bytes_w": (sz, [H, i]),
+            "qds_adjoint_step_w": (i, [H, i, ctypes.POINTER(_Sources), vp, ctypes.c_ulonglong, vp, vp, vp, sz, vp,
+                                       vp]),
+            "qds_working_bytes": (sz, [H, i]),
+            "qds_steps_taken": (ctypes.c_ulonglong, [H]),
+            "qds_save_working": (i, [H, i, vp, sz, vp]),
+            "qds_restore_working": (i, [H, vp, sz, ctypes.c_ulonglong, vp]),
             "qds_adjoint_step": (i, [H, i, ctypes.POINTER(_Sources), vp, vp, vp, sz, vp, vp]),
         }
         for name, (res, args) in sig.items():
@@ -260,6 +267,66 @@ class QDSSolver:
                                       ctypes.c_void_p(lam.data_ptr()), ctypes.c_void_p(wptr), nbytes,
                                       None if dLdg is None else ctypes.c_void_p(dLdg.data_ptr()),
                                       _stream_ptr(stream)))
+
+    # -- working snapshots and the conversion-free transposed step --------
+    def steps_taken(self) -> int:
+        return int(lib().qds_steps_taken(self.h))
+
+    def working_bytes(self, i: int = 0, em_only=False) -> int:
+        nbytes = int(lib().qds_working_bytes(self.h, i))
+        if em_only:  # the EM group's six plane sets lead the working state
+            p = self.params[i]
+            ld = p.nr + (p.nr & 1) if p.fp32 else p.nr
+            nbytes = 6 * p.n_modes * p.nx * ld * (8 if p.fp32 else 16)
+        return nbytes
+
+    def save_working(self, i: int = 0, out=None, em_only=False, stream=None):
+        """Copy of the current state as the kernels hold it (a uint8 device
+        tensor of qds_working_bytes; ``em_only``: only the EM group's planes,
+        all the transposed step reads), and the step count it belongs to."""
+        nbytes = self.working_bytes(i, em_only)
+        if out is None:
+            out = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        _check(lib().qds_save_working(self.h, i, ctypes.c_void_p(out.data_ptr()), out.numel(), _stream_ptr(stream)))
+        return out, self.steps_taken()
+
+    def restore_working(self, snap, step: int, stream=None):
+        _check(lib().qds_restore_working(self.h, ctypes.c_void_p(snap.data_ptr()), snap.numel(), int(step),
+                                         _stream_ptr(stream)))
+
+    def adjoint_step_w(self, fwd_snap, fwd_step: int, lam_in, lam_out, i: int = 0, jx=None, jth=None, s_ext=None,
+                       dLdg=None, stream=None):
+        """One transposed step without conversions (qds_adjoint_step_w):
+        ``fwd_snap`` a working snapshot at the start of the step taken
+        ``fwd_step`` steps after the import; ``lam_in`` / ``lam_out`` the
+        adjoint after / before the step, canonical layout in the working
+        precision (complex64 in FP32), distinct tensors."""
+        p = self.params[i]
+        for t in (lam_in, lam_out):
+            assert t.is_cuda and t.is_contiguous() and t.numel() == p.state_elems()
+            assert t.dtype == (torch.complex64 if p.fp32 else torch.complex128)
+
+        def ptr(t):
+            if t is None:
+                return None
+            assert t.is_cuda and t.dtype == self.rdtype and t.is_contiguous()
+            return t.data_ptr()
+        if dLdg is not None:
+            assert dLdg.dtype == torch.float64 and dLdg.is_cuda
+        nbytes = lib().qds_adjoint_work_bytes_w(self.h, i)
+        if nbytes == 0:
+            _check(1)
+        work = getattr(self, "_adj_work_w", None)
+        if work is None or work.numel() < nbytes + 256:
+            work = self._adj_work_w = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        wptr = work.data_ptr() + (-work.data_ptr()) % 256
+        src = _Sources(ptr(jx), None, ptr(jth), ptr(s_ext))
+        self._adj_keep_w = (fwd_snap, lam_in, lam_out, jx, jth, s_ext, dLdg)
+        _check(lib().qds_adjoint_step_w(self.h, i, ctypes.byref(src), ctypes.c_void_p(fwd_snap.data_ptr()),
+                                        int(fwd_step), ctypes.c_void_p(lam_in.data_ptr()),
+                                        ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(wptr), nbytes,
+                                        None if dLdg is None else ctypes.c_void_p(dLdg.data_ptr()),
+                                        _stream_ptr(stream)))
 
     def diagnostics(self, i: int = 0, profile=False, stream=None):
         out = (ctypes.c_double * 4)()

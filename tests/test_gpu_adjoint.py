@@ -123,6 +123,45 @@ def test_adjoint_step_coupling_derivative(prec):
     assert abs(dg - fd) < tol * abs(fd), (dg, fd)
 
 
+@pytest.mark.parametrize("M,mw", [(1, False), (3, True), (4, True), (2, False)])
+@pytest.mark.parametrize("prec", [0, 32])
+def test_working_transpose_matches_canonical_transpose(M, mw, prec):
+    """qds_adjoint_step_w on an EM-only working snapshot taken after a few
+    steps (ring offset 5 in the moving window) gives what qds_adjoint_step
+    gives on the canonical state of the same moment, entry for entry; the
+    canonical path only converts, so the two differ only by the order of the
+    atomic additions of the scatters (a few units in the last place)."""
+    Q = _Q()
+    nx, nr = 124, 41
+    m_a, g = 0.05, 0.6
+    dr = stable_dr(M, m_a)
+    flags = oracle.AXION | oracle.AREM | (oracle.MOVING_WINDOW if mw else 0)
+    rng = np.random.default_rng(700 + 10 * M + mw)
+    p = Q.Params(nx, nr, M, dr, m_a=m_a, g=g, flags=flags | prec)
+    solver = Q.QDSSolver(p, device=DEV)
+    rd = solver.rdtype
+    solver.set_state(torch.from_numpy(I.random_state(rng, M, nx, nr)).to(DEV))
+    jx, jr, jt = (torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(rd) for a in I.random_sources(rng, M, nx, nr, 0.3))
+    solver.step(5, jx=jx, jr=jr, jth=jt)
+    snap, k = solver.save_working(em_only=True)
+    assert k == 5 and snap.numel() == solver.working_bytes(0, em_only=True)
+    fwd = solver.get_state()
+    lam = I.random_state(rng, M, nx, nr, axis_consistent=False) * em_axion_mask(M, nx, nr)
+    lam_w = torch.from_numpy(lam).to(DEV).to(rd).contiguous()
+    lam_c = lam_w.to(torch.complex128, copy=True)  # a copy also in FP64: adjoint_step works in place
+    out_w = torch.full_like(lam_w, float("nan"))
+    dg_c = torch.zeros(1, dtype=torch.float64, device=DEV)
+    dg_w = torch.zeros(1, dtype=torch.float64, device=DEV)
+    solver.adjoint_step(fwd, lam_c, jx=jx, jth=jt, dLdg=dg_c)
+    solver.adjoint_step_w(snap, k, lam_w, out_w, jx=jx, jth=jt, dLdg=dg_w)
+    torch.cuda.synchronize()
+    a, b = out_w.to(torch.complex128).cpu().numpy(), lam_c.cpu().numpy()
+    eps = 1e-14 if prec == 0 else 1e-6
+    bad = np.argwhere(np.abs(a - b) > eps * np.abs(b).max()).ravel()
+    assert bad.size == 0, (bad[:10], a[bad[:5]], b[bad[:5]])
+    assert abs(float(dg_w.item()) - float(dg_c.item())) <= eps * abs(float(dg_c.item()))
+
+
 def test_adjoint_rejects_unsupported_boundaries():
     Q = _Q()
     p = Q.Params(16, 8, 2, 2.0, g=0.5, flags=oracle.AXION | oracle.X_PERIODIC)
