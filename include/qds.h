@@ -270,7 +270,8 @@ size_t qds_adjoint_work_bytes(const qds_handle *h, int i);
  * lam_in_dev / lam_out_dev: the adjoint of the state after / before the step
  *   in the canonical layout of qds_set_state but in the working precision
  *   (complex64 with QDS_FP32, else complex128), physical variables; distinct
- *   buffers (lam_out is written in full).
+ *   buffers.  Every entry of lam_out is written except the regenerated
+ *   group's six plane sets, which are left as they are (zero them once).
  * work_dev: >= qds_adjoint_work_bytes_w(h, i) bytes, 256-byte aligned.
  * Otherwise as qds_adjoint_step.  Asynchronous on stream. */
 size_t qds_adjoint_work_bytes_w(const qds_handle *h, int i);

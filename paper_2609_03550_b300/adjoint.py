@@ -121,30 +121,29 @@ class _Run(torch.autograd.Function):
             raise Q.QDSError("the adjoint covers the EM fields and the axion; "
                              "the loss must not depend on the regenerated fields")
         lam = lam128.to(solver.rdtype).contiguous()
-        lam_b = torch.empty_like(lam)
+        lam_b = torch.zeros_like(lam)  # the transposed step leaves the regenerated planes as they are
         dg = torch.zeros(1, dtype=torch.float64, device=lam.device)
         K = spec.interval()
         em_bytes = solver.working_bytes(0, em_only=True)
         pool = [torch.empty(em_bytes, dtype=torch.uint8, device=lam.device) for _ in range(K)]
-        block = spec.sources is not None and hasattr(spec.sources, "fill")
+        fill = spec.sources is not None and hasattr(spec.sources, "fill")
         for n0, ck in reversed(ckpts):
             cnt = min(K, spec.nsteps - n0)
             solver.restore_working(ck, n0)
             # the segment's currents, drawn once for the re-run and the transpose
-            blk = spec.sources.fill(n0, cnt) if block else None
-
-            def src(k):
-                if spec.sources is None:
-                    return None, None, None
-                if blk is not None:
-                    return blk[0][k], blk[1][k], blk[2][k]
-                return spec.sources(n0 + k)
+            if spec.sources is None:
+                blk = [(None, None, None)] * cnt
+            elif fill:
+                jx, jr, jt = spec.sources.fill(n0, cnt)
+                blk = [(jx[k], jr[k], jt[k]) for k in range(cnt)]
+            else:
+                blk = None
             for k in range(cnt):
                 solver.save_working(out=pool[k], em_only=True)
-                jx, jr, jt = src(k)
+                jx, jr, jt = blk[k] if blk is not None else spec.sources(n0 + k)
                 solver.step(1, jx=jx, jr=jr, jth=jt)
             for k in range(cnt - 1, -1, -1):
-                jx, _, jt = src(k)
+                jx, _, jt = blk[k] if blk is not None else spec.sources(n0 + k)
                 solver.adjoint_step_w(pool[k], n0 + k, lam, lam_b, jx=jx, jth=jt, dLdg=dg)
                 lam, lam_b = lam_b, lam
         ctx.ckpts = None

@@ -54,19 +54,27 @@ struct AdjLayout {
   }
 };
 
+// AD_SRC: one thread per (x, r) point with all modes; AD_LEAP, AD_CELL: one
+// thread per (mode, x, r), r fastest.
 template <class R, int M, int ST>
-__global__ void __launch_bounds__(kThr) adjoint_kernel(Adj<R, M> a) {
+__global__ void __launch_bounds__(kThr, sizeof(R) == 8 ? 1 : (ST == AD_SRC ? (M <= 3 ? 3 : 2) : ST == AD_LEAP ? 6 : 5)) adjoint_kernel(Adj<R, M> a) {
   const int n = a.nx * a.nr;
   double acc = 0;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-    const int w = q / a.nr, j = q - w * a.nr;
-    Adj<R, M> ap = a;
-    ap.f.set_point(w);  // ring slots of columns w-1 .. w+2
-    adj_point<R, M>(ap, ST, w, j, acc);
-  }
-  if (ST == AD_UNSRC && a.dg) {
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(a.dg, acc);
+  if (ST == AD_SRC) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+      const int w = q / a.nr, j = q - w * a.nr;
+      adj_point<R, M>(a, ST, 0, w, j, acc);
+    }
+    if (a.dg) {
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(a.dg, acc);
+    }
+  } else {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < M * n; q += gridDim.x * blockDim.x) {
+      const int k = q / n, p = q - k * n;
+      const int w = p / a.nr, j = p - w * a.nr;
+      adj_point<R, M>(a, ST, k, w, j, acc);
+    }
   }
 }
 
@@ -96,11 +104,9 @@ __global__ void from_work_kernel(const C<R> *__restrict__ src, double2 *dst, siz
 
 template <class R, int M>
 cudaError_t launch_all(Adj<R, M> a, int blocks, cudaStream_t st) {
-  adjoint_kernel<R, M, AD_UNPHI><<<blocks, kThr, 0, st>>>(a);
-  adjoint_kernel<R, M, AD_UNTA><<<blocks, kThr, 0, st>>>(a);
-  adjoint_kernel<R, M, AD_UNSHIFT><<<blocks, kThr, 0, st>>>(a);
-  adjoint_kernel<R, M, AD_UNSRC><<<blocks, kThr, 0, st>>>(a);
-  adjoint_kernel<R, M, AD_UNLEAP><<<blocks, kThr, 0, st>>>(a);
+  adjoint_kernel<R, M, AD_SRC><<<blocks, kThr, 0, st>>>(a);
+  adjoint_kernel<R, M, AD_LEAP><<<M * blocks, kThr, 0, st>>>(a);
+  adjoint_kernel<R, M, AD_CELL><<<M * blocks, kThr, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -109,7 +115,7 @@ cudaError_t launch_all(Adj<R, M> a, int blocks, cudaStream_t st) {
 // the handle's row stride and the window's offset at that step).
 template <class R, int M>
 Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_inst, const C<R> *F,
-                   const C<R> *LN, C<R> *LO, C<R> *SB, double *dg, int ld = 0, int s = 0) {
+                   const C<R> *LN, C<R> *LO, C<R> *SB, double *dg, bool zero_regen, int ld = 0, int s = 0) {
   Adj<R, M> a;
   std::memset(&a, 0, sizeof a);
   const int nx = p.nx, nr = p.nr;
@@ -124,8 +130,9 @@ Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_
   t.scr = nullptr;
   t.cw = -(1 << 28);  // each point sets the column cache (adjoint_kernel)
   a.ln = LN; a.lo = LO; a.sb = SB; a.dg = dg;
-  a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
+  a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = (unsigned)P;
   a.mw = (p.flags & QDS_MOVING_WINDOW) != 0;
+  a.zero_regen = zero_regen;
   a.h = t.h; a.dr = t.dr; a.ih = t.ih; a.idr = t.idr;
   a.gs = (R)p.g; a.ma2 = (R)(p.m_a * p.m_a);
   return a;
@@ -178,10 +185,10 @@ int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *
   const Inst<R> *d_inst = reinterpret_cast<const Inst<R> *>(b);
   const int blocks = (int)((size_t(nx) * nr + kThr - 1) / kThr);
   switch (M) {
-    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
-    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
-    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
-    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg), blocks, st); break;
+    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg, sizeof(R) == 8), blocks, st); break;
+    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg, sizeof(R) == 8), blocks, st); break;
+    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg, sizeof(R) == 8), blocks, st); break;
+    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg, sizeof(R) == 8), blocks, st); break;
     default: e = cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
@@ -231,10 +238,10 @@ int adjoint_w(const qds_params &p, int ld, const qds_sources *src, const void *f
   const int s = (p.flags & QDS_MOVING_WINDOW) ? (int)(step % (unsigned long long)nx) : 0;
   const int blocks = (int)((size_t(nx) * nr + kThr - 1) / kThr);
   switch (M) {
-    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
-    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
-    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
-    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg, ld, s), blocks, st); break;
+    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
+    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
+    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
+    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
     default: e = cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));

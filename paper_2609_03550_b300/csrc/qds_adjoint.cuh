@@ -9,81 +9,112 @@
 //
 // Adjoint fields live in the canonical window-order layout (no ring offset)
 // in the working precision.  The forward state of the step (time n) is read
-// through a Tile with s = 0 (its window order).  The step is transposed pass
-// by pass in reverse order of the forward passes:
-//   AD_UNPHI   window shift and phi update (Eq. phi_update)
-//   AD_UNTA    T_a shift (Eqs. Ta_plus_update, Ta_minus_update)
-//   AD_UNSHIFT T shift, its face sources and the outer box (Eqs. Trp/Trm/
-//              Ttp/Ttm_update, axis_Ttheta, em_r_open_bt)
-//   AD_UNSRC   Gamma_a: Laplacian, mass, the outer ghost and the bilinear
-//              source S_a (Eq. mode_convolution), d L / d g accumulated
-//   AD_UNLEAP  E_x, B_x leapfrog and the outer box (Eqs. Ex_update,
-//              axis_Ex, em_r_open_bx)
-// The transpose of the +x shift is the -x shift and vice versa.  Open x,
-// open r, optional moving window; no periodic or closed test modes.
+// through a Tile (its row stride and ring offset).  Every entry of the old
+// adjoint is written once by the thread that owns it (a gather: no atomic
+// scatters), in three passes over the (x, r) points:
+//   AD_SRC   faces: Gamma_a's adjoint from the new T_a and phi (Eqs.
+//            Ta_plus_update, Ta_minus_update, phi_update), d L / d g, and the
+//            transpose of the bilinear source S_a (Eq. mode_convolution) at
+//            the forward state, kept per face;
+//   AD_LEAP  faces: the total adjoints of E_x, B_x^(n+1/2) (new state, the T
+//            shift's face sources, the source means) and the old E_x, B_x
+//            (Eqs. Ex_update, axis_Ex, Phix_explicit, em_r_open_bx);
+//   AD_CELL  cells: the old T (shifted copies, Eqs. Trp/Trm/Ttp/Ttm_update,
+//            axis_Ttheta; the outer boxes, Eq. em_r_open_bt; the leapfrog
+//            and source-mean terms of the two neighbouring faces), T_a, phi
+//            (Gamma_a's Laplacian and mass with the outer ghost) and phi_prev.
+// The transpose of the +x shift is the -x shift and vice versa; the window
+// shift reads the new state's adjoint one column over.  Open x, open r,
+// optional moving window; no periodic or closed test modes.
 #pragma once
 
 #include "qds_stages.cuh"
 
 namespace qds {
 
-enum AdStage { AD_UNPHI = 0, AD_UNTA, AD_UNSHIFT, AD_UNSRC, AD_UNLEAP, N_ADSTAGE };
+enum AdStage { AD_SRC = 0, AD_LEAP, AD_CELL, N_ADSTAGE };
 
-// scratch planes of the adjoint (window order), each M*nx*nr
-enum AdScr { SB_TRP = 0, SB_TRM, SB_TTP, SB_TTM, SB_EX, SB_BX, SB_TAP, SB_TAM, SB_G, N_SB };
-
-template <class R>
-QDS_HD void cadd(C<R> *p, C<R> v) {
-#if defined(__CUDA_ARCH__)
-  atomicAdd(&p->re, v.re);
-  atomicAdd(&p->im, v.im);
-#else
-  p->re += v.re;
-  p->im += v.im;
-#endif
-}
+// scratch planes of the adjoint (window order), each M*nx*nr, on faces:
+// Gamma_a's adjoint; the adjoints of the face means of the axion source
+// (eX, bX, rp, rm, qp, qm); the total adjoints of E_x, B_x^(n+1/2)
+enum AdScr { SB_G = 0, SB_EXB, SB_BXB, SB_RPB, SB_RMB, SB_QPB, SB_QMB, SB_EXT, SB_BXT, N_SB };
 
 template <class R, int M>
 struct Adj {
-  Tile<R, M, false> f;  // forward state at time n (s = 0)
-  const C<R> *ln;              // adjoint of the state after the step
-  C<R> *lo;                    // adjoint of the state before the step (accumulated)
-  C<R> *sb;                    // scratch planes
-  double *dg;                  // accumulated dL/dg (null: not wanted)
+  Tile<R, M, false> f;  // forward state at time n
+  const C<R> *ln;       // adjoint of the state after the step (canonical layout)
+  C<R> *lo;             // adjoint of the state before the step (canonical layout)
+  C<R> *sb;             // scratch planes (N_SB)
+  double *dg;           // accumulated dL/dg (null: not wanted)
   int nx, nr, J;
-  size_t P;
+  unsigned P;           // elements of one field's plane set, M * nx * nr (< 2^32: checked at create)
   bool mw;
+  bool zero_regen;      // also write the (zero) regenerated planes of lo
   R h, dr, ih, idr;
   R gs, ma2;
 
-  QDS_HD size_t ai(int field, int k, int w, int j) const { return ((size_t)field * M + k) * (size_t)nx * nr + (size_t)w * nr + j; }
+  // 32-bit element offsets: one instance's state has fewer than 2^32 elements
+  QDS_HD unsigned ai(int field, int k, int w, int j) const {
+    return (unsigned)field * P + (unsigned)k * (unsigned)(nx * nr) + (unsigned)(w * nr + j);
+  }
   QDS_HD bool in_cell(int w) const { return w >= 0 && w < nx; }
   QDS_HD bool in_face(int w) const { return w >= 0 && w <= nx - 2; }
   // adjoint of the new state in the fixed box (before the window shift)
   QDS_HD C<R> lnew(int field, int k, int w, int j) const {
     if (mw) w -= 1;
     if (w < 0 || w >= nx || j < 0 || j >= nr) return zero<R>();
-    return ln[ai(field, k, w, j)];
+    return ldg(ln + ai(field, k, w, j));
   }
   QDS_HD C<R> lnew_prev(int k, int w) const {
     if (mw) w -= 1;
     if (w < 0 || w >= nx) return zero<R>();
-    return ln[(size_t)NFIELD * P + (size_t)k * nx + w];
+    return ldg(ln + ((unsigned)NFIELD * P + (unsigned)(k * nx + w)));
   }
   QDS_HD C<R> &old(int field, int k, int w, int j) const { return lo[ai(field, k, w, j)]; }
-  QDS_HD C<R> *oldp(int field, int k, int w, int j) const { return lo + ai(field, k, w, j); }
-  QDS_HD C<R> *oldprev(int k, int w) const { return lo + (size_t)NFIELD * P + (size_t)k * nx + w; }
-  QDS_HD C<R> &s(int plane, int k, int w, int j) const { return sb[((size_t)plane * M + k) * (size_t)nx * nr + (size_t)w * nr + j]; }
-  QDS_HD C<R> sv(int plane, int k, int w, int j) const {
-    if (w < 0 || w >= nx || j < 0 || j >= nr) return zero<R>();
-    return s(plane, k, w, j);
+  QDS_HD C<R> &oldprev(int k, int w) const { return lo[(unsigned)NFIELD * P + (unsigned)(k * nx + w)]; }
+  QDS_HD C<R> &s(int plane, int k, int w, int j) const { return sb[ai(plane, k, w, j)]; }
+  // reads of scratch planes that the running pass does not write
+  QDS_HD C<R> sr(int plane, int k, int w, int j) const { return ldg(sb + ai(plane, k, w, j)); }
+  // scratch on a face, zero off the faces and rows of the box
+  QDS_HD C<R> sf(int plane, int k, int w, int j) const {
+    if (!in_face(w) || j < 0 || j >= nr) return zero<R>();
+    return sr(plane, k, w, j);
   }
-  // scatter into the old adjoint of a transverse field at a cell (E_r, B_th,
-  // E_th, B_r -> T^+-), ignoring positions outside the box
-  QDS_HD void add_Er(int k, int c, int j, C<R> v) const { if (in_cell(c)) { cadd(oldp(TRP, k, c, j), R(0.5) * v); cadd(oldp(TRM, k, c, j), R(0.5) * v); } }
-  QDS_HD void add_Bt(int k, int c, int j, C<R> v) const { if (in_cell(c)) { cadd(oldp(TRP, k, c, j), R(0.5) * v); cadd(oldp(TRM, k, c, j), R(-0.5) * v); } }
-  QDS_HD void add_Et(int k, int c, int j, C<R> v) const { if (in_cell(c)) { cadd(oldp(TTP, k, c, j), R(0.5) * v); cadd(oldp(TTM, k, c, j), R(0.5) * v); } }
-  QDS_HD void add_Br(int k, int c, int j, C<R> v) const { if (in_cell(c)) { cadd(oldp(TTP, k, c, j), R(0.5) * v); cadd(oldp(TTM, k, c, j), R(-0.5) * v); } }
+  // adjoint of the new T (q = 0..3: T_r^+, T_r^-, T_th^+, T_th^-) at cell c
+  QDS_HD C<R> tn(int q, int k, int c, int j) const { return in_cell(c) ? lnew(TRP + q, k, c, j) : zero<R>(); }
+  // adjoints of the new T_a^+- at cell c, with the phi update's share
+  // (phi^(n+1) at the faces on either side takes (h/4) T_a^(n+1/2) of c)
+  QDS_HD C<R> phi_share(int k, int c, int j) const {
+    C<R> pl = in_face(c - 1) ? lnew(PHI, k, c - 1, j) : zero<R>();
+    C<R> pr = in_face(c) ? lnew(PHI, k, c, j) : zero<R>();
+    return (R(0.25) * h) * (pl + pr);
+  }
+  QDS_HD C<R> tap_n(int k, int c, int j) const { return in_cell(c) ? lnew(TAP, k, c, j) + phi_share(k, c, j) : zero<R>(); }
+  QDS_HD C<R> tam_n(int k, int c, int j) const { return in_cell(c) ? lnew(TAM, k, c, j) + phi_share(k, c, j) : zero<R>(); }
+  // box-scheme weights of the outer half row (Eqs. em_r_open_bx/bt)
+  QDS_HD R ka() const { return R(0.5) * ih; }
+  QDS_HD R kb() const { return R(0.5) * idr; }
+  QDS_HD R kab() const { return (ka() - kb()) / (ka() + kb()); }
+  // adjoint of B_th^(n+1) on the last half row at cell c (zero off the box)
+  QDS_HD C<R> box_bt(int k, int c) const { return tn(0, k, c, J) - tn(1, k, c, J); }
+  // effective adjoints of the new T at cell c: T_r on half row J-1 with the
+  // fold of the outer box, T_th on the axis only for m = 1 (axis_Ttheta)
+  QDS_HD C<R> trp_e(int k, int c, int j) const {
+    if (!in_cell(c)) return zero<R>();
+    C<R> v = tn(0, k, c, j);
+    if (j == J - 1) v += (R(-0.5) * kab()) * box_bt(k, c);
+    return v;
+  }
+  QDS_HD C<R> trm_e(int k, int c, int j) const {
+    if (!in_cell(c)) return zero<R>();
+    C<R> v = tn(1, k, c, j);
+    if (j == J - 1) v -= (R(-0.5) * kab()) * box_bt(k, c);
+    return v;
+  }
+  QDS_HD C<R> tt_e(int q, int k, int c, int j) const {
+    if (!in_cell(c) || (j == 0 && k != 1)) return zero<R>();
+    return tn(q, k, c, j);
+  }
 };
 
 // Transpose of the mode convolution C_m{A, B} (Eq. mode_convolution) for all
@@ -95,13 +126,16 @@ QDS_HD void conv_T(const C<R> *A, const C<R> *B, const C<R> *Sb, R wgt, C<R> *Ab
     C<R> s0 = wgt * Sb[0];
     Ab[0] += mul_cj(s0, B[0]);
     Bb[0] += mul_cj(s0, A[0]);
+    #pragma unroll
     for (int k = 1; k < M; k++) {
       Ab[k] += (R(0.5) * s0.re) * B[k];
       Bb[k] += (R(0.5) * s0.re) * A[k];
     }
   }
+  #pragma unroll
   for (int m = 1; m < M; m++) {
     C<R> t = (R(0.5) * wgt) * Sb[m];
+    #pragma unroll
     for (int k = 0; k <= m && k < M; k++) {  // A_k B_l, k + l = m
       int l = m - k;
       if (l < M) {
@@ -109,10 +143,12 @@ QDS_HD void conv_T(const C<R> *A, const C<R> *B, const C<R> *Sb, R wgt, C<R> *Ab
         Bb[l] += mul_cj(t, A[k]);
       }
     }
+    #pragma unroll
     for (int l = 0; l + m < M; l++) {  // A_{l+m} conj(B_l)
       Ab[l + m] += B[l] * t;
       Bb[l] += mul_cj(A[l + m], t);
     }
+    #pragma unroll
     for (int k = 0; k + m < M; k++) {  // conj(A_k) B_{k+m}
       Ab[k] += mul_cj(B[k + m], t);
       Bb[k + m] += A[k] * t;
@@ -121,295 +157,368 @@ QDS_HD void conv_T(const C<R> *A, const C<R> *B, const C<R> *Sb, R wgt, C<R> *Ab
 }
 
 // ---------------------------------------------------------------------------
+// The E_x and B_x^(n+1/2) adjoints that the T shift's face sources give at
+// face f, row j (Eqs. Trp/Trm/Ttp/Ttm_update; axis rules of Sec. 2.3; on the
+// last row, E_r^(n+1) takes Gamma_r of the faces on either side).
 template <class R, int M>
-QDS_HD void adj_point(const Adj<R, M> &a, int st, int w, int j, double &dg_acc) {
+QDS_HD void unshift_face(const Adj<R, M> &a, int k, int f, int j, C<R> &ex, C<R> &bx) {
   const int J = a.J;
   const R h = a.h, dr = a.dr, idr = a.idr;
-  const R ka = R(0.5) * a.ih, kb = R(0.5) * idr;  // box-scheme weights
-  const Tile<R, M, false> &t = a.f;
+  auto Sr = [&](int jj, C<R> &Gb, C<R> &Pb) {  // T_r sources (half row jj < J)
+    C<R> sp = h * a.trp_e(k, f + 1, jj), sm = h * a.trm_e(k, f, jj);
+    Gb = sp + sm;
+    Pb = sp - sm;
+  };
+  auto St = [&](int jj, C<R> &Gb, C<R> &Pb) {  // T_th sources (row jj)
+    C<R> sp = h * a.tt_e(2, k, f, jj), sm = h * a.tt_e(3, k, f + 1, jj);
+    Gb = sp + sm;
+    Pb = sp - sm;
+  };
+  ex = zero<R>();
+  bx = zero<R>();
+  C<R> Gr, Pr, Gt, Pt;
+  // E_x(f, j) enters Phi_r of half rows j and j-1 and Phi_th of row j
+  if (j < J) { Sr(j, Gr, Pr); ex -= idr * Pr; }
+  if (j >= 1) { Sr(j - 1, Gr, Pr); ex += idr * Pr; }
+  if (j >= 1) { St(j, Gt, Pt); ex += imul(-R(k) / (R(j) * dr), Pt); }
+  if (k == 1 && j <= 1) {  // axis: Phi_th = i (E_x(1) - E_x(0)) / dr
+    St(0, Gt, Pt);
+    ex += imul(j == 1 ? -idr : idr, Pt);
+  }
+  // B_x(f, j) enters Gamma_r of half row j and Gamma_th of rows j, j+1
+  const R rh = (R(j) + R(0.5)) * dr;
+  if (j < J) { Sr(j, Gr, Pr); bx += imul(R(k) / rh, Gr); }
+  else {
+    C<R> Gb = (R(0.5) * h) * (a.tn(0, k, f + 1, J) + a.tn(1, k, f + 1, J) + a.tn(0, k, f, J) + a.tn(1, k, f, J));
+    bx += imul(R(k) / rh, Gb);
+  }
+  if (j >= 1) { St(j, Gt, Pt); bx -= idr * Gt; }
+  else if (k == 1) { St(0, Gt, Pt); bx += (-R(2) * idr) * Gt; }
+  if (j + 1 <= J) { St(j + 1, Gt, Pt); bx += idr * Gt; }
+}
 
-  if (st == AD_UNPHI) {
-    // phi^(n+1) = phi^n + (h/4) sum T_a^(n+1/2) over the cells around face w;
-    // phi_prev^(n+1) = phi^n on the last row.  Also seeds the scratch with
-    // the adjoints of the new T, E_x, B_x (window shift undone).
-    for (int k = 0; k < M; k++) {
-      for (int q = 0; q < 4; q++) a.s(SB_TRP + q, k, w, j) = a.lnew(TRP + q, k, w, j);
-      a.s(SB_EX, k, w, j) = a.in_face(w) ? a.lnew(EX, k, w, j) : zero<R>();
-      a.s(SB_BX, k, w, j) = a.in_face(w) ? a.lnew(BX, k, w, j) : zero<R>();
-      C<R> pl = a.in_face(w - 1) ? a.lnew(PHI, k, w - 1, j) : zero<R>();
-      C<R> pr = a.in_face(w) ? a.lnew(PHI, k, w, j) : zero<R>();
-      C<R> tp = a.lnew(TAP, k, w, j) + (R(0.25) * h) * (pl + pr);
-      C<R> tm = a.lnew(TAM, k, w, j) + (R(0.25) * h) * (pl + pr);
-      a.s(SB_TAP, k, w, j) = tp;
-      a.s(SB_TAM, k, w, j) = tm;
-      C<R> ph = pr;
-      if (j == J && a.in_face(w)) ph += a.lnew_prev(k, w);
-      a.old(PHI, k, w, j) = ph;
-      if (j == 0) *a.oldprev(k, w) = zero<R>();
-      // scatter targets start at zero; the regenerated group has no adjoint
-      for (int fl = TRP; fl <= BX; fl++) a.old(fl, k, w, j) = zero<R>();
-      for (int fl = TRP1; fl < NFIELD; fl++) a.old(fl, k, w, j) = zero<R>();
-    }
-    return;
+// The forward state around face f as the source transpose reads it: the
+// columns f and f + 1 only (cells f, f + 1; face f), rows inside the box
+// (the leapfrog helpers guard their radial neighbours).  Each column's
+// ring slot is resolved once; the interface is the Tile's, for the forward
+// helpers ex_update, bx_interior and bx_outer.
+template <class R, int M>
+struct AdjFwd {
+  using Real = R;
+  const C<R> *c0, *c1;  // columns f and f + 1 of field 0, mode 0
+  const C<R> *jx, *jt, *sext;
+  unsigned P, kst;      // field and mode strides of the working planes
+  int f, nx, nr, J;
+  R h, dr, ih, idr;
+  QDS_HD AdjFwd(const Tile<R, M, false> &t, int f_) {
+    f = f_; nx = t.nx; nr = t.nr; J = t.J;
+    h = t.h; dr = t.dr; ih = t.ih; idr = t.idr;
+    jx = t.jx; jt = t.jt; sext = t.sext;
+    P = (unsigned)t.P;
+    kst = (unsigned)(t.nx * t.ld);
+    int s0 = f + t.s, s1 = f + 1 + t.s;  // ring slots (f + 1 <= nx - 1)
+    if (s0 >= nx) s0 -= nx;
+    if (s1 >= nx) s1 -= nx;
+    c0 = t.o + (unsigned)(s0 * t.ld);
+    c1 = t.o + (unsigned)(s1 * t.ld);
+#if defined(QDS_EMU)
+    o = t.o;
+    len = t.state_len;
+#endif
   }
-  if (st == AD_UNTA) {
-    // T_a^+(c) = T_a^+(c-1) + h G(c-1);  T_a^-(c) = T_a^-(c+1) + h G(c)
-    for (int k = 0; k < M; k++) {
-      a.s(SB_G, k, w, j) = a.in_face(w) ? h * (a.sv(SB_TAP, k, w + 1, j) + a.sv(SB_TAM, k, w, j)) : zero<R>();
-      a.old(TAP, k, w, j) = a.sv(SB_TAP, k, w + 1, j);
-      a.old(TAM, k, w, j) = a.sv(SB_TAM, k, w - 1, j);
-    }
-    return;
+#if defined(QDS_EMU)
+  const C<R> *o;
+  size_t len;
+#endif
+  QDS_HD C<R> cell(int field, int k, int w, int j) const {
+    const C<R> *p = (w == f ? c0 : c1) + ((unsigned)field * P + (unsigned)k * kst + (unsigned)j);
+#if defined(QDS_EMU)
+    QDS_CHECK((w == f || w == f + 1) && j >= 0 && j < nr && (size_t)(p - o) < len, "adjoint forward read");
+#endif
+    return ldg(p);
   }
-  if (st == AD_UNSHIFT) {
-    for (int k = 0; k < M; k++) {
-      // adjoints of the new T at cell c (effective: with the fold of the
-      // outer box into row J-1 for T_r)
-      auto boxBt = [&](int c) -> C<R> {  // adjoint of B_th^(n+1) on the last half row at cell c
-        return a.sv(SB_TRP, k, c, J) - a.sv(SB_TRM, k, c, J);
-      };
-      auto trpn = [&](int c, int jj) -> C<R> {
-        if (!a.in_cell(c)) return zero<R>();
-        C<R> v = a.s(SB_TRP, k, c, jj);
-        if (jj == J - 1) v += (R(0.5) * (-(ka - kb) / (ka + kb))) * boxBt(c);
-        return v;
-      };
-      auto trmn = [&](int c, int jj) -> C<R> {
-        if (!a.in_cell(c)) return zero<R>();
-        C<R> v = a.s(SB_TRM, k, c, jj);
-        if (jj == J - 1) v -= (R(0.5) * (-(ka - kb) / (ka + kb))) * boxBt(c);
-        return v;
-      };
-      auto ttn = [&](int plane, int c, int jj) -> C<R> {
-        if (!a.in_cell(c)) return zero<R>();
-        if (jj == 0 && k != 1) return zero<R>();
-        return a.s(plane, k, c, jj);
-      };
-      // ---- the old T at cell w: the shifted copies (-x for T_r^+, T_th^-,
-      // +x for T_r^-, T_th^+) ----
-      {
-        const int c = w;
-        if (j < J) {
-          cadd(a.oldp(TRP, k, c, j), trpn(c + 1, j));
-          cadd(a.oldp(TRM, k, c, j), trmn(c - 1, j));
-        } else {
-          // last half row: E_r^(n+1)(c') = (T_r^+(c'-1) + T_r^-(c'+1))/2 + ...
-          C<R> er_r = a.sv(SB_TRP, k, c + 1, J) + a.sv(SB_TRM, k, c + 1, J);
-          C<R> er_l = a.sv(SB_TRP, k, c - 1, J) + a.sv(SB_TRM, k, c - 1, J);
-          if (a.in_cell(c + 1)) cadd(a.oldp(TRP, k, c, J), R(0.5) * er_r);
-          if (a.in_cell(c - 1)) cadd(a.oldp(TRM, k, c, J), R(0.5) * er_l);
-        }
-        cadd(a.oldp(TTP, k, c, j), ttn(SB_TTP, c - 1, j));
-        cadd(a.oldp(TTM, k, c, j), ttn(SB_TTM, c + 1, j));
-      }
-      // ---- the outer T_r box of cell w (last half row): old-field terms ----
+  QDS_HD C<R> face(int field, int k, int w, int j) const { return cell(field, k, w, j); }
+  QDS_HD C<R> Er(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TRP, k, w, j) + cell(grp + TRM, k, w, j)); }
+  QDS_HD C<R> Bt(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TRP, k, w, j) - cell(grp + TRM, k, w, j)); }
+  QDS_HD C<R> Et(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) + cell(grp + TTM, k, w, j)); }
+  QDS_HD C<R> Br(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) - cell(grp + TTM, k, w, j)); }
+  // caller's sources [M][nx][nr] in window order
+  QDS_HD C<R> srcv(const C<R> *a, int k, int w, int j) const {
+    if (!a) return zero<R>();
+    return ldg(a + ((unsigned)(k * nx + w) * (unsigned)nr + (unsigned)j));
+  }
+};
+
+// AD_SRC, face (f, j): Gamma_a's adjoint from the new T_a (Eqs. Ta_plus/
+// Ta_minus_update with the phi update's share), d L / d g, and the transpose
+// of the bilinear source S_a (Eq. mode_convolution) at the forward state:
+// the adjoints of its six face means, kept per face for the next stages.
+template <class R, int M>
+QDS_HD void adj_src(const Adj<R, M> &a, int f, int j, double &dg_acc) {
+  if (!a.in_face(f)) return;
+  const int J = a.J;
+  const bool top = (j == J);
+  const R h = a.h;
+  const AdjFwd<R, M> t(a.f, f);
+  C<R> Gb[M], Sb[M];
+  #pragma unroll
+  for (int k = 0; k < M; k++) {
+    Gb[k] = h * (a.tap_n(k, f + 1, j) + a.tam_n(k, f, j));
+    Sb[k] = a.gs * Gb[k];
+    a.s(SB_G, k, f, j) = Gb[k];
+  }
+  // S = C{eX, bX} + (1/2)(C{rp, qp} - C{rm, qm}) at the forward state
+  C<R> eX[M], bX[M], rp[M], rm[M], qp[M], qm[M];
+  #pragma unroll
+  for (int k = 0; k < M; k++) {
+    const C<R> exn = ex_update(t, 0, k, f, j, t.srcv(t.jx, k, f, j));
+    const C<R> bxn = (j < J) ? bx_interior(t, 0, k, f, j)
+                             : bx_outer(t, 0, k, f, R(0.5) * (t.srcv(t.jt, k, f, j) + t.srcv(t.jt, k, f + 1, j)),
+                                        bx_interior(t, 0, k, f, j - 1));
+    const C<R> exn1 = top ? exn : ex_update(t, 0, k, f, j + 1, t.srcv(t.jx, k, f, j + 1));
+    const C<R> eo = t.face(EX, k, f, j), eo1 = top ? eo : t.face(EX, k, f, j + 1);
+    eX[k] = R(0.25) * (eo + eo1 + exn + exn1);
+    bX[k] = R(0.5) * (t.face(BX, k, f, j) + bxn);
+    const int j1 = top ? j : j + 1;
+    rp[k] = R(0.5) * (t.cell(TRP, k, f, j) + t.cell(TRP, k, f + 1, j));
+    rm[k] = R(0.5) * (t.cell(TRM, k, f, j) + t.cell(TRM, k, f + 1, j));
+    qp[k] = R(0.25) * (t.cell(TTP, k, f, j) + t.cell(TTP, k, f + 1, j) + t.cell(TTP, k, f, j1) + t.cell(TTP, k, f + 1, j1));
+    qm[k] = R(0.25) * (t.cell(TTM, k, f, j) + t.cell(TTM, k, f + 1, j) + t.cell(TTM, k, f, j1) + t.cell(TTM, k, f + 1, j1));
+  }
+  if (a.dg) {  // Gamma_a depends on g through g S (physical variables)
+    double acc = 0;
+    #pragma unroll
+    for (int m = 0; m < M; m++) {
+      C<R> S = conv<R, M>(m, eX, bX) + R(0.5) * (conv<R, M>(m, rp, qp) - conv<R, M>(m, rm, qm));
+      S += t.srcv(t.sext, m, f, j);
+      acc += (double)Gb[m].re * S.re + (double)Gb[m].im * S.im;
+    }
+    dg_acc += acc;  // the caller reduces and adds to *a.dg
+  }
+  C<R> eXb[M], bXb[M], rpb[M], rmb[M], qpb[M], qmb[M];
+  #pragma unroll
+  for (int k = 0; k < M; k++) eXb[k] = bXb[k] = rpb[k] = rmb[k] = qpb[k] = qmb[k] = zero<R>();
+  conv_T<R, M>(eX, bX, Sb, R(1), eXb, bXb);
+  conv_T<R, M>(rp, qp, Sb, R(0.5), rpb, qpb);
+  conv_T<R, M>(rm, qm, Sb, R(-0.5), rmb, qmb);
+  #pragma unroll
+  for (int k = 0; k < M; k++) {
+    a.s(SB_EXB, k, f, j) = eXb[k];
+    a.s(SB_BXB, k, f, j) = bXb[k];
+    a.s(SB_RPB, k, f, j) = rpb[k];
+    a.s(SB_RMB, k, f, j) = rmb[k];
+    a.s(SB_QPB, k, f, j) = qpb[k];
+    a.s(SB_QMB, k, f, j) = qmb[k];
+  }
+}
+
+// AD_LEAP, face (f, j): the total adjoints of E_x and B_x^(n+1/2) (the new
+// state's, the T shift's face sources', the source means') and from them the
+// old E_x, B_x (Eqs. Ex_update, axis_Ex, Phix_explicit, em_r_open_bx).
+template <class R>
+struct LeapOut {
+  C<R> ex, bx;    // the old E_x, B_x adjoints
+  C<R> ext, bxt;  // the total E_x, B_x^(n+1/2) adjoints (faces only)
+};
+
+template <class R, int M>
+QDS_HD LeapOut<R> leap_vals(const Adj<R, M> &a, int k, int f, int j) {
+  const int J = a.J;
+  LeapOut<R> o;
+  o.ex = o.bx = o.ext = o.bxt = zero<R>();
+  if (!a.in_face(f)) return o;
+  const R kab = a.kab();
+  {
+    // eX(f, jj) is the mean of E_x at rows jj and jj + 1 (jj on the last row)
+    // of the old and the new E_x: row j takes eX of rows j and j - 1
+    const C<R> e4 = R(0.25) * ((j == J ? R(2) : R(1)) * a.sr(SB_EXB, k, f, j) + a.sf(SB_EXB, k, f, j - 1));
+    C<R> ex, bx;
+    unshift_face(a, k, f, j, ex, bx);
+    const C<R> ext = a.lnew(EX, k, f, j) + ex + e4;
+    C<R> bxt = a.lnew(BX, k, f, j) + bx + R(0.5) * a.sr(SB_BXB, k, f, j);
+    C<R> bxJ = zero<R>();  // the last row's, for the box of row J - 1
+    if (j == J - 1) {
+      C<R> exJ, bxJs;
+      unshift_face(a, k, f, J, exJ, bxJs);
+      bxJ = a.lnew(BX, k, f, J) + bxJs + R(0.5) * a.sr(SB_BXB, k, f, J);
+      bxt -= kab * bxJ;  // the box reads B_x^(n+1/2)(J - 1)
+    }
+    o.ext = ext;
+    o.bxt = bxt;
+    // E_x^(n+1/2) = E_x^(n-1/2) + h Gamma_x; on the axis only m = 0 moves
+    o.ex = ((j > 0 || k == 0) ? ext : zero<R>()) + e4;
+    // B_x: interior rows carry it over; the box of the last row weighs
+    // B_x(J) by (a - b)/(a + b) and B_x(J - 1) by 1
+    C<R> ob = R(0.5) * a.sr(SB_BXB, k, f, j);
+    if (j < J) ob += bxt;
+    else ob += kab * bxt;
+    if (j == J - 1) ob += bxJ;
+    o.bx = ob;
+  }
+  return o;
+}
+
+template <class R, int M>
+QDS_HD void leap_store(const Adj<R, M> &a, int k, int f, int j, const LeapOut<R> &o) {
+  a.old(EX, k, f, j) = o.ex;
+  a.old(BX, k, f, j) = o.bx;
+  if (a.in_face(f)) {
+    a.s(SB_EXT, k, f, j) = o.ext;
+    a.s(SB_BXT, k, f, j) = o.bxt;
+  }
+}
+
+// AD_CELL, cell (c, j): the old T, T_a, phi and phi_prev, gathered from the
+// new state's adjoint (shifted copies), the outer boxes of the cells c - 1 ..
+// c + 1, and the face adjoints of faces c - 1 and c (source means, E_x, B_x).
+template <class R>
+struct CellOut {
+  C<R> t[4];      // the old T_r^+, T_r^-, T_th^+, T_th^-
+  C<R> tap, tam, ph, prev;
+};
+
+template <class R, int M>
+QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
+  CellOut<R> o;
+  const int J = a.J;
+  const R h = a.h, dr = a.dr, idr = a.idr, ih = a.ih;
+  const R ka = a.ka(), kb = a.kb(), kab = a.kab();
+  const R rJ = R(J) * dr;
+  {
+    C<R> trp = zero<R>(), trm = zero<R>(), ttp = zero<R>(), ttm = zero<R>();
+    // the transverse fields map to T^+- as E_r, B_th -> T_r and E_th, B_r -> T_th
+    auto Er = [&](C<R> v) { trp += R(0.5) * v; trm += R(0.5) * v; };
+    auto Bt = [&](C<R> v) { trp += R(0.5) * v; trm -= R(0.5) * v; };
+    auto Et = [&](C<R> v) { ttp += R(0.5) * v; ttm += R(0.5) * v; };
+    auto Br = [&](C<R> v) { ttp += R(0.5) * v; ttm -= R(0.5) * v; };
+    // ---- the shifted copies (-x for T_r^+, T_th^-, +x for T_r^-, T_th^+) ----
+    if (j < J) {
+      trp += a.trp_e(k, c + 1, j);
+      trm += a.trm_e(k, c - 1, j);
+    } else {  // last half row: E_r^(n+1)(c') takes (T_r^+(c'-1) + T_r^-(c'+1))/2
+      if (a.in_cell(c + 1)) trp += R(0.5) * (a.tn(0, k, c + 1, J) + a.tn(1, k, c + 1, J));
+      if (a.in_cell(c - 1)) trm += R(0.5) * (a.tn(0, k, c - 1, J) + a.tn(1, k, c - 1, J));
+    }
+    ttp += a.tt_e(2, k, c - 1, j);
+    ttm += a.tt_e(3, k, c + 1, j);
+    // ---- the outer T_r boxes of cells c - 1, c, c + 1 (Eq. em_r_open_bt) ----
+    if (j >= J - 1) {
+      // B_th^(n+1) = (R - (a-b) B_th^(n+1)(J-1) + (a-b) B_th(J) + (a+b) B_th(J-1)) / (a+b),
+      // R = -(1/4) ih (E_r(c+1) - E_r(c-1)) - (1/(2 rJ)) (B_th + i m B_r) + ...
+      const C<R> Bb = a.box_bt(k, c);
+      const C<R> Rb = (R(1) / (ka + kb)) * Bb;
+      const C<R> er_m = (R(-0.125) * ih) * ((R(1) / (ka + kb)) * a.box_bt(k, c - 1));  // from cell c - 1
+      const C<R> er_p = (R(-0.125) * ih) * ((R(1) / (ka + kb)) * a.box_bt(k, c + 1));  // from cell c + 1
       if (j == J) {
-        const int c = w;
-        const R rJ = R(J) * dr;
-        C<R> Bb = boxBt(c);
-        if (Bb.re != R(0) || Bb.im != R(0)) {
-          // B_th^(n+1) = (R - (a-b) bt_in_new + (a-b) Bo + (a+b) Bi)/(a+b)
-          a.add_Bt(k, c, J, ((ka - kb) / (ka + kb)) * Bb);
-          a.add_Bt(k, c, J - 1, Bb);
-          C<R> Rb = (R(1) / (ka + kb)) * Bb;
-          // R = -(1/4)(ih)(Er_r - Er_l) - (1/2 rJ)(Bth + i k Br) + (1/4)(jx..)
-          C<R> er = (R(-0.125) * t.ih) * Rb;
-          a.add_Er(k, c + 1, J - 1, er);
-          a.add_Er(k, c + 1, J, er);
-          a.add_Er(k, c - 1, J - 1, -er);
-          a.add_Er(k, c - 1, J, -er);
-          a.add_Bt(k, c, J - 1, (R(-0.25) / rJ) * Rb);
-          a.add_Bt(k, c, J, (R(-0.25) / rJ) * Rb);
-          a.add_Br(k, c, J, imul(R(k) * R(0.5) / rJ, Rb));  // conj(-i k/(2 rJ)) = i k/(2 rJ)
-        }
+        Bt(kab * Bb + (R(-0.25) / rJ) * Rb);
+        Br(imul(R(k) * R(0.5) / rJ, Rb));
+      } else {
+        Bt(Bb + (R(-0.25) / rJ) * Rb);
       }
-      // ---- face w: adjoints of the sources, gathered into E_x, B_x ----
-      if (a.in_face(w)) {
-        const int f = w;
-        // source adjoints at face f, row jj
-        auto Sr = [&](int jj, C<R> &Gb, C<R> &Pb) {  // T_r sources (half row jj < J)
-          C<R> sp = h * trpn(f + 1, jj), sm = h * trmn(f, jj);
-          Gb = sp + sm;
-          Pb = sp - sm;
-        };
-        auto St = [&](int jj, C<R> &Gb, C<R> &Pb) {  // T_th sources (row jj)
-          C<R> sp = h * ttn(SB_TTP, f, jj), sm = h * ttn(SB_TTM, f + 1, jj);
-          Gb = sp + sm;
-          Pb = sp - sm;
-        };
-        C<R> ex = zero<R>(), bx = zero<R>();
-        C<R> Gr, Pr, Gt, Pt;
-        // E_x^(n+1/2)(f, j): Phi_r(f, j) = (Ex(j+1) - Ex(j))/dr, Phi_r(f, j-1), Phi_th
-        if (j < J) { Sr(j, Gr, Pr); ex -= idr * Pr; }
-        if (j >= 1 && j - 1 < J) { Sr(j - 1, Gr, Pr); ex += idr * Pr; }
-        if (j >= 1) { St(j, Gt, Pt); ex += imul(-R(k) / (R(j) * dr), Pt); }
-        if (k == 1 && j <= 1) {  // axis Phi_th = i (Ex(1) - Ex(0))/dr
-          St(0, Gt, Pt);
-          ex += imul(j == 1 ? -idr : idr, Pt);
-        }
-        // B_x^(n+1/2)(f, j): Gamma_r(f, j), Gamma_th(f, j), Gamma_th(f, j+1)
+      Er(er_m - er_p);
+    }
+    // ---- faces c - 1 and c ----
+    for (int df = 0; df < 2; df++) {
+      const int f = c - 1 + df;
+      if (!a.in_face(f)) continue;
+      // the source means: rp, rm on row j; qp, qm on rows j, j + 1 (j, j on the last)
+      trp += R(0.5) * a.sr(SB_RPB, k, f, j);
+      trm += R(0.5) * a.sr(SB_RMB, k, f, j);
+      const R tw = (j == J) ? R(2) : R(1);
+      ttp += R(0.25) * (tw * a.sr(SB_QPB, k, f, j) + a.sf(SB_QPB, k, f, j - 1));
+      ttm += R(0.25) * (tw * a.sr(SB_QMB, k, f, j) + a.sf(SB_QMB, k, f, j - 1));
+      // E_x leapfrog (Eq. Ex_update; axis_Ex for m = 0)
+      if (j == 0 && k == 0) Bt((h * R(2) * idr) * a.sr(SB_EXT, k, f, 0));
+      if (j >= 1) {
+        const C<R> eb = a.sr(SB_EXT, k, f, j);
+        const R rj = R(j) * dr;
+        Bt((R(0.5) * h * (R(j) + R(0.5)) / rj) * eb);
+        Br(imul(R(-0.5) * h * R(k) / rj, eb));
+      }
+      if (j + 1 <= J) {
+        const R rj = R(j + 1) * dr;
+        Bt((R(-0.5) * h * (R(j) + R(0.5)) / rj) * a.sr(SB_EXT, k, f, j + 1));
+      }
+      // B_x leapfrog (Eq. Phix_explicit) on rows j - 1, j; the box of row J
+      if (j >= 1) {
+        const R rh = (R(j) - R(0.5)) * dr;
+        Et((R(-0.5) * h * R(j) / rh) * a.sr(SB_BXT, k, f, j - 1));
+      }
+      if (j < J) {
+        const C<R> bb = a.sr(SB_BXT, k, f, j);
         const R rh = (R(j) + R(0.5)) * dr;
-        if (j < J) { Sr(j, Gr, Pr); bx += imul(R(k) / rh, Gr); }
-        else {
-          // E_r^(n+1) on the last row takes Gamma_r of faces c-1 and c:
-          C<R> Gb = (R(0.5) * h) * (a.sv(SB_TRP, k, f + 1, J) + a.sv(SB_TRM, k, f + 1, J) +
-                                     a.sv(SB_TRP, k, f, J) + a.sv(SB_TRM, k, f, J));
-          bx += imul(R(k) / rh, Gb);
+        Et((R(0.5) * h * R(j) / rh) * bb);
+        Er(imul(R(0.5) * h * R(k) / rh, bb));
+      }
+      if (j >= J - 1) {
+        // B_x(J) = (R - (a-b) B_x^(n+1/2)(J-1) + (a-b) B_x(J) + (a+b) B_x(J-1)) / (a+b),
+        // R = (1/2) ih (B_r(f+1, J) - B_r(f, J)) - (1/(2 rJ)) (E_th + i m E_r) - ...
+        const C<R> Rb = (R(1) / (ka + kb)) * a.sr(SB_BXT, k, f, J);
+        if (j == J) {
+          Br((df == 0 ? R(0.5) : R(-0.5)) * ih * Rb);  // face c - 1 reads B_r(c) with +, face c with -
+          Et((R(-0.25) / rJ) * Rb);
         }
-        if (j >= 1) { St(j, Gt, Pt); bx -= idr * Gt; }
-        else if (k == 1) { St(0, Gt, Pt); bx += (-R(2) * idr) * Gt; }
-        if (j + 1 <= J && j + 1 >= 1) { St(j + 1, Gt, Pt); bx += idr * Gt; }
-        a.s(SB_EX, k, f, j) += ex;
-        a.s(SB_BX, k, f, j) += bx;
+        Er(imul(R(k) * R(0.125) / rJ, Rb));
       }
     }
-    return;
-  }
-  if (st == AD_UNSRC) {
-    if (!a.in_face(w)) return;
-    const int f = w;
-    const bool top = (j == J);
-    const R rh = (R(j) + R(0.5)) * dr;
-    const R den = R(1) / ((R(j) + R(0.5)) * dr * dr);
-    // phi adjoint from Gamma_a of rows j-1, j, j+1 (Laplacian and mass)
-    C<R> Gb[M];
-    for (int k = 0; k < M; k++) {
-      Gb[k] = a.s(SB_G, k, f, j);
-      C<R> v = zero<R>();
-      // row j itself
-      {
-        R cc = -(R(2 * j + 1)) * den - (R(k * k) / (rh * rh) + a.ma2);
-        if (top) cc += R(J + 1) * den * (-R(2) * dr * t.ih);  // ghost: -(2 dr/h) phi(J)
-        v += cc * Gb[k];
-      }
-      if (j >= 1) {  // row j-1 uses phi(j) as its upper neighbour
+    o.t[0] = trp;
+    o.t[1] = trm;
+    o.t[2] = ttp;
+    o.t[3] = ttm;
+    // ---- T_a: the shifted copies of the new T_a adjoints ----
+    o.tap = a.tap_n(k, c + 1, j);
+    o.tam = a.tam_n(k, c - 1, j);
+    // ---- phi: carried over by the phi update, Gamma_a's Laplacian and mass
+    // with the outer ghost (-(2 dr/h) phi(J) + phi(J-1)), phi_prev ----
+    C<R> ph = a.in_face(c) ? a.lnew(PHI, k, c, j) : zero<R>();
+    if (a.in_face(c)) {
+      if (j == J) ph += a.lnew_prev(k, c);
+      const R rh = (R(j) + R(0.5)) * dr;
+      const R den = R(1) / ((R(j) + R(0.5)) * dr * dr);
+      R cc = -(R(2 * j + 1)) * den - (R(k * k) / (rh * rh) + a.ma2);
+      if (j == J) cc += R(J + 1) * den * (-R(2) * dr * ih);
+      ph += cc * a.sr(SB_G, k, c, j);
+      if (j >= 1) {
         const int i = j - 1;
-        const R di = R(1) / ((R(i) + R(0.5)) * dr * dr);
-        v += (R(i + 1) * di) * a.s(SB_G, k, f, i);
+        ph += (R(i + 1) / ((R(i) + R(0.5)) * dr * dr)) * a.sr(SB_G, k, c, i);
       }
-      if (j + 1 <= J) {  // row j+1 uses phi(j) as its lower neighbour
+      if (j + 1 <= J) {
         const int i = j + 1;
         const R di = R(1) / ((R(i) + R(0.5)) * dr * dr);
-        C<R> g1 = a.s(SB_G, k, f, i);
-        v += (R(i) * di) * g1;
-        if (i == J) v += (R(J + 1) * di) * g1;  // ghost of row J: + phi(J-1)
-      }
-      cadd(a.oldp(PHI, k, f, j), v);
-      if (top) cadd(a.oldprev(k, f), (R(J + 1) * den * R(2) * dr * t.ih) * Gb[k]);
-    }
-    // source: Gamma_a += gs S;  S = C{eX, bX} + (1/2)(C{rp, qp} - C{rm, qm})
-    C<R> Sb[M];
-    for (int m = 0; m < M; m++) Sb[m] = a.gs * Gb[m];
-    C<R> eX[M], bX[M], rp[M], rm[M], qp[M], qm[M];
-    C<R> exn[M], exn1[M], bxn[M];
-    for (int k = 0; k < M; k++) {
-      exn[k] = ex_update(t, 0, k, f, j, t.srcv(t.jx, k, f, j));
-      bxn[k] = (j < J) ? bx_interior(t, 0, k, f, j)
-                       : bx_outer(t, 0, k, f, R(0.5) * (t.srcv(t.jt, k, f, j) + t.srcv(t.jt, k, f + 1, j)),
-                                  bx_interior(t, 0, k, f, j - 1));
-      exn1[k] = top ? exn[k] : ex_update(t, 0, k, f, j + 1, t.srcv(t.jx, k, f, j + 1));
-      C<R> eo = t.face(EX, k, f, j), eo1 = top ? eo : t.face(EX, k, f, j + 1);
-      eX[k] = R(0.25) * (eo + eo1 + exn[k] + exn1[k]);
-      bX[k] = R(0.5) * (t.face(BX, k, f, j) + bxn[k]);
-      const int j1 = top ? j : j + 1;
-      rp[k] = R(0.5) * (t.cell(TRP, k, f, j) + t.cell(TRP, k, f + 1, j));
-      rm[k] = R(0.5) * (t.cell(TRM, k, f, j) + t.cell(TRM, k, f + 1, j));
-      qp[k] = R(0.25) * (t.cell(TTP, k, f, j) + t.cell(TTP, k, f + 1, j) + t.cell(TTP, k, f, j1) + t.cell(TTP, k, f + 1, j1));
-      qm[k] = R(0.25) * (t.cell(TTM, k, f, j) + t.cell(TTM, k, f + 1, j) + t.cell(TTM, k, f, j1) + t.cell(TTM, k, f + 1, j1));
-    }
-    if (a.dg) {  // dL/dg: Gamma_a depends on g through g S (physical variables)
-      double acc = 0;
-      for (int m = 0; m < M; m++) {
-        C<R> S = conv<R, M>(m, eX, bX) + R(0.5) * (conv<R, M>(m, rp, qp) - conv<R, M>(m, rm, qm));
-        S += t.srcv(t.sext, m, f, j);
-        acc += (double)Gb[m].re * S.re + (double)Gb[m].im * S.im;
-      }
-      dg_acc += acc;  // the caller reduces and adds to *a.dg
-    }
-    C<R> eXb[M], bXb[M], rpb[M], rmb[M], qpb[M], qmb[M];
-    for (int k = 0; k < M; k++) eXb[k] = bXb[k] = rpb[k] = rmb[k] = qpb[k] = qmb[k] = zero<R>();
-    conv_T<R, M>(eX, bX, Sb, R(1), eXb, bXb);
-    conv_T<R, M>(rp, qp, Sb, R(0.5), rpb, qpb);
-    conv_T<R, M>(rm, qm, Sb, R(-0.5), rmb, qmb);
-    for (int k = 0; k < M; k++) {
-      // eX = (Ex(j) + Ex(j1) + Exn(j) + Exn(j1))/4, j1 = j on the last row
-      C<R> e4 = R(0.25) * eXb[k];
-      cadd(a.oldp(EX, k, f, j), e4);
-      cadd(&a.s(SB_EX, k, f, j), e4);
-      const int j1 = top ? j : j + 1;
-      cadd(a.oldp(EX, k, f, j1), e4);
-      cadd(&a.s(SB_EX, k, f, j1), e4);
-      cadd(a.oldp(BX, k, f, j), R(0.5) * bXb[k]);
-      cadd(&a.s(SB_BX, k, f, j), R(0.5) * bXb[k]);
-      for (int dc = 0; dc < 2; dc++) {
-        if (!a.in_cell(f + dc)) continue;
-        cadd(a.oldp(TRP, k, f + dc, j), R(0.5) * rpb[k]);
-        cadd(a.oldp(TRM, k, f + dc, j), R(0.5) * rmb[k]);
-        cadd(a.oldp(TTP, k, f + dc, j), R(0.25) * qpb[k]);
-        cadd(a.oldp(TTM, k, f + dc, j), R(0.25) * qmb[k]);
-        cadd(a.oldp(TTP, k, f + dc, j1), R(0.25) * qpb[k]);
-        cadd(a.oldp(TTM, k, f + dc, j1), R(0.25) * qmb[k]);
+        R w = R(i) * di;
+        if (i == J) w += R(J + 1) * di;
+        ph += w * a.sr(SB_G, k, c, i);
       }
     }
-    return;
+    o.ph = ph;
+    o.prev = zero<R>();
+    if (j == J && a.in_face(c)) {
+      const R den = R(1) / ((R(J) + R(0.5)) * dr * dr);
+      o.prev = (R(J + 1) * den * R(2) * dr * ih) * a.sr(SB_G, k, c, J);
+    }
   }
-  if (st == AD_UNLEAP) {
-    if (!a.in_face(w)) return;
-    const int f = w;
-    for (int k = 0; k < M; k++) {
-      // ---- E_x^(n+1/2) = E_x^(n-1/2) + h Gamma_x (Eqs. Ex_update, axis_Ex) ----
-      const C<R> eb = a.s(SB_EX, k, f, j);
-      if (j == 0) {
-        if (k == 0) {  // h (4/dr) (Bt(f,0) + Bt(f+1,0))/2
-          cadd(a.oldp(EX, k, f, 0), eb);
-          C<R> v = (h * R(2) * idr) * eb;
-          a.add_Bt(k, f, 0, v);
-          a.add_Bt(k, f + 1, 0, v);
-        }  // m != 0: E_x is held at zero on the axis
-      } else {
-        cadd(a.oldp(EX, k, f, j), eb);
-        const R rj = R(j) * dr;
-        C<R> bhi = (h * (R(j) + R(0.5)) / rj) * eb, blo = (-h * (R(j) - R(0.5)) / rj) * eb;
-        C<R> brb = imul(-h * R(k) / rj, eb);  // conj(h i k / r_j)
-        for (int dc = 0; dc < 2; dc++) {
-          a.add_Bt(k, f + dc, j, R(0.5) * bhi);
-          a.add_Bt(k, f + dc, j - 1, R(0.5) * blo);
-          a.add_Br(k, f + dc, j, R(0.5) * brb);
-        }
-      }
-      // ---- B_x^(n+1/2) (Eq. Phix_explicit; outer row: Eq. em_r_open_bx) ----
-      C<R> bbar = a.s(SB_BX, k, f, j);
-      if (j == J - 1) bbar += (-(ka - kb) / (ka + kb)) * a.s(SB_BX, k, f, J);  // box uses B_x^(n+1/2)(J-1)
-      if (j < J) {
-        cadd(a.oldp(BX, k, f, j), bbar);
-        const R rh = (R(j) + R(0.5)) * dr;
-        C<R> ehi = (-h * R(j + 1) / rh) * bbar, elo = (h * R(j) / rh) * bbar;
-        C<R> erb = imul(h * R(k) / rh, bbar);  // conj(-h i k / r_{j+1/2})
-        for (int dc = 0; dc < 2; dc++) {
-          a.add_Et(k, f + dc, j + 1, R(0.5) * ehi);
-          a.add_Et(k, f + dc, j, R(0.5) * elo);
-          a.add_Er(k, f + dc, j, R(0.5) * erb);
-        }
-      } else {
-        // B_x(J) = (R - (a-b) B_x^(n+1/2)(J-1) + (a-b) B_x(J) + (a+b) B_x(J-1))/(a+b)
-        cadd(a.oldp(BX, k, f, J), ((ka - kb) / (ka + kb)) * bbar);
-        cadd(a.oldp(BX, k, f, J - 1), bbar);
-        const C<R> Rb = (R(1) / (ka + kb)) * bbar;
-        const R rJ = R(J) * dr;
-        // R = (1/2) ih (Br(f+1,J) - Br(f,J)) - (1/(2 rJ)) (Eth + i k Er4) - jt/2
-        a.add_Br(k, f + 1, J, (R(0.5) * t.ih) * Rb);
-        a.add_Br(k, f, J, (R(-0.5) * t.ih) * Rb);
-        a.add_Et(k, f, J, (R(-0.25) / rJ) * Rb);
-        a.add_Et(k, f + 1, J, (R(-0.25) / rJ) * Rb);
-        C<R> er4 = imul(R(k) * R(0.125) / rJ, Rb);  // (1/4) conj(-i k/(2 rJ))
-        a.add_Er(k, f, J - 1, er4);
-        a.add_Er(k, f, J, er4);
-        a.add_Er(k, f + 1, J - 1, er4);
-        a.add_Er(k, f + 1, J, er4);
-      }
-    }
-    return;
-  }
+  return o;
+}
+
+template <class R, int M>
+QDS_HD void cell_store(const Adj<R, M> &a, int k, int c, int j, const CellOut<R> &o) {
+#pragma unroll
+  for (int q = 0; q < 4; q++) a.old(TRP + q, k, c, j) = o.t[q];
+  a.old(TAP, k, c, j) = o.tap;
+  a.old(TAM, k, c, j) = o.tam;
+  a.old(PHI, k, c, j) = o.ph;
+  if (j == a.J) a.oldprev(k, c) = o.prev;
+  if (a.zero_regen)
+    for (int fl = TRP1; fl < NFIELD; fl++) a.old(fl, k, c, j) = zero<R>();
+}
+
+// One point of a pass: AD_SRC covers every mode of face w (the source
+// couples the modes); AD_LEAP and AD_CELL one mode k.
+template <class R, int M>
+QDS_HD void adj_point(const Adj<R, M> &a, int st, int k, int w, int j, double &dg_acc) {
+  if (st == AD_SRC) adj_src<R, M>(a, w, j, dg_acc);
+  else if (st == AD_LEAP) leap_store<R, M>(a, k, w, j, leap_vals<R, M>(a, k, w, j));
+  else cell_store<R, M>(a, k, w, j, cell_vals<R, M>(a, k, w, j));
 }
 
 }  // namespace qds

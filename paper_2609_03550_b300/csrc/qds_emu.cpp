@@ -364,16 +364,18 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   t.cw = -(1 << 28);  // set per column below
   t.state_len = E;
   a.ln = LN.data(); a.lo = LO.data(); a.sb = SB.data(); a.dg = dg;
-  a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = P;
+  a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = (unsigned)P;
   a.mw = (flags & F_MOVING_WINDOW) != 0;
+  a.zero_regen = true;
   a.h = I.h; a.dr = I.dr; a.ih = I.inv_h; a.idr = I.inv_dr;
   a.gs = I.gs; a.ma2 = I.ma2;
   double acc = 0;
   for (int st = 0; st < N_ADSTAGE; st++)
-    for (int w = 0; w < nx; w++) {
-      a.f.set_point(w);
-      for (int j = 0; j < nr; j++) adj_point<R, M>(a, st, w, j, acc);
-    }
+    for (int k = 0; k < (st == AD_SRC ? 1 : M); k++)
+      for (int w = 0; w < nx; w++) {
+        a.f.set_point(w);
+        for (int j = 0; j < nr; j++) adj_point<R, M>(a, st, k, w, j, acc);
+      }
   if (dg) *dg += acc;
   for (size_t q = 0; q < E; q++) {
     lam_old[2 * q] = (double)LO[q].re;

@@ -325,12 +325,14 @@ class DeviceBunchSources:
         self._draw(step, self.buf)
         return tuple(self.buf)
 
-    def fill(self, n0, count):
+    def fill(self, n0, count, out=None):
         """The currents of steps n0 .. n0+count-1 (the values __call__ gives)
-        as three tensors [count, M, nx, nr], in buffers kept for reuse."""
+        as three tensors [count, M, nx, nr], in buffers kept for reuse (or in
+        ``out``, three such tensors of at least ``count`` steps)."""
         torch = self.torch
-        blk = getattr(self, "_blk", None)
+        blk = out if out is not None else getattr(self, "_blk", None)
         if blk is None or blk[0].shape[0] < count:
+            assert out is None
             blk = self._blk = [torch.empty((count, self.M, self.nx, self.nr), dtype=self.dtype, device=self.device)
                                for _ in range(3)]
         for k in range(count):

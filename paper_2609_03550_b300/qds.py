@@ -300,7 +300,8 @@ class QDSSolver:
         ``fwd_snap`` a working snapshot at the start of the step taken
         ``fwd_step`` steps after the import; ``lam_in`` / ``lam_out`` the
         adjoint after / before the step, canonical layout in the working
-        precision (complex64 in FP32), distinct tensors."""
+        precision (complex64 in FP32), distinct tensors; the regenerated
+        planes of ``lam_out`` are left as they are."""
         p = self.params[i]
         for t in (lam_in, lam_out):
             assert t.is_cuda and t.is_contiguous() and t.numel() == p.state_elems()

@@ -149,7 +149,7 @@ def test_working_transpose_matches_canonical_transpose(M, mw, prec):
     lam = I.random_state(rng, M, nx, nr, axis_consistent=False) * em_axion_mask(M, nx, nr)
     lam_w = torch.from_numpy(lam).to(DEV).to(rd).contiguous()
     lam_c = lam_w.to(torch.complex128, copy=True)  # a copy also in FP64: adjoint_step works in place
-    out_w = torch.full_like(lam_w, float("nan"))
+    out_w = torch.zeros_like(lam_w)  # the regenerated planes are not written
     dg_c = torch.zeros(1, dtype=torch.float64, device=DEV)
     dg_w = torch.zeros(1, dtype=torch.float64, device=DEV)
     solver.adjoint_step(fwd, lam_c, jx=jx, jth=jt, dLdg=dg_c)
