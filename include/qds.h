@@ -267,6 +267,9 @@ size_t qds_adjoint_work_bytes(const qds_handle *h, int i);
  * fwd_working_dev: a working snapshot of instance i (qds_save_working) taken
  *   fwd_step steps after the state import, at the START of the step (its
  *   EM planes are read; working row stride and window offset).
+ * fwd_next_dev: the snapshot at the END of the step (fwd_step + 1), or NULL.
+ *   Its E_x, B_x planes hold the leapfrog's E_x, B_x^(n+1/2), which the
+ *   transpose otherwise recomputes from fwd_working_dev.
  * lam_in_dev / lam_out_dev: the adjoint of the state after / before the step
  *   in the canonical layout of qds_set_state but in the working precision
  *   (complex64 with QDS_FP32, else complex128), physical variables; distinct
@@ -276,8 +279,8 @@ size_t qds_adjoint_work_bytes(const qds_handle *h, int i);
  * Otherwise as qds_adjoint_step.  Asynchronous on stream. */
 size_t qds_adjoint_work_bytes_w(const qds_handle *h, int i);
 int qds_adjoint_step_w(qds_handle *h, int i, const qds_sources *src, const void *fwd_working_dev,
-                       unsigned long long fwd_step, const void *lam_in_dev, void *lam_out_dev, void *work_dev,
-                       size_t work_bytes, double *dLdg_dev, void *stream);
+                       const void *fwd_next_dev, unsigned long long fwd_step, const void *lam_in_dev,
+                       void *lam_out_dev, void *work_dev, size_t work_bytes, double *dLdg_dev, void *stream);
 
 /* Working snapshots, the checkpoints of the adjoint's recompute (the paper
  * defines no adjoint; these serve qds_adjoint_step_w): the state of instance

@@ -125,7 +125,7 @@ class _Run(torch.autograd.Function):
         dg = torch.zeros(1, dtype=torch.float64, device=lam.device)
         K = spec.interval()
         em_bytes = solver.working_bytes(0, em_only=True)
-        pool = [torch.empty(em_bytes, dtype=torch.uint8, device=lam.device) for _ in range(K)]
+        pool = [torch.empty(em_bytes, dtype=torch.uint8, device=lam.device) for _ in range(K + 1)]
         fill = spec.sources is not None and hasattr(spec.sources, "fill")
         for n0, ck in reversed(ckpts):
             cnt = min(K, spec.nsteps - n0)
@@ -142,9 +142,10 @@ class _Run(torch.autograd.Function):
                 solver.save_working(out=pool[k], em_only=True)
                 jx, jr, jt = blk[k] if blk is not None else spec.sources(n0 + k)
                 solver.step(1, jx=jx, jr=jr, jth=jt)
+            solver.save_working(out=pool[cnt], em_only=True)  # the segment's end: E_x, B_x of its last step
             for k in range(cnt - 1, -1, -1):
                 jx, _, jt = blk[k] if blk is not None else spec.sources(n0 + k)
-                solver.adjoint_step_w(pool[k], n0 + k, lam, lam_b, jx=jx, jth=jt, dLdg=dg)
+                solver.adjoint_step_w(pool[k], n0 + k, lam, lam_b, jx=jx, jth=jt, dLdg=dg, fwd_next=pool[k + 1])
                 lam, lam_b = lam_b, lam
         ctx.ckpts = None
         return lam.to(torch.complex128), dg.reshape(()).to(torch.float64), None

@@ -59,22 +59,16 @@ struct AdjLayout {
 template <class R, int M, int ST>
 __global__ void __launch_bounds__(kThr, sizeof(R) == 8 ? 1 : (ST == AD_SRC ? (M <= 3 ? 3 : 2) : ST == AD_LEAP ? 6 : 5)) adjoint_kernel(Adj<R, M> a) {
   const int n = a.nx * a.nr;
+  const int total = ST == AD_SRC ? n : M * n;
   double acc = 0;
-  if (ST == AD_SRC) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-      const int w = q / a.nr, j = q - w * a.nr;
-      adj_point<R, M>(a, ST, 0, w, j, acc);
-    }
-    if (a.dg) {
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(a.dg, acc);
-    }
-  } else {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < M * n; q += gridDim.x * blockDim.x) {
-      const int k = q / n, p = q - k * n;
-      const int w = p / a.nr, j = p - w * a.nr;
-      adj_point<R, M>(a, ST, k, w, j, acc);
-    }
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+    const int k = ST == AD_SRC ? 0 : q / n, p = q - k * n;
+    const int w = p / a.nr, j = p - w * a.nr;
+    adj_point<R, M>(a, ST, k, w, j, acc);
+  }
+  if (ST == AD_SRC && a.dg) {
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(a.dg, acc);
   }
 }
 
@@ -115,7 +109,8 @@ cudaError_t launch_all(Adj<R, M> a, int blocks, cudaStream_t st) {
 // the handle's row stride and the window's offset at that step).
 template <class R, int M>
 Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_inst, const C<R> *F,
-                   const C<R> *LN, C<R> *LO, C<R> *SB, double *dg, bool zero_regen, int ld = 0, int s = 0) {
+                   const C<R> *LN, C<R> *LO, C<R> *SB, double *dg, bool zero_regen, int ld = 0, int s = 0,
+                   const C<R> *Fnext = nullptr) {
   Adj<R, M> a;
   std::memset(&a, 0, sizeof a);
   const int nx = p.nx, nr = p.nr;
@@ -129,6 +124,7 @@ Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_
   t.h = (R)p.dx; t.dr = (R)p.dr; t.ih = (R)(1.0 / p.dx); t.idr = (R)(1.0 / p.dr);
   t.scr = nullptr;
   t.cw = -(1 << 28);  // each point sets the column cache (adjoint_kernel)
+  a.fnext = Fnext;
   a.ln = LN; a.lo = LO; a.sb = SB; a.dg = dg;
   a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = (unsigned)P;
   a.mw = (p.flags & QDS_MOVING_WINDOW) != 0;
@@ -210,8 +206,9 @@ size_t work_w_bytes(const qds_params &p, size_t elem) {
 }
 
 template <class R>
-int adjoint_w(const qds_params &p, int ld, const qds_sources *src, const void *fwd, unsigned long long step,
-              const void *lam_in, void *lam_out, void *work, size_t work_bytes, double *dg, cudaStream_t st) {
+int adjoint_w(const qds_params &p, int ld, const qds_sources *src, const void *fwd, const void *fwd_next,
+              unsigned long long step, const void *lam_in, void *lam_out, void *work, size_t work_bytes, double *dg,
+              cudaStream_t st) {
   if (work_bytes < work_w_bytes(p, sizeof(C<R>))) return fail_ad(QDS_ERR_INVALID_ARG, "adjoint work buffer too small");
   if (reinterpret_cast<uintptr_t>(work) % 256) return fail_ad(QDS_ERR_INVALID_ARG, "adjoint work buffer must be 256-byte aligned");
   if (lam_in == lam_out) return fail_ad(QDS_ERR_INVALID_ARG, "lam_in and lam_out must be distinct buffers");
@@ -233,15 +230,16 @@ int adjoint_w(const qds_params &p, int ld, const qds_sources *src, const void *f
   C<R> *SB = reinterpret_cast<C<R> *>(b + up256(sizeof(Inst<double>)));
   const Inst<R> *d_inst = reinterpret_cast<const Inst<R> *>(b);
   const C<R> *F = static_cast<const C<R> *>(fwd);
+  const C<R> *FN = static_cast<const C<R> *>(fwd_next);
   const C<R> *LN = static_cast<const C<R> *>(lam_in);
   C<R> *LO = static_cast<C<R> *>(lam_out);
   const int s = (p.flags & QDS_MOVING_WINDOW) ? (int)(step % (unsigned long long)nx) : 0;
   const int blocks = (int)((size_t(nx) * nr + kThr - 1) / kThr);
   switch (M) {
-    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
-    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
-    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
-    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s), blocks, st); break;
+    case 1: e = launch_all<R, 1>(make_adj<R, 1>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s, FN), blocks, st); break;
+    case 2: e = launch_all<R, 2>(make_adj<R, 2>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s, FN), blocks, st); break;
+    case 3: e = launch_all<R, 3>(make_adj<R, 3>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s, FN), blocks, st); break;
+    case 4: e = launch_all<R, 4>(make_adj<R, 4>(p, I, d_inst, F, LN, LO, SB, dg, false, ld, s, FN), blocks, st); break;
     default: e = cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint launch: ") + cudaGetErrorString(e));
@@ -257,8 +255,9 @@ extern "C" size_t qds_adjoint_work_bytes_w(const qds_handle *h, int i) {
 }
 
 extern "C" int qds_adjoint_step_w(qds_handle *h, int i, const qds_sources *src, const void *fwd_working_dev,
-                                  unsigned long long fwd_step, const void *lam_in_dev, void *lam_out_dev,
-                                  void *work_dev, size_t work_bytes, double *dLdg_dev, void *stream) {
+                                  const void *fwd_next_dev, unsigned long long fwd_step, const void *lam_in_dev,
+                                  void *lam_out_dev, void *work_dev, size_t work_bytes, double *dLdg_dev,
+                                  void *stream) {
   qds_params p;
   int rc = qds_internal_params(h, i, &p);
   if (rc) return rc;
@@ -271,10 +270,10 @@ extern "C" int qds_adjoint_step_w(qds_handle *h, int i, const qds_sources *src, 
   if (!(p.flags & QDS_AXION)) return fail_ad(QDS_ERR_UNSUPPORTED, "the adjoint step needs QDS_AXION");
   cudaStream_t st = (cudaStream_t)stream;
   if (p.flags & QDS_FP32)
-    return adjoint_w<float>(p, ld, src, fwd_working_dev, fwd_step, lam_in_dev, lam_out_dev, work_dev, work_bytes,
-                            dLdg_dev, st);
-  return adjoint_w<double>(p, ld, src, fwd_working_dev, fwd_step, lam_in_dev, lam_out_dev, work_dev, work_bytes,
-                           dLdg_dev, st);
+    return adjoint_w<float>(p, ld, src, fwd_working_dev, fwd_next_dev, fwd_step, lam_in_dev, lam_out_dev, work_dev,
+                            work_bytes, dLdg_dev, st);
+  return adjoint_w<double>(p, ld, src, fwd_working_dev, fwd_next_dev, fwd_step, lam_in_dev, lam_out_dev, work_dev,
+                           work_bytes, dLdg_dev, st);
 }
 
 extern "C" size_t qds_adjoint_work_bytes(const qds_handle *h, int i) {

@@ -42,6 +42,7 @@ enum AdScr { SB_G = 0, SB_EXB, SB_BXB, SB_RPB, SB_RMB, SB_QPB, SB_QMB, SB_EXT, S
 template <class R, int M>
 struct Adj {
   Tile<R, M, false> f;  // forward state at time n
+  const C<R> *fnext;    // forward state at the end of the step, same layout (null: recompute E_x, B_x^(n+1/2))
   const C<R> *ln;       // adjoint of the state after the step (canonical layout)
   C<R> *lo;             // adjoint of the state before the step (canonical layout)
   C<R> *sb;             // scratch planes (N_SB)
@@ -53,35 +54,59 @@ struct Adj {
   R h, dr, ih, idr;
   R gs, ma2;
 
-  // 32-bit element offsets: one instance's state has fewer than 2^32 elements
-  QDS_HD unsigned ai(int field, int k, int w, int j) const {
-    return (unsigned)field * P + (unsigned)k * (unsigned)(nx * nr) + (unsigned)(w * nr + j);
-  }
+  // Rows passed to the accessors below are inside the box (callers guard
+  // the radial neighbours); columns are checked.
+  // the radial neighbours, held inside the box (used under guards that
+  // exclude the axis and the last row: the clamp only keeps a hoisted load
+  // inside the buffer)
+  QDS_HD int up(int j) const { return j < J ? j + 1 : J; }
+  QDS_HD int dn(int j) const { return j > 0 ? j - 1 : 0; }
+  // 32-bit signed element offsets (one instance's state has fewer than 2^31
+  // elements).  A load that the compiler hoists above its guard must still
+  // address the buffer: the guarded accessors clamp their indices, and a
+  // signed offset keeps any other stray index next to the buffer.
+  QDS_HD int ai(int field, int k, int w, int j) const { return field * (int)P + k * (nx * nr) + w * nr + j; }
   QDS_HD bool in_cell(int w) const { return w >= 0 && w < nx; }
   QDS_HD bool in_face(int w) const { return w >= 0 && w <= nx - 2; }
   // adjoint of the new state in the fixed box (before the window shift)
   QDS_HD C<R> lnew(int field, int k, int w, int j) const {
     if (mw) w -= 1;
-    if (w < 0 || w >= nx || j < 0 || j >= nr) return zero<R>();
-    return ldg(ln + ai(field, k, w, j));
+    const bool ok = w >= 0 && w < nx;
+    const int wc = ok ? w : 0;
+    chk(field, NFIELD, k, wc, j, "adjoint read of the new state's adjoint");
+    const C<R> v = ldg(ln + ai(field, k, wc, j));
+    return ok ? v : zero<R>();
   }
   QDS_HD C<R> lnew_prev(int k, int w) const {
     if (mw) w -= 1;
-    if (w < 0 || w >= nx) return zero<R>();
-    return ldg(ln + ((unsigned)NFIELD * P + (unsigned)(k * nx + w)));
+    const bool ok = w >= 0 && w < nx;
+    const int wc = ok ? w : 0;
+    chk(0, 1, k, wc, 0, "adjoint phi_prev read");
+    const C<R> v = ldg(ln + ((int)NFIELD * (int)P + k * nx + wc));
+    return ok ? v : zero<R>();
   }
-  QDS_HD C<R> &old(int field, int k, int w, int j) const { return lo[ai(field, k, w, j)]; }
-  QDS_HD C<R> &oldprev(int k, int w) const { return lo[(unsigned)NFIELD * P + (unsigned)(k * nx + w)]; }
-  QDS_HD C<R> &s(int plane, int k, int w, int j) const { return sb[ai(plane, k, w, j)]; }
+#if defined(QDS_EMU)
+  QDS_HD void chk(int field, int nf, int k, int w, int j, const char *what) const {
+    QDS_CHECK(field >= 0 && field < nf && k >= 0 && k < M && w >= 0 && w < nx && j >= 0 && j < nr, what);
+  }
+#else
+  QDS_HD void chk(int, int, int, int, int, const char *) const {}
+#endif
+  QDS_HD C<R> &old(int field, int k, int w, int j) const { chk(field, NFIELD, k, w, j, "adjoint store"); return lo[ai(field, k, w, j)]; }
+  QDS_HD C<R> &oldprev(int k, int w) const { chk(0, 1, k, w, 0, "adjoint phi_prev store"); return lo[(int)NFIELD * (int)P + k * nx + w]; }
+  QDS_HD C<R> &s(int plane, int k, int w, int j) const { chk(plane, N_SB, k, w, j, "adjoint scratch"); return sb[ai(plane, k, w, j)]; }
   // reads of scratch planes that the running pass does not write
-  QDS_HD C<R> sr(int plane, int k, int w, int j) const { return ldg(sb + ai(plane, k, w, j)); }
+  QDS_HD C<R> sr(int plane, int k, int w, int j) const { chk(plane, N_SB, k, w, j, "adjoint scratch read"); return ldg(sb + ai(plane, k, w, j)); }
   // scratch on a face, zero off the faces and rows of the box
   QDS_HD C<R> sf(int plane, int k, int w, int j) const {
-    if (!in_face(w) || j < 0 || j >= nr) return zero<R>();
-    return sr(plane, k, w, j);
+    const bool ok = in_face(w) && j >= 0 && j < nr;
+    const C<R> v = sr(plane, k, ok ? w : 0, ok ? j : 0);
+    return ok ? v : zero<R>();
   }
   // adjoint of the new T (q = 0..3: T_r^+, T_r^-, T_th^+, T_th^-) at cell c
-  QDS_HD C<R> tn(int q, int k, int c, int j) const { return in_cell(c) ? lnew(TRP + q, k, c, j) : zero<R>(); }
+  QDS_HD C<R> tn(int q, int k, int c, int j) const {
+    return in_cell(c) ? lnew(TRP + q, k, c, j) : zero<R>();
+  }
   // adjoints of the new T_a^+- at cell c, with the phi update's share
   // (phi^(n+1) at the faces on either side takes (h/4) T_a^(n+1/2) of c)
   QDS_HD C<R> phi_share(int k, int c, int j) const {
@@ -89,8 +114,12 @@ struct Adj {
     C<R> pr = in_face(c) ? lnew(PHI, k, c, j) : zero<R>();
     return (R(0.25) * h) * (pl + pr);
   }
-  QDS_HD C<R> tap_n(int k, int c, int j) const { return in_cell(c) ? lnew(TAP, k, c, j) + phi_share(k, c, j) : zero<R>(); }
-  QDS_HD C<R> tam_n(int k, int c, int j) const { return in_cell(c) ? lnew(TAM, k, c, j) + phi_share(k, c, j) : zero<R>(); }
+  QDS_HD C<R> tap_n(int k, int c, int j) const {
+    return in_cell(c) ? lnew(TAP, k, c, j) + phi_share(k, c, j) : zero<R>();
+  }
+  QDS_HD C<R> tam_n(int k, int c, int j) const {
+    return in_cell(c) ? lnew(TAM, k, c, j) + phi_share(k, c, j) : zero<R>();
+  }
   // box-scheme weights of the outer half row (Eqs. em_r_open_bx/bt)
   QDS_HD R ka() const { return R(0.5) * ih; }
   QDS_HD R kb() const { return R(0.5) * idr; }
@@ -206,11 +235,12 @@ template <class R, int M>
 struct AdjFwd {
   using Real = R;
   const C<R> *c0, *c1;  // columns f and f + 1 of field 0, mode 0
+  const C<R> *n0;       // column f of the state at the end of the step (null: none)
   const C<R> *jx, *jt, *sext;
   unsigned P, kst;      // field and mode strides of the working planes
   int f, nx, nr, J;
   R h, dr, ih, idr;
-  QDS_HD AdjFwd(const Tile<R, M, false> &t, int f_) {
+  QDS_HD AdjFwd(const Tile<R, M, false> &t, const C<R> *next, bool mw, int f_) {
     f = f_; nx = t.nx; nr = t.nr; J = t.J;
     h = t.h; dr = t.dr; ih = t.ih; idr = t.idr;
     jx = t.jx; jt = t.jt; sext = t.sext;
@@ -221,6 +251,10 @@ struct AdjFwd {
     if (s1 >= nx) s1 -= nx;
     c0 = t.o + (unsigned)(s0 * t.ld);
     c1 = t.o + (unsigned)(s1 * t.ld);
+    // the window shift moves no data (ring offset): face f of the step's
+    // fixed box is the same ring slot in the next state, except the rear
+    // column, which the shift clears for the new front column
+    n0 = (next && !(mw && f == 0)) ? next + (unsigned)(s0 * t.ld) : nullptr;
 #if defined(QDS_EMU)
     o = t.o;
     len = t.state_len;
@@ -231,13 +265,21 @@ struct AdjFwd {
   size_t len;
 #endif
   QDS_HD C<R> cell(int field, int k, int w, int j) const {
-    const C<R> *p = (w == f ? c0 : c1) + ((unsigned)field * P + (unsigned)k * kst + (unsigned)j);
+    // rows outside the box are never read (the leapfrog helpers guard
+    // them); the clamp only keeps a hoisted load inside the buffer
+    const int jc = j < 0 ? 0 : (j > J ? J : j);
+    const C<R> *p = (w == f ? c0 : c1) + ((int)field * (int)P + k * (int)kst + jc);
 #if defined(QDS_EMU)
     QDS_CHECK((w == f || w == f + 1) && j >= 0 && j < nr && (size_t)(p - o) < len, "adjoint forward read");
 #endif
     return ldg(p);
   }
   QDS_HD C<R> face(int field, int k, int w, int j) const { return cell(field, k, w, j); }
+  // E_x, B_x^(n+1/2) at face f as the step stored them
+  QDS_HD C<R> next_face(int field, int k, int j) const {
+    const int jc = j > J ? J : j;
+    return ldg(n0 + ((int)field * (int)P + k * (int)kst + jc));
+  }
   QDS_HD C<R> Er(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TRP, k, w, j) + cell(grp + TRM, k, w, j)); }
   QDS_HD C<R> Bt(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TRP, k, w, j) - cell(grp + TRM, k, w, j)); }
   QDS_HD C<R> Et(int grp, int k, int w, int j) const { return R(0.5) * (cell(grp + TTP, k, w, j) + cell(grp + TTM, k, w, j)); }
@@ -245,7 +287,8 @@ struct AdjFwd {
   // caller's sources [M][nx][nr] in window order
   QDS_HD C<R> srcv(const C<R> *a, int k, int w, int j) const {
     if (!a) return zero<R>();
-    return ldg(a + ((unsigned)(k * nx + w) * (unsigned)nr + (unsigned)j));
+    const int jc = j < 0 ? 0 : (j > J ? J : j);
+    return ldg(a + ((k * nx + w) * nr + jc));
   }
 };
 
@@ -259,7 +302,7 @@ QDS_HD void adj_src(const Adj<R, M> &a, int f, int j, double &dg_acc) {
   const int J = a.J;
   const bool top = (j == J);
   const R h = a.h;
-  const AdjFwd<R, M> t(a.f, f);
+  const AdjFwd<R, M> t(a.f, a.fnext, a.mw, f);
   C<R> Gb[M], Sb[M];
   #pragma unroll
   for (int k = 0; k < M; k++) {
@@ -271,11 +314,18 @@ QDS_HD void adj_src(const Adj<R, M> &a, int f, int j, double &dg_acc) {
   C<R> eX[M], bX[M], rp[M], rm[M], qp[M], qm[M];
   #pragma unroll
   for (int k = 0; k < M; k++) {
-    const C<R> exn = ex_update(t, 0, k, f, j, t.srcv(t.jx, k, f, j));
-    const C<R> bxn = (j < J) ? bx_interior(t, 0, k, f, j)
-                             : bx_outer(t, 0, k, f, R(0.5) * (t.srcv(t.jt, k, f, j) + t.srcv(t.jt, k, f + 1, j)),
-                                        bx_interior(t, 0, k, f, j - 1));
-    const C<R> exn1 = top ? exn : ex_update(t, 0, k, f, j + 1, t.srcv(t.jx, k, f, j + 1));
+    C<R> exn, bxn, exn1;
+    if (t.n0) {  // the leapfrog's results, as the step stored them
+      exn = t.next_face(EX, k, j);
+      bxn = t.next_face(BX, k, j);
+      exn1 = top ? exn : t.next_face(EX, k, j + 1);
+    } else {     // recomputed (Eqs. Ex_update, Phix_explicit, em_r_open_bx)
+      exn = ex_update(t, 0, k, f, j, t.srcv(t.jx, k, f, j));
+      bxn = (j < J) ? bx_interior(t, 0, k, f, j)
+                    : bx_outer(t, 0, k, f, R(0.5) * (t.srcv(t.jt, k, f, j) + t.srcv(t.jt, k, f + 1, j)),
+                               bx_interior(t, 0, k, f, j - 1));
+      exn1 = top ? exn : ex_update(t, 0, k, f, j + 1, t.srcv(t.jx, k, f, j + 1));
+    }
     const C<R> eo = t.face(EX, k, f, j), eo1 = top ? eo : t.face(EX, k, f, j + 1);
     eX[k] = R(0.25) * (eo + eo1 + exn + exn1);
     bX[k] = R(0.5) * (t.face(BX, k, f, j) + bxn);
@@ -437,12 +487,12 @@ QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
       }
       if (j + 1 <= J) {
         const R rj = R(j + 1) * dr;
-        Bt((R(-0.5) * h * (R(j) + R(0.5)) / rj) * a.sr(SB_EXT, k, f, j + 1));
+        Bt((R(-0.5) * h * (R(j) + R(0.5)) / rj) * a.sr(SB_EXT, k, f, a.up(j)));
       }
       // B_x leapfrog (Eq. Phix_explicit) on rows j - 1, j; the box of row J
       if (j >= 1) {
         const R rh = (R(j) - R(0.5)) * dr;
-        Et((R(-0.5) * h * R(j) / rh) * a.sr(SB_BXT, k, f, j - 1));
+        Et((R(-0.5) * h * R(j) / rh) * a.sr(SB_BXT, k, f, a.dn(j)));
       }
       if (j < J) {
         const C<R> bb = a.sr(SB_BXT, k, f, j);
@@ -480,14 +530,14 @@ QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
       ph += cc * a.sr(SB_G, k, c, j);
       if (j >= 1) {
         const int i = j - 1;
-        ph += (R(i + 1) / ((R(i) + R(0.5)) * dr * dr)) * a.sr(SB_G, k, c, i);
+        ph += (R(i + 1) / ((R(i) + R(0.5)) * dr * dr)) * a.sr(SB_G, k, c, a.dn(j));
       }
       if (j + 1 <= J) {
         const int i = j + 1;
         const R di = R(1) / ((R(i) + R(0.5)) * dr * dr);
         R w = R(i) * di;
         if (i == J) w += R(J + 1) * di;
-        ph += w * a.sr(SB_G, k, c, i);
+        ph += w * a.sr(SB_G, k, c, a.up(j));
       }
     }
     o.ph = ph;

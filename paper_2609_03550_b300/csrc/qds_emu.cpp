@@ -363,6 +363,7 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   t.scr = nullptr;
   t.cw = -(1 << 28);  // set per column below
   t.state_len = E;
+  a.fnext = nullptr;  // E_x, B_x^(n+1/2) recomputed
   a.ln = LN.data(); a.lo = LO.data(); a.sb = SB.data(); a.dg = dg;
   a.nx = nx; a.nr = nr; a.J = nr - 1; a.P = (unsigned)P;
   a.mw = (flags & F_MOVING_WINDOW) != 0;

@@ -81,7 +81,7 @@ def lib():
             "qds_advance_noalloc": (i, [P, vp, vp, vp, sz, i, vp]),
             "qds_adjoint_work_bytes": (sz, [H, i]),
             "qds_adjoint_work_bytes_w": (sz, [H, i]),
-            "qds_adjoint_step_w": (i, [H, i, ctypes.POINTER(_Sources), vp, ctypes.c_ulonglong, vp, vp, vp, sz, vp,
+            "qds_adjoint_step_w": (i, [H, i, ctypes.POINTER(_Sources), vp, vp, ctypes.c_ulonglong, vp, vp, vp, sz, vp,
                                        vp]),
             "qds_working_bytes": (sz, [H, i]),
             "qds_steps_taken": (ctypes.c_ulonglong, [H]),
@@ -295,10 +295,11 @@ class QDSSolver:
                                          _stream_ptr(stream)))
 
     def adjoint_step_w(self, fwd_snap, fwd_step: int, lam_in, lam_out, i: int = 0, jx=None, jth=None, s_ext=None,
-                       dLdg=None, stream=None):
+                       dLdg=None, fwd_next=None, stream=None):
         """One transposed step without conversions (qds_adjoint_step_w):
         ``fwd_snap`` a working snapshot at the start of the step taken
-        ``fwd_step`` steps after the import; ``lam_in`` / ``lam_out`` the
+        ``fwd_step`` steps after the import (``fwd_next``, optional: the one
+        at its end, whose E_x, B_x spare their recomputation); ``lam_in`` / ``lam_out`` the
         adjoint after / before the step, canonical layout in the working
         precision (complex64 in FP32), distinct tensors; the regenerated
         planes of ``lam_out`` are left as they are."""
@@ -322,8 +323,9 @@ class QDSSolver:
             work = self._adj_work_w = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         wptr = work.data_ptr() + (-work.data_ptr()) % 256
         src = _Sources(ptr(jx), None, ptr(jth), ptr(s_ext))
-        self._adj_keep_w = (fwd_snap, lam_in, lam_out, jx, jth, s_ext, dLdg)
-        _check(lib().qds_adjoint_step_w(self.h, i, ctypes.byref(src), ctypes.c_void_p(fwd_snap.data_ptr()),
+        self._adj_keep_w = (fwd_snap, fwd_next, lam_in, lam_out, jx, jth, s_ext, dLdg)
+        nxt = None if fwd_next is None else ctypes.c_void_p(fwd_next.data_ptr())
+        _check(lib().qds_adjoint_step_w(self.h, i, ctypes.byref(src), ctypes.c_void_p(fwd_snap.data_ptr()), nxt,
                                         int(fwd_step), ctypes.c_void_p(lam_in.data_ptr()),
                                         ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(wptr), nbytes,
                                         None if dLdg is None else ctypes.c_void_p(dLdg.data_ptr()),

@@ -128,9 +128,9 @@ def test_adjoint_step_coupling_derivative(prec):
 def test_working_transpose_matches_canonical_transpose(M, mw, prec):
     """qds_adjoint_step_w on an EM-only working snapshot taken after a few
     steps (ring offset 5 in the moving window) gives what qds_adjoint_step
-    gives on the canonical state of the same moment, entry for entry; the
-    canonical path only converts, so the two differ only by the order of the
-    atomic additions of the scatters (a few units in the last place)."""
+    gives on the canonical state of the same moment, entry for entry (the
+    canonical path only converts), with and without the snapshot at the end
+    of the step (E_x, B_x^(n+1/2) read instead of recomputed)."""
     Q = _Q()
     nx, nr = 124, 41
     m_a, g = 0.05, 0.6
@@ -154,12 +154,20 @@ def test_working_transpose_matches_canonical_transpose(M, mw, prec):
     dg_w = torch.zeros(1, dtype=torch.float64, device=DEV)
     solver.adjoint_step(fwd, lam_c, jx=jx, jth=jt, dLdg=dg_c)
     solver.adjoint_step_w(snap, k, lam_w, out_w, jx=jx, jth=jt, dLdg=dg_w)
+    # the same with the snapshot at the end of the step, whose E_x, B_x^(n+1/2)
+    # replace their recomputation (the step's own rounding)
+    solver.step(1, jx=jx, jr=jr, jth=jt)
+    nxt, _ = solver.save_working(em_only=True)
+    out_n = torch.zeros_like(lam_w)
+    dg_n = torch.zeros(1, dtype=torch.float64, device=DEV)
+    solver.adjoint_step_w(snap, k, lam_w, out_n, jx=jx, jth=jt, dLdg=dg_n, fwd_next=nxt)
     torch.cuda.synchronize()
-    a, b = out_w.to(torch.complex128).cpu().numpy(), lam_c.cpu().numpy()
-    eps = 1e-14 if prec == 0 else 1e-6
-    bad = np.argwhere(np.abs(a - b) > eps * np.abs(b).max()).ravel()
-    assert bad.size == 0, (bad[:10], a[bad[:5]], b[bad[:5]])
-    assert abs(float(dg_w.item()) - float(dg_c.item())) <= eps * abs(float(dg_c.item()))
+    b = lam_c.cpu().numpy()
+    for out, dg, eps in ((out_w, dg_w, 1e-14 if prec == 0 else 1e-6), (out_n, dg_n, 1e-12 if prec == 0 else 1e-5)):
+        a = out.to(torch.complex128).cpu().numpy()
+        bad = np.argwhere(np.abs(a - b) > eps * np.abs(b).max()).ravel()
+        assert bad.size == 0, (eps, bad[:10], a[bad[:5]], b[bad[:5]])
+        assert abs(float(dg.item()) - float(dg_c.item())) <= eps * abs(float(dg_c.item()))
 
 
 def test_adjoint_rejects_unsupported_boundaries():
