@@ -38,6 +38,13 @@ BYTES_PER_UNIT = {"f32": 2 * WORDS * 8, "f64": 2 * WORDS * 16}
 from paper_2609_03550_b300.ranks import env_rank  # noqa: E402
 
 
+# The transposed step's algorithmic bytes per cell-mode (FP32): it reads the
+# forward EM fields (6 complex words), the adjoint after the step (EM and
+# axion, 9), the currents j_x, j_theta (2), and writes the adjoint before the
+# step (9): 26 complex words of 8 bytes.
+ADJ_BYTES_PER_UNIT = 26 * 8
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -270,6 +277,41 @@ def adjoint_bench(device, steps, every):
     fwd, bwd = ev[0].elapsed_time(ev[1]) / 1e3, ev[1].elapsed_time(ev[2]) / 1e3
     Lv, gg = float(L.detach()), float(g.grad)
     units = wl.cell_modes() * steps
+    # the transposed step alone (qds_adjoint_step_w with the snapshots at the
+    # start and the end of the step), as the backward pass runs it
+    s = Q.QDSSolver(p, device=device)
+    s.set_state(base)
+    jx, jr, jt = src(0)
+    s.step(3, jx=jx, jr=jr, jth=jt)
+    snap, k0 = s.save_working(em_only=True)
+    s.step(1, jx=jx, jr=jr, jth=jt)
+    nxt, _ = s.save_working(em_only=True)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(5)
+    plane = wl.M * wl.nx * wl.nr
+    lam = torch.randn(p.state_elems(), dtype=torch.complex64, device=device, generator=gen)
+    lam[9 * plane:15 * plane] = 0
+    lam_b = torch.zeros_like(lam)
+    dg = torch.zeros(1, dtype=torch.float64, device=device)
+    bufs = [lam, lam_b]
+    for i in range(3):
+        s.adjoint_step_w(snap, k0, bufs[i % 2], bufs[(i + 1) % 2], jx=jx, jth=jt, dLdg=dg, fwd_next=nxt)
+    reps = 20
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(reps):
+        s.adjoint_step_w(snap, k0, bufs[i % 2], bufs[(i + 1) % 2], jx=jx, jth=jt, dLdg=dg, fwd_next=nxt)
+    e1.record()
+    torch.cuda.synchronize()
+    t_adj = e0.elapsed_time(e1) / reps / 1e3
+    peak, peak_kind = measured_peak()
+    achieved = wl.cell_modes() * ADJ_BYTES_PER_UNIT / t_adj / 1e9
+    transposed = {"ms": t_adj * 1e3, "launches": 3, "cell_modes": wl.cell_modes(),
+                  "bytes_per_cell_mode": ADJ_BYTES_PER_UNIT,
+                  "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                               "frac": achieved / peak, "peak_kind": peak_kind},
+                  "timing": f"mean of {reps} calls after 3, CUDA events; inputs larger than L2"}
     return {"workload": wl.name, "steps": steps, "checkpoint_every": spec.interval(), "dtype": "f32",
             "params": "laser-2 radial profile (%d complex), omega2, g" % wl.nr,
             "loss": "axion energy in window cells [%d, %d)" % ex["window"], "L": Lv,
@@ -277,6 +319,7 @@ def adjoint_bench(device, steps, every):
             "value": units / (fwd + bwd), "unit": "cell-mode updates/s (forward + gradient)",
             "dLdg_vs_2L_over_g": abs(gg - 2 * Lv / wl.g) / abs(gg),
             "grad_finite": bool(torch.isfinite(prof.grad).all()) and math.isfinite(float(om.grad)) and math.isfinite(gg),
+            "transposed_step": transposed,
             "checks": "gradients vs oracle central differences and oracle Jacobian columns: tests/test_gpu_adjoint.py"}
 
 

@@ -12,17 +12,17 @@
 // through a Tile (its row stride and ring offset).  Every entry of the old
 // adjoint is written once by the thread that owns it (a gather: no atomic
 // scatters), in three passes over the (x, r) points:
-//   AD_SRC   faces: Gamma_a's adjoint from the new T_a and phi (Eqs.
-//            Ta_plus_update, Ta_minus_update, phi_update), d L / d g, and the
-//            transpose of the bilinear source S_a (Eq. mode_convolution) at
-//            the forward state, kept per face;
+//   AD_SRC   faces: the old T_a and Gamma_a's adjoint from the new T_a and
+//            phi (Eqs. Ta_plus_update, Ta_minus_update, phi_update), d L / d g,
+//            and the transpose of the bilinear source S_a (Eq.
+//            mode_convolution) at the forward state, kept per face;
 //   AD_LEAP  faces: the total adjoints of E_x, B_x^(n+1/2) (new state, the T
-//            shift's face sources, the source means) and the old E_x, B_x
-//            (Eqs. Ex_update, axis_Ex, Phix_explicit, em_r_open_bx);
+//            shift's face sources, the source means), the old E_x, B_x (Eqs.
+//            Ex_update, axis_Ex, Phix_explicit, em_r_open_bx), phi and
+//            phi_prev (Gamma_a's Laplacian and mass with the outer ghost);
 //   AD_CELL  cells: the old T (shifted copies, Eqs. Trp/Trm/Ttp/Ttm_update,
 //            axis_Ttheta; the outer boxes, Eq. em_r_open_bt; the leapfrog
-//            and source-mean terms of the two neighbouring faces), T_a, phi
-//            (Gamma_a's Laplacian and mass with the outer ghost) and phi_prev.
+//            and source-mean terms of the two neighbouring faces).
 // The transpose of the +x shift is the -x shift and vice versa; the window
 // shift reads the new state's adjoint one column over.  Open x, open r,
 // optional moving window; no periodic or closed test modes.
@@ -298,7 +298,16 @@ struct AdjFwd {
 // the adjoints of its six face means, kept per face for the next stages.
 template <class R, int M>
 QDS_HD void adj_src(const Adj<R, M> &a, int f, int j, double &dg_acc) {
-  if (!a.in_face(f)) return;
+  if (!a.in_face(f)) {
+    // the ends of the T_a shifts: T_a^+ of the last cell and T_a^- of the
+    // first feed no new T_a
+    #pragma unroll
+    for (int k = 0; k < M; k++) {
+      a.old(TAP, k, f, j) = zero<R>();
+      a.old(TAM, k, 0, j) = zero<R>();
+    }
+    return;
+  }
   const int J = a.J;
   const bool top = (j == J);
   const R h = a.h;
@@ -306,7 +315,12 @@ QDS_HD void adj_src(const Adj<R, M> &a, int f, int j, double &dg_acc) {
   C<R> Gb[M], Sb[M];
   #pragma unroll
   for (int k = 0; k < M; k++) {
-    Gb[k] = h * (a.tap_n(k, f + 1, j) + a.tam_n(k, f, j));
+    // T_a^+(c + 1) = T_a^+(c) + h Gamma_a(c + 1/2), T_a^-(c) = T_a^-(c + 1) + h
+    // Gamma_a(c + 1/2): face f gives the old T_a^+ of cell f and T_a^- of f + 1
+    const C<R> tp = a.tap_n(k, f + 1, j), tm = a.tam_n(k, f, j);
+    a.old(TAP, k, f, j) = tp;
+    a.old(TAM, k, f + 1, j) = tm;
+    Gb[k] = h * (tp + tm);
     Sb[k] = a.gs * Gb[k];
     a.s(SB_G, k, f, j) = Gb[k];
   }
@@ -369,15 +383,48 @@ template <class R>
 struct LeapOut {
   C<R> ex, bx;    // the old E_x, B_x adjoints
   C<R> ext, bxt;  // the total E_x, B_x^(n+1/2) adjoints (faces only)
+  C<R> ph, prev;  // the old phi and (last row) phi_prev adjoints
 };
 
 template <class R, int M>
 QDS_HD LeapOut<R> leap_vals(const Adj<R, M> &a, int k, int f, int j) {
   const int J = a.J;
   LeapOut<R> o;
-  o.ex = o.bx = o.ext = o.bxt = zero<R>();
+  o.ex = o.bx = o.ext = o.bxt = o.ph = o.prev = zero<R>();
   if (!a.in_face(f)) return o;
   const R kab = a.kab();
+  {
+    const int c = f;
+    const R dr = a.dr, ih = a.ih;
+    // ---- phi: carried over by the phi update, Gamma_a's Laplacian and mass
+    // with the outer ghost (-(2 dr/h) phi(J) + phi(J-1)), phi_prev (phi off
+    // the faces, in the last column, has no adjoint: the zeros above) ----
+    C<R> ph = a.lnew(PHI, k, c, j);
+    {
+      if (j == J) ph += a.lnew_prev(k, c);
+      const R rh = (R(j) + R(0.5)) * dr;
+      const R den = R(1) / ((R(j) + R(0.5)) * dr * dr);
+      R cc = -(R(2 * j + 1)) * den - (R(k * k) / (rh * rh) + a.ma2);
+      if (j == J) cc += R(J + 1) * den * (-R(2) * dr * ih);
+      ph += cc * a.sr(SB_G, k, c, j);
+      if (j >= 1) {
+        const int i = j - 1;
+        ph += (R(i + 1) / ((R(i) + R(0.5)) * dr * dr)) * a.sr(SB_G, k, c, a.dn(j));
+      }
+      if (j + 1 <= J) {
+        const int i = j + 1;
+        const R di = R(1) / ((R(i) + R(0.5)) * dr * dr);
+        R w = R(i) * di;
+        if (i == J) w += R(J + 1) * di;
+        ph += w * a.sr(SB_G, k, c, a.up(j));
+      }
+    }
+    o.ph = ph;
+    if (j == J) {
+      const R den = R(1) / ((R(J) + R(0.5)) * dr * dr);
+      o.prev = (R(J + 1) * den * R(2) * dr * ih) * a.sr(SB_G, k, c, J);
+    }
+  }
   {
     // eX(f, jj) is the mean of E_x at rows jj and jj + 1 (jj on the last row)
     // of the old and the new E_x: row j takes eX of rows j and j - 1
@@ -412,6 +459,8 @@ template <class R, int M>
 QDS_HD void leap_store(const Adj<R, M> &a, int k, int f, int j, const LeapOut<R> &o) {
   a.old(EX, k, f, j) = o.ex;
   a.old(BX, k, f, j) = o.bx;
+  a.old(PHI, k, f, j) = o.ph;
+  if (j == a.J) a.oldprev(k, f) = o.prev;
   if (a.in_face(f)) {
     a.s(SB_EXT, k, f, j) = o.ext;
     a.s(SB_BXT, k, f, j) = o.bxt;
@@ -424,7 +473,6 @@ QDS_HD void leap_store(const Adj<R, M> &a, int k, int f, int j, const LeapOut<R>
 template <class R>
 struct CellOut {
   C<R> t[4];      // the old T_r^+, T_r^-, T_th^+, T_th^-
-  C<R> tap, tam, ph, prev;
 };
 
 template <class R, int M>
@@ -515,37 +563,6 @@ QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
     o.t[1] = trm;
     o.t[2] = ttp;
     o.t[3] = ttm;
-    // ---- T_a: the shifted copies of the new T_a adjoints ----
-    o.tap = a.tap_n(k, c + 1, j);
-    o.tam = a.tam_n(k, c - 1, j);
-    // ---- phi: carried over by the phi update, Gamma_a's Laplacian and mass
-    // with the outer ghost (-(2 dr/h) phi(J) + phi(J-1)), phi_prev ----
-    C<R> ph = a.in_face(c) ? a.lnew(PHI, k, c, j) : zero<R>();
-    if (a.in_face(c)) {
-      if (j == J) ph += a.lnew_prev(k, c);
-      const R rh = (R(j) + R(0.5)) * dr;
-      const R den = R(1) / ((R(j) + R(0.5)) * dr * dr);
-      R cc = -(R(2 * j + 1)) * den - (R(k * k) / (rh * rh) + a.ma2);
-      if (j == J) cc += R(J + 1) * den * (-R(2) * dr * ih);
-      ph += cc * a.sr(SB_G, k, c, j);
-      if (j >= 1) {
-        const int i = j - 1;
-        ph += (R(i + 1) / ((R(i) + R(0.5)) * dr * dr)) * a.sr(SB_G, k, c, a.dn(j));
-      }
-      if (j + 1 <= J) {
-        const int i = j + 1;
-        const R di = R(1) / ((R(i) + R(0.5)) * dr * dr);
-        R w = R(i) * di;
-        if (i == J) w += R(J + 1) * di;
-        ph += w * a.sr(SB_G, k, c, a.up(j));
-      }
-    }
-    o.ph = ph;
-    o.prev = zero<R>();
-    if (j == J && a.in_face(c)) {
-      const R den = R(1) / ((R(J) + R(0.5)) * dr * dr);
-      o.prev = (R(J + 1) * den * R(2) * dr * ih) * a.sr(SB_G, k, c, J);
-    }
   }
   return o;
 }
@@ -554,10 +571,6 @@ template <class R, int M>
 QDS_HD void cell_store(const Adj<R, M> &a, int k, int c, int j, const CellOut<R> &o) {
 #pragma unroll
   for (int q = 0; q < 4; q++) a.old(TRP + q, k, c, j) = o.t[q];
-  a.old(TAP, k, c, j) = o.tap;
-  a.old(TAM, k, c, j) = o.tam;
-  a.old(PHI, k, c, j) = o.ph;
-  if (j == a.J) a.oldprev(k, c) = o.prev;
   if (a.zero_regen)
     for (int fl = TRP1; fl < NFIELD; fl++) a.old(fl, k, c, j) = zero<R>();
 }
