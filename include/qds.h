@@ -241,6 +241,24 @@ int qds_mode_products(int n_modes, int npts, int npairs, const void *a_dev, cons
 int qds_mode_products_theta_points(int n_modes);
 
 /* ---------------------------------------------------------------------------
+ * Synthetic per-step currents of the driven workloads (input generation, not
+ * part of the scheme), for the `count` steps step .. step + count - 1:
+ * j_x, j_r, j_theta [count][n_modes][nx][nr] (interleaved complex, FP32 or
+ * FP64 per fp32) receive uniform noise in [-amp, amp) on the real and
+ * imaginary parts of every mode and cell (m = 0 real), and j_x of m = 0 also
+ * the bunch bunch_dev [nx][nr] (FP64, may be NULL).  The noise of element e
+ * (components, then modes, x and r) of step n is SplitMix64 (Steele, Lea and
+ * Flood, OOPSLA 2014) of a key made from seed and n, plus 2e (real) and
+ * 2e + 1 (imaginary); with u its top 24 bits the value is the FP32 number
+ * (float)amp * (u 2^-23 - 1), the same in FP32 and FP64 runs; the bunch is
+ * added in FP64 and the sum rounded once.  Any step redraws alone with the
+ * same values.  Asynchronous on stream; returns
+ * QDS_ERR_INVALID_ARG for bad sizes or NULL outputs. */
+int qds_bunch_currents(int n_modes, int nx, int nr, unsigned long long seed, unsigned long long step, int count,
+                       double amp, const double *bunch_dev, void *jx_dev, void *jr_dev, void *jth_dev, int fp32,
+                       void *stream);
+
+/* ---------------------------------------------------------------------------
  * Adjoint (transpose) of one step of the EM group and the axion (Sec. 2;
  * the transpose of the +x transport shift is the -x shift).  For a real
  * functional L of the state the adjoint of a complex value z is

@@ -86,8 +86,9 @@ def _advance(solver, spec, n0, count):
 class _Run(torch.autograd.Function):
     """Forward: checkpoints are working snapshots (the state as the kernels
     hold it, qds_save_working).  Backward: per segment, the checkpoint is
-    restored, the segment re-run keeping the EM planes of the state before
-    every step (all the transposed step reads), and the transposed steps
+    restored into a handle that advances the EM group alone, the segment
+    re-run keeping the EM planes of the state before every step (all the
+    transposed step reads), and the transposed steps
     (qds_adjoint_step_w) run in reverse on the adjoint held in the working
     precision, two buffers in turn: no conversion to complex128 between
     steps."""
@@ -127,9 +128,16 @@ class _Run(torch.autograd.Function):
         em_bytes = solver.working_bytes(0, em_only=True)
         pool = [torch.empty(em_bytes, dtype=torch.uint8, device=lam.device) for _ in range(K + 1)]
         fill = spec.sources is not None and hasattr(spec.sources, "fill")
+        # The re-runs advance the EM group alone: it is driven by the currents
+        # only (S_a and j_a never feed back into it, Sec. 2.2), and the
+        # transposed step reads no other forward field.  A handle without the
+        # axion and the regenerated group has the same working layout.
+        rp = _params_with_g(p, p.g)
+        rp.flags = p.flags & ~(Q.AXION | Q.AREM)
+        em = Q.QDSSolver(rp, device=spec.device)
         for n0, ck in reversed(ckpts):
             cnt = min(K, spec.nsteps - n0)
-            solver.restore_working(ck, n0)
+            em.restore_working(ck, n0)
             # the segment's currents, drawn once for the re-run and the transpose
             if spec.sources is None:
                 blk = [(None, None, None)] * cnt
@@ -139,10 +147,10 @@ class _Run(torch.autograd.Function):
             else:
                 blk = None
             for k in range(cnt):
-                solver.save_working(out=pool[k], em_only=True)
+                em.save_working(out=pool[k], em_only=True)
                 jx, jr, jt = blk[k] if blk is not None else spec.sources(n0 + k)
-                solver.step(1, jx=jx, jr=jr, jth=jt)
-            solver.save_working(out=pool[cnt], em_only=True)  # the segment's end: E_x, B_x of its last step
+                em.step(1, jx=jx, jr=jr, jth=jt)
+            em.save_working(out=pool[cnt], em_only=True)  # the segment's end: E_x, B_x of its last step
             for k in range(cnt - 1, -1, -1):
                 jx, _, jt = blk[k] if blk is not None else spec.sources(n0 + k)
                 solver.adjoint_step_w(pool[k], n0 + k, lam, lam_b, jx=jx, jth=jt, dLdg=dg, fwd_next=pool[k + 1])

@@ -9,7 +9,7 @@ LIB = os.path.join(HERE, "libqds.so")
 EMU = os.path.join(HERE, "libqds_emu.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qds_api.cu", "qds_noalloc.cu", "qds_adjoint.cu", "qds_modes.cu"]
+SOURCES = ["qds_api.cu", "qds_noalloc.cu", "qds_adjoint.cu", "qds_modes.cu", "qds_inputs.cu"]
 HEADERS = ["qds_common.cuh", "qds_stages.cuh", "qds_kernels.cuh", "qds_march.cuh", "qds_adjoint.cuh"]
 
 

@@ -288,9 +288,11 @@ class DeviceBunchSources:
     three fixed buffers (so a solver sees the same source pointers every
     step): the m = 0 bunch j_x, stationary in a window that moves at c, plus
     uniform noise of amplitude noise * |rho| on every component, mode and
-    cell (imaginary part zero for m = 0), from torch's device generator
-    seeded by (seed, step).  Calling it with the same step reproduces the
-    same values."""
+    cell (imaginary part zero for m = 0).  The noise is counter-based
+    (qds_bunch_currents: SplitMix64 keyed by (seed, step)) and FP32-exact, the
+    bunch added in FP64 and rounded once, so an FP32 run sees the FP64 run's
+    values rounded, and calling it with the same step reproduces the same
+    values."""
 
     def __init__(self, wl, device, dtype):
         import torch
@@ -301,25 +303,17 @@ class DeviceBunchSources:
         self.dtype, self.device = dtype, device
         x = (torch.arange(wl.nx, dtype=torch.float64, device=device) + 0.5)[:, None]
         r = (torch.arange(wl.nr, dtype=torch.float64, device=device) * wl.dr)[None, :]
-        self.bunch = (b["rho"] * torch.exp(-((x - b["x0"]) ** 2) / (2 * b["sx"] ** 2))
-                      * torch.exp(-(r ** 2) / (2 * b["sr"] ** 2)))[None].expand(wl.M, -1, -1)
+        self.bunch_re = (b["rho"] * torch.exp(-((x - b["x0"]) ** 2) / (2 * b["sx"] ** 2))
+                         * torch.exp(-(r ** 2) / (2 * b["sr"] ** 2))).contiguous()
         self.buf = [torch.zeros((wl.M, wl.nx, wl.nr), dtype=dtype, device=device) for _ in range(3)]
-        self.gen = torch.Generator(device=device)
-        # drawn in float64 whatever the working precision, so that an FP32
-        # run sees the FP64 run's values rounded
-        self.noise = torch.empty((3, 2, wl.M, wl.nx, wl.nr), dtype=torch.float64, device=device)
-        self.bunch64 = self.bunch.to(torch.complex128)
 
     def _draw(self, step, out):
-        torch = self.torch
-        self.gen.manual_seed(self.seed * 1_000_003 + int(step))
-        self.noise.uniform_(-1.0, 1.0, generator=self.gen)
-        self.noise[:, 1, 0] = 0.0
-        for c in range(3):
-            z = torch.complex(self.amp * self.noise[c, 0], self.amp * self.noise[c, 1])
-            if c == 0:
-                z[0] += self.bunch64[0]
-            out[c].copy_(z)
+        """The currents of step ``step`` into ``out`` ([M, nx, nr] each), or
+        of the steps step .. step + count - 1 ([count, M, nx, nr] each), in
+        one launch."""
+        from . import qds as Q
+        Q.bunch_currents(self.seed, int(step), self.amp, self.bunch_re, *out,
+                         stream=self.torch.cuda.current_stream(self.device))
 
     def __call__(self, step):
         self._draw(step, self.buf)
@@ -335,6 +329,6 @@ class DeviceBunchSources:
             assert out is None
             blk = self._blk = [torch.empty((count, self.M, self.nx, self.nr), dtype=self.dtype, device=self.device)
                                for _ in range(3)]
-        for k in range(count):
-            self._draw(n0 + k, [b[k] for b in blk])
-        return tuple(b[:count] for b in blk)
+        views = [b[:count] for b in blk]
+        self._draw(n0, views)
+        return tuple(views)

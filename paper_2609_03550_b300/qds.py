@@ -66,6 +66,8 @@ def lib():
             "qds_set_inflow_i": (i, [H, i, vp, vp, ctypes.c_longlong, vp]),
             "qds_mode_products": (i, [i, i, i, vp, vp, ctypes.POINTER(ctypes.c_double), vp, i, i, vp]),
             "qds_mode_products_theta_points": (i, [i]),
+            "qds_bunch_currents": (i, [i, i, i, ctypes.c_ulonglong, ctypes.c_ulonglong, i, ctypes.c_double, vp, vp,
+                                       vp, vp, i, vp]),
             "qds_diagnostics": (i, [H, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_diagnostics_i": (i, [H, i, ctypes.POINTER(ctypes.c_double), vp, vp]),
             "qds_num_instances": (i, [H]),
@@ -422,6 +424,25 @@ class QDSSolver:
 
 
 MODES_DIRECT, MODES_THETA = 0, 1
+
+
+def bunch_currents(seed: int, step: int, amp: float, bunch, jx, jr, jth, stream=None):
+    """Synthetic currents (qds_bunch_currents) written into the device
+    tensors jx, jr, jth: [M, nx, nr] for step ``step``, or [count, M, nx, nr]
+    for the steps step .. step + count - 1 (complex64 or complex128): uniform
+    noise of amplitude amp, m = 0 real, plus the float64 bunch [nx, nr] (or
+    None) on j_x of m = 0."""
+    M, nx, nr = jx.shape[-3:]
+    count = jx.shape[0] if jx.dim() == 4 else 1
+    fp32 = jx.dtype == torch.complex64
+    for t in (jx, jr, jth):
+        assert t.is_cuda and t.is_contiguous() and t.dtype == jx.dtype and t.shape == jx.shape
+    if bunch is not None:
+        assert bunch.is_cuda and bunch.dtype == torch.float64 and bunch.is_contiguous() and bunch.numel() == nx * nr
+    _check(lib().qds_bunch_currents(int(M), int(nx), int(nr), int(seed), int(step), int(count), float(amp),
+                                    None if bunch is None else ctypes.c_void_p(bunch.data_ptr()),
+                                    ctypes.c_void_p(jx.data_ptr()), ctypes.c_void_p(jr.data_ptr()),
+                                    ctypes.c_void_p(jth.data_ptr()), int(fp32), _stream_ptr(stream)))
 
 
 def mode_products(A, B, w, method=MODES_DIRECT, out=None, stream=None):
