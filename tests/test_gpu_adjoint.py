@@ -170,6 +170,37 @@ def test_working_transpose_matches_canonical_transpose(M, mw, prec):
         assert abs(float(dg.item()) - float(dg_c.item())) <= eps * abs(float(dg_c.item()))
 
 
+@pytest.mark.parametrize("prec", [0, 32])
+def test_em_only_handle_reproduces_the_em_planes(prec):
+    """The backward re-runs segments on a handle without the axion and the
+    regenerated group: after driven steps from a restored working snapshot,
+    its EM fields equal the full step's bit for bit (the EM group does not
+    depend on the other groups)."""
+    import copy
+    Q = _Q()
+    M, nx, nr = 3, 150, 37
+    dr = stable_dr(M, 0.05)
+    rng = np.random.default_rng(900 + prec)
+    p = Q.Params(nx, nr, M, dr, m_a=0.05, g=0.7, flags=oracle.AXION | oracle.AREM | oracle.MOVING_WINDOW | prec)
+    pe = copy.copy(p)
+    pe.flags = p.flags & ~(oracle.AXION | oracle.AREM)
+    full, em = Q.QDSSolver(p, device=DEV), Q.QDSSolver(pe, device=DEV)
+    full.set_state(torch.from_numpy(I.random_state(rng, M, nx, nr)).to(DEV))
+    srcs = [tuple(torch.from_numpy(np.ascontiguousarray(a)).to(DEV).to(full.rdtype)
+                  for a in I.random_sources(rng, M, nx, nr, 0.3)) for _ in range(4)]
+    full.step(2, jx=srcs[0][0], jr=srcs[0][1], jth=srcs[0][2])
+    ck, n0 = full.save_working()
+    em.restore_working(ck, n0)
+    for jx, jr, jt in srcs[1:]:
+        full.step(1, jx=jx, jr=jr, jth=jt)
+        em.step(1, jx=jx, jr=jr, jth=jt)
+    assert full.steps_taken() == em.steps_taken() == 5
+    # the EM planes of the canonical state (the working layout pads FP32 rows)
+    n6 = 6 * M * nx * nr
+    a, b = full.get_state()[:n6], em.get_state()[:n6]
+    assert torch.equal(a, b)
+
+
 def test_adjoint_rejects_unsupported_boundaries():
     Q = _Q()
     p = Q.Params(16, 8, 2, 2.0, g=0.5, flags=oracle.AXION | oracle.X_PERIODIC)
