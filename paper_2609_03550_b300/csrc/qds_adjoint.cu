@@ -131,6 +131,7 @@ Adj<R, M> make_adj(const qds_params &p, const Inst<R> &h_inst, const Inst<R> *d_
   a.zero_regen = zero_regen;
   a.h = t.h; a.dr = t.dr; a.ih = t.ih; a.idr = t.idr;
   a.gs = (R)p.g; a.ma2 = (R)(p.m_a * p.m_a);
+  a.set_consts();
   return a;
 }
 

@@ -53,6 +53,13 @@ struct Adj {
   bool zero_regen;      // also write the (zero) regenerated planes of lo
   R h, dr, ih, idr;
   R gs, ma2;
+  R c_kab, c_ikab, c_irJ;  // (a - b)/(a + b), 1/(a + b) of the outer box, 1/r_J (set with set_consts)
+
+  QDS_HD void set_consts() {
+    c_kab = kab();
+    c_ikab = R(1) / (ka() + kb());
+    c_irJ = R(1) / (R(J) * dr);
+  }
 
   // Rows passed to the accessors below are inside the box (callers guard
   // the radial neighbours); columns are checked.
@@ -131,13 +138,13 @@ struct Adj {
   QDS_HD C<R> trp_e(int k, int c, int j) const {
     if (!in_cell(c)) return zero<R>();
     C<R> v = tn(0, k, c, j);
-    if (j == J - 1) v += (R(-0.5) * kab()) * box_bt(k, c);
+    if (j == J - 1) v += (R(-0.5) * c_kab) * box_bt(k, c);
     return v;
   }
   QDS_HD C<R> trm_e(int k, int c, int j) const {
     if (!in_cell(c)) return zero<R>();
     C<R> v = tn(1, k, c, j);
-    if (j == J - 1) v -= (R(-0.5) * kab()) * box_bt(k, c);
+    if (j == J - 1) v -= (R(-0.5) * c_kab) * box_bt(k, c);
     return v;
   }
   QDS_HD C<R> tt_e(int q, int k, int c, int j) const {
@@ -209,17 +216,17 @@ QDS_HD void unshift_face(const Adj<R, M> &a, int k, int f, int j, C<R> &ex, C<R>
   // E_x(f, j) enters Phi_r of half rows j and j-1 and Phi_th of row j
   if (j < J) { Sr(j, Gr, Pr); ex -= idr * Pr; }
   if (j >= 1) { Sr(j - 1, Gr, Pr); ex += idr * Pr; }
+  const R irh = R(1) / ((R(j) + R(0.5)) * dr);  // 1/r_(j+1/2)
   if (j >= 1) { St(j, Gt, Pt); ex += imul(-R(k) / (R(j) * dr), Pt); }
   if (k == 1 && j <= 1) {  // axis: Phi_th = i (E_x(1) - E_x(0)) / dr
     St(0, Gt, Pt);
     ex += imul(j == 1 ? -idr : idr, Pt);
   }
   // B_x(f, j) enters Gamma_r of half row j and Gamma_th of rows j, j+1
-  const R rh = (R(j) + R(0.5)) * dr;
-  if (j < J) { Sr(j, Gr, Pr); bx += imul(R(k) / rh, Gr); }
+  if (j < J) { Sr(j, Gr, Pr); bx += imul(R(k) * irh, Gr); }
   else {
     C<R> Gb = (R(0.5) * h) * (a.tn(0, k, f + 1, J) + a.tn(1, k, f + 1, J) + a.tn(0, k, f, J) + a.tn(1, k, f, J));
-    bx += imul(R(k) / rh, Gb);
+    bx += imul(R(k) * irh, Gb);
   }
   if (j >= 1) { St(j, Gt, Pt); bx -= idr * Gt; }
   else if (k == 1) { St(0, Gt, Pt); bx += (-R(2) * idr) * Gt; }
@@ -350,14 +357,16 @@ QDS_HD void adj_src(const Adj<R, M> &a, int f, int j, double &dg_acc) {
     qm[k] = R(0.25) * (t.cell(TTM, k, f, j) + t.cell(TTM, k, f + 1, j) + t.cell(TTM, k, f, j1) + t.cell(TTM, k, f + 1, j1));
   }
   if (a.dg) {  // Gamma_a depends on g through g S (physical variables)
-    double acc = 0;
+    // the point's share in the working precision (FP64 arithmetic is slow on
+    // this part), the sums over points in FP64
+    R acc = R(0);
     #pragma unroll
     for (int m = 0; m < M; m++) {
       C<R> S = conv<R, M>(m, eX, bX) + R(0.5) * (conv<R, M>(m, rp, qp) - conv<R, M>(m, rm, qm));
       S += t.srcv(t.sext, m, f, j);
-      acc += (double)Gb[m].re * S.re + (double)Gb[m].im * S.im;
+      acc += Gb[m].re * S.re + Gb[m].im * S.im;
     }
-    dg_acc += acc;  // the caller reduces and adds to *a.dg
+    dg_acc += (double)acc;  // the caller reduces and adds to *a.dg
   }
   C<R> eXb[M], bXb[M], rpb[M], rmb[M], qpb[M], qmb[M];
   #pragma unroll
@@ -392,7 +401,7 @@ QDS_HD LeapOut<R> leap_vals(const Adj<R, M> &a, int k, int f, int j) {
   LeapOut<R> o;
   o.ex = o.bx = o.ext = o.bxt = o.ph = o.prev = zero<R>();
   if (!a.in_face(f)) return o;
-  const R kab = a.kab();
+  const R kab = a.c_kab;
   {
     const int c = f;
     const R dr = a.dr, ih = a.ih;
@@ -402,27 +411,25 @@ QDS_HD LeapOut<R> leap_vals(const Adj<R, M> &a, int k, int f, int j) {
     C<R> ph = a.lnew(PHI, k, c, j);
     {
       if (j == J) ph += a.lnew_prev(k, c);
-      const R rh = (R(j) + R(0.5)) * dr;
-      const R den = R(1) / ((R(j) + R(0.5)) * dr * dr);
-      R cc = -(R(2 * j + 1)) * den - (R(k * k) / (rh * rh) + a.ma2);
+      // d_i = 1 / ((i + 1/2) dr^2) = idr / r_(i+1/2)
+      const R irh = R(1) / ((R(j) + R(0.5)) * dr);
+      const R den = irh * a.idr;
+      R cc = -(R(2 * j + 1)) * den - (R(k * k) * irh * irh + a.ma2);
       if (j == J) cc += R(J + 1) * den * (-R(2) * dr * ih);
       ph += cc * a.sr(SB_G, k, c, j);
       if (j >= 1) {
-        const int i = j - 1;
-        ph += (R(i + 1) / ((R(i) + R(0.5)) * dr * dr)) * a.sr(SB_G, k, c, a.dn(j));
+        const R di = a.idr / ((R(j) - R(0.5)) * dr);
+        ph += (R(j) * di) * a.sr(SB_G, k, c, a.dn(j));
       }
       if (j + 1 <= J) {
         const int i = j + 1;
-        const R di = R(1) / ((R(i) + R(0.5)) * dr * dr);
+        const R di = a.idr / ((R(i) + R(0.5)) * dr);
         R w = R(i) * di;
         if (i == J) w += R(J + 1) * di;
         ph += w * a.sr(SB_G, k, c, a.up(j));
       }
-    }
-    o.ph = ph;
-    if (j == J) {
-      const R den = R(1) / ((R(J) + R(0.5)) * dr * dr);
-      o.prev = (R(J + 1) * den * R(2) * dr * ih) * a.sr(SB_G, k, c, J);
+      o.ph = ph;
+      if (j == J) o.prev = (R(J + 1) * den * R(2) * dr * ih) * a.sr(SB_G, k, c, J);
     }
   }
   {
@@ -480,8 +487,12 @@ QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
   CellOut<R> o;
   const int J = a.J;
   const R h = a.h, dr = a.dr, idr = a.idr, ih = a.ih;
-  const R ka = a.ka(), kb = a.kb(), kab = a.kab();
-  const R rJ = R(J) * dr;
+  const R kab = a.c_kab, ikab = a.c_ikab, irJ = a.c_irJ;
+  // reciprocal radii of the rows this cell's faces reach (0 where unused)
+  const R ir_j = j >= 1 ? R(1) / (R(j) * dr) : R(0);                // 1/r_j
+  const R ir_j1 = R(1) / (R(j + 1) * dr);                           // 1/r_(j+1)
+  const R ir_hm = j >= 1 ? R(1) / ((R(j) - R(0.5)) * dr) : R(0);    // 1/r_(j-1/2)
+  const R ir_h = R(1) / ((R(j) + R(0.5)) * dr);                     // 1/r_(j+1/2)
   {
     C<R> trp = zero<R>(), trm = zero<R>(), ttp = zero<R>(), ttm = zero<R>();
     // the transverse fields map to T^+- as E_r, B_th -> T_r and E_th, B_r -> T_th
@@ -504,14 +515,14 @@ QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
       // B_th^(n+1) = (R - (a-b) B_th^(n+1)(J-1) + (a-b) B_th(J) + (a+b) B_th(J-1)) / (a+b),
       // R = -(1/4) ih (E_r(c+1) - E_r(c-1)) - (1/(2 rJ)) (B_th + i m B_r) + ...
       const C<R> Bb = a.box_bt(k, c);
-      const C<R> Rb = (R(1) / (ka + kb)) * Bb;
-      const C<R> er_m = (R(-0.125) * ih) * ((R(1) / (ka + kb)) * a.box_bt(k, c - 1));  // from cell c - 1
-      const C<R> er_p = (R(-0.125) * ih) * ((R(1) / (ka + kb)) * a.box_bt(k, c + 1));  // from cell c + 1
+      const C<R> Rb = ikab * Bb;
+      const C<R> er_m = (R(-0.125) * ih) * (ikab * a.box_bt(k, c - 1));  // from cell c - 1
+      const C<R> er_p = (R(-0.125) * ih) * (ikab * a.box_bt(k, c + 1));  // from cell c + 1
       if (j == J) {
-        Bt(kab * Bb + (R(-0.25) / rJ) * Rb);
-        Br(imul(R(k) * R(0.5) / rJ, Rb));
+        Bt(kab * Bb + (R(-0.25) * irJ) * Rb);
+        Br(imul(R(k) * R(0.5) * irJ, Rb));
       } else {
-        Bt(Bb + (R(-0.25) / rJ) * Rb);
+        Bt(Bb + (R(-0.25) * irJ) * Rb);
       }
       Er(er_m - er_p);
     }
@@ -529,34 +540,30 @@ QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
       if (j == 0 && k == 0) Bt((h * R(2) * idr) * a.sr(SB_EXT, k, f, 0));
       if (j >= 1) {
         const C<R> eb = a.sr(SB_EXT, k, f, j);
-        const R rj = R(j) * dr;
-        Bt((R(0.5) * h * (R(j) + R(0.5)) / rj) * eb);
-        Br(imul(R(-0.5) * h * R(k) / rj, eb));
+        Bt((R(0.5) * h * (R(j) + R(0.5)) * ir_j) * eb);
+        Br(imul(R(-0.5) * h * R(k) * ir_j, eb));
       }
       if (j + 1 <= J) {
-        const R rj = R(j + 1) * dr;
-        Bt((R(-0.5) * h * (R(j) + R(0.5)) / rj) * a.sr(SB_EXT, k, f, a.up(j)));
+        Bt((R(-0.5) * h * (R(j) + R(0.5)) * ir_j1) * a.sr(SB_EXT, k, f, a.up(j)));
       }
       // B_x leapfrog (Eq. Phix_explicit) on rows j - 1, j; the box of row J
       if (j >= 1) {
-        const R rh = (R(j) - R(0.5)) * dr;
-        Et((R(-0.5) * h * R(j) / rh) * a.sr(SB_BXT, k, f, a.dn(j)));
+        Et((R(-0.5) * h * R(j) * ir_hm) * a.sr(SB_BXT, k, f, a.dn(j)));
       }
       if (j < J) {
         const C<R> bb = a.sr(SB_BXT, k, f, j);
-        const R rh = (R(j) + R(0.5)) * dr;
-        Et((R(0.5) * h * R(j) / rh) * bb);
-        Er(imul(R(0.5) * h * R(k) / rh, bb));
+        Et((R(0.5) * h * R(j) * ir_h) * bb);
+        Er(imul(R(0.5) * h * R(k) * ir_h, bb));
       }
       if (j >= J - 1) {
         // B_x(J) = (R - (a-b) B_x^(n+1/2)(J-1) + (a-b) B_x(J) + (a+b) B_x(J-1)) / (a+b),
         // R = (1/2) ih (B_r(f+1, J) - B_r(f, J)) - (1/(2 rJ)) (E_th + i m E_r) - ...
-        const C<R> Rb = (R(1) / (ka + kb)) * a.sr(SB_BXT, k, f, J);
+        const C<R> Rb = ikab * a.sr(SB_BXT, k, f, J);
         if (j == J) {
           Br((df == 0 ? R(0.5) : R(-0.5)) * ih * Rb);  // face c - 1 reads B_r(c) with +, face c with -
-          Et((R(-0.25) / rJ) * Rb);
+          Et((R(-0.25) * irJ) * Rb);
         }
-        Er(imul(R(k) * R(0.125) / rJ, Rb));
+        Er(imul(R(k) * R(0.125) * irJ, Rb));
       }
     }
     o.t[0] = trp;

@@ -370,6 +370,7 @@ void emu_adjoint(const double *fwd, const double *lam_new, double *lam_old, int 
   a.zero_regen = true;
   a.h = I.h; a.dr = I.dr; a.ih = I.inv_h; a.idr = I.inv_dr;
   a.gs = I.gs; a.ma2 = I.ma2;
+  a.set_consts();
   double acc = 0;
   for (int st = 0; st < N_ADSTAGE; st++)
     for (int k = 0; k < (st == AD_SRC ? 1 : M); k++)
