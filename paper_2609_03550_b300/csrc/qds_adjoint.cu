@@ -33,7 +33,7 @@ int fail_ad(int code, const std::string &m) {
 constexpr int kThr = 256;
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-// work layout: [Inst<R>] [N_SB scratch planes] [lambda^(n+1) copy]
+// work layout: [a descriptor-sized slot, unused] [N_SB scratch planes] [lambda^(n+1) copy]
 //              FP32 only: [forward state] [lambda^n]
 template <class R>
 struct AdjLayout {
@@ -155,8 +155,8 @@ int adjoint(const qds_params &p, const qds_sources *src, const void *fwd, void *
     I.jt = (const C<R> *)src->jth;
     I.sext = (const C<R> *)src->s_ext;
   }
-  cudaError_t e = cudaMemcpyAsync(b, &I, sizeof I, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint descriptor: ") + cudaGetErrorString(e));
+  // the passes take the descriptor's values by argument: no device copy
+  cudaError_t e = cudaSuccess;
   C<R> *SB = reinterpret_cast<C<R> *>(b + L.off_scr);
   C<R> *LN = reinterpret_cast<C<R> *>(b + L.off_ln);
   const C<R> *F;
@@ -226,8 +226,8 @@ int adjoint_w(const qds_params &p, int ld, const qds_sources *src, const void *f
     I.jt = (const C<R> *)src->jth;
     I.sext = (const C<R> *)src->s_ext;
   }
-  cudaError_t e = cudaMemcpyAsync(b, &I, sizeof I, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail_ad(QDS_ERR_CUDA, std::string("adjoint descriptor: ") + cudaGetErrorString(e));
+  // the passes take the descriptor's values by argument: no device copy
+  cudaError_t e = cudaSuccess;
   C<R> *SB = reinterpret_cast<C<R> *>(b + up256(sizeof(Inst<double>)));
   const Inst<R> *d_inst = reinterpret_cast<const Inst<R> *>(b);
   const C<R> *F = static_cast<const C<R> *>(fwd);
