@@ -193,44 +193,129 @@ QDS_HD void conv_T(const C<R> *A, const C<R> *B, const C<R> *Sb, R wgt, C<R> *Ab
 }
 
 // ---------------------------------------------------------------------------
+// Per-thread views for one mode: the columns a point reads, resolved once
+// (window shift, column checks, clamped base), so that each read is an
+// offset from a base and a select.  Rows passed are inside the box.
+//
+// The new state's adjoint at the cells c + dc, dc = -1, 0, +1.
+template <class R, int M>
+struct NewCols {
+  const C<R> *p[3];
+  bool ok[3];
+  int P;
+#if defined(QDS_EMU)
+  const Adj<R, M> *ad;
+  int k, c;
+#endif
+  QDS_HD NewCols(const Adj<R, M> &a, int k_, int c_) {
+    P = (int)a.P;
+    const int shift = a.mw ? 1 : 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const int w = c_ + d - 1, ws = w - shift;
+      ok[d] = a.in_cell(w) && ws >= 0 && ws < a.nx;
+      p[d] = a.ln + (k_ * (a.nx * a.nr) + (ok[d] ? ws : 0) * a.nr);
+    }
+#if defined(QDS_EMU)
+    ad = &a;
+    k = k_;
+    c = c_;
+#endif
+  }
+  QDS_HD C<R> at(int field, int dc, int row) const {
+#if defined(QDS_EMU)
+    ad->chk(field, NFIELD, k, 0, row, "adjoint read of the new state's adjoint (column view)");
+#endif
+    const C<R> v = ldg(p[dc + 1] + (field * P + row));
+    return ok[dc + 1] ? v : zero<R>();
+  }
+};
+
+// The scratch planes at the faces c - 1 (df = 0) and c (df = 1).
+template <class R, int M>
+struct ScrFaces {
+  const C<R> *p[2];
+  bool ok[2];
+  int P;
+#if defined(QDS_EMU)
+  const Adj<R, M> *ad;
+  int k;
+#endif
+  QDS_HD ScrFaces(const Adj<R, M> &a, int k_, int c) {
+    P = (int)a.P;
+#pragma unroll
+    for (int d = 0; d < 2; d++) {
+      const int f = c - 1 + d;
+      ok[d] = a.in_face(f);
+      p[d] = a.sb + (k_ * (a.nx * a.nr) + (ok[d] ? f : 0) * a.nr);
+    }
+#if defined(QDS_EMU)
+    ad = &a;
+    k = k_;
+#endif
+  }
+  QDS_HD C<R> at(int plane, int df, int row) const {
+#if defined(QDS_EMU)
+    ad->chk(plane, N_SB, k, 0, row, "adjoint scratch read (face view)");
+#endif
+    const C<R> v = ldg(p[df] + (plane * P + row));
+    return ok[df] ? v : zero<R>();
+  }
+};
+
+// ---------------------------------------------------------------------------
 // The E_x and B_x^(n+1/2) adjoints that the T shift's face sources give at
 // face f, row j (Eqs. Trp/Trm/Ttp/Ttm_update; axis rules of Sec. 2.3; on the
 // last row, E_r^(n+1) takes Gamma_r of the faces on either side).
 template <class R, int M>
-QDS_HD void unshift_face(const Adj<R, M> &a, int k, int f, int j, C<R> &ex, C<R> &bx) {
+QDS_HD void unshift_face(const Adj<R, M> &a, const NewCols<R, M> &nc, int k, int j, C<R> &ex, C<R> &bx) {
   const int J = a.J;
-  const R h = a.h, dr = a.dr, idr = a.idr;
-  auto Sr = [&](int jj, C<R> &Gb, C<R> &Pb) {  // T_r sources (half row jj < J)
-    C<R> sp = h * a.trp_e(k, f + 1, jj), sm = h * a.trm_e(k, f, jj);
-    Gb = sp + sm;
-    Pb = sp - sm;
+  const R h = a.h, dr = a.dr, idr = a.idr, kf = R(-0.5) * a.c_kab;
+  const int jm = j > 0 ? j - 1 : 0, jp = j < J ? j + 1 : J;
+  // effective new T at cell f + dc (the box fold of T_r on half row J - 1,
+  // T_th on the axis only for m = 1)
+  auto boxbt = [&](int dc) { return nc.at(TRP, dc, J) - nc.at(TRM, dc, J); };
+  auto trp = [&](int dc, int jj) {
+    C<R> v = nc.at(TRP, dc, jj);
+    if (jj == J - 1) v += kf * boxbt(dc);
+    return v;
   };
-  auto St = [&](int jj, C<R> &Gb, C<R> &Pb) {  // T_th sources (row jj)
-    C<R> sp = h * a.tt_e(2, k, f, jj), sm = h * a.tt_e(3, k, f + 1, jj);
-    Gb = sp + sm;
-    Pb = sp - sm;
+  auto trm = [&](int dc, int jj) {
+    C<R> v = nc.at(TRM, dc, jj);
+    if (jj == J - 1) v -= kf * boxbt(dc);
+    return v;
   };
+  auto tt = [&](int q, int dc, int jj) { return (jj == 0 && k != 1) ? zero<R>() : nc.at(TRP + q, dc, jj); };
+  // T_r sources of half rows j and j - 1, T_th sources of rows j, j + 1, 0
+  const C<R> sp_j = h * trp(1, j), sm_j = h * trm(0, j);
+  const C<R> Gr = sp_j + sm_j, Pr = sp_j - sm_j;
+  const C<R> sp_m = h * trp(1, jm), sm_m = h * trm(0, jm);
+  const C<R> Pr_m = sp_m - sm_m;
+  const C<R> tp_j = h * tt(2, 0, j), tm_j = h * tt(3, 1, j);
+  const C<R> Gt = tp_j + tm_j, Pt = tp_j - tm_j;
+  const C<R> tp_p = h * tt(2, 0, jp), tm_p = h * tt(3, 1, jp);
+  const C<R> Gt_p = tp_p + tm_p;
+  const C<R> tp_0 = h * tt(2, 0, 0), tm_0 = h * tt(3, 1, 0);
+  const C<R> Gt_0 = tp_0 + tm_0, Pt_0 = tp_0 - tm_0;
   ex = zero<R>();
   bx = zero<R>();
-  C<R> Gr, Pr, Gt, Pt;
   // E_x(f, j) enters Phi_r of half rows j and j-1 and Phi_th of row j
-  if (j < J) { Sr(j, Gr, Pr); ex -= idr * Pr; }
-  if (j >= 1) { Sr(j - 1, Gr, Pr); ex += idr * Pr; }
-  const R irh = R(1) / ((R(j) + R(0.5)) * dr);  // 1/r_(j+1/2)
-  if (j >= 1) { St(j, Gt, Pt); ex += imul(-R(k) / (R(j) * dr), Pt); }
-  if (k == 1 && j <= 1) {  // axis: Phi_th = i (E_x(1) - E_x(0)) / dr
-    St(0, Gt, Pt);
-    ex += imul(j == 1 ? -idr : idr, Pt);
+  if (j < J) ex -= idr * Pr;
+  if (j >= 1) {
+    ex += idr * Pr_m;
+    ex += imul(-R(k) / (R(j) * dr), Pt);
   }
+  if (k == 1 && j <= 1) ex += imul(j == 1 ? -idr : idr, Pt_0);  // axis: Phi_th = i (E_x(1) - E_x(0)) / dr
   // B_x(f, j) enters Gamma_r of half row j and Gamma_th of rows j, j+1
-  if (j < J) { Sr(j, Gr, Pr); bx += imul(R(k) * irh, Gr); }
+  const R irh = R(1) / ((R(j) + R(0.5)) * dr);
+  if (j < J) bx += imul(R(k) * irh, Gr);
   else {
-    C<R> Gb = (R(0.5) * h) * (a.tn(0, k, f + 1, J) + a.tn(1, k, f + 1, J) + a.tn(0, k, f, J) + a.tn(1, k, f, J));
+    const C<R> Gb = (R(0.5) * h) * (nc.at(TRP, 1, J) + nc.at(TRM, 1, J) + nc.at(TRP, 0, J) + nc.at(TRM, 0, J));
     bx += imul(R(k) * irh, Gb);
   }
-  if (j >= 1) { St(j, Gt, Pt); bx -= idr * Gt; }
-  else if (k == 1) { St(0, Gt, Pt); bx += (-R(2) * idr) * Gt; }
-  if (j + 1 <= J) { St(j + 1, Gt, Pt); bx += idr * Gt; }
+  if (j >= 1) bx -= idr * Gt;
+  else if (k == 1) bx += (-R(2) * idr) * Gt_0;
+  if (j + 1 <= J) bx += idr * Gt_p;
 }
 
 // The forward state around face f as the source transpose reads it: the
@@ -401,64 +486,66 @@ QDS_HD LeapOut<R> leap_vals(const Adj<R, M> &a, int k, int f, int j) {
   LeapOut<R> o;
   o.ex = o.bx = o.ext = o.bxt = o.ph = o.prev = zero<R>();
   if (!a.in_face(f)) return o;
-  const R kab = a.c_kab;
+  const R kab = a.c_kab, dr = a.dr, ih = a.ih;
+  const int jm = j > 0 ? j - 1 : 0, jp = j < J ? j + 1 : J;
+  const NewCols<R, M> nf(a, k, f);  // dc = 0: cell f, +1: cell f + 1
+  const C<R> *sp = a.sb + (k * (a.nx * a.nr) + f * a.nr);
+  const int P = (int)a.P;
+  auto S = [&](int plane, int row) {
+#if defined(QDS_EMU)
+    a.chk(plane, N_SB, k, f, row, "adjoint scratch read (own face)");
+#endif
+    return ldg(sp + (plane * P + row));
+  };
+  // ---- phi: carried over by the phi update, Gamma_a's Laplacian and mass
+  // with the outer ghost (-(2 dr/h) phi(J) + phi(J-1)), phi_prev (phi off
+  // the faces, in the last column, has no adjoint: the zeros above) ----
   {
-    const int c = f;
-    const R dr = a.dr, ih = a.ih;
-    // ---- phi: carried over by the phi update, Gamma_a's Laplacian and mass
-    // with the outer ghost (-(2 dr/h) phi(J) + phi(J-1)), phi_prev (phi off
-    // the faces, in the last column, has no adjoint: the zeros above) ----
-    C<R> ph = a.lnew(PHI, k, c, j);
-    {
-      if (j == J) ph += a.lnew_prev(k, c);
-      // d_i = 1 / ((i + 1/2) dr^2) = idr / r_(i+1/2)
-      const R irh = R(1) / ((R(j) + R(0.5)) * dr);
-      const R den = irh * a.idr;
-      R cc = -(R(2 * j + 1)) * den - (R(k * k) * irh * irh + a.ma2);
-      if (j == J) cc += R(J + 1) * den * (-R(2) * dr * ih);
-      ph += cc * a.sr(SB_G, k, c, j);
-      if (j >= 1) {
-        const R di = a.idr / ((R(j) - R(0.5)) * dr);
-        ph += (R(j) * di) * a.sr(SB_G, k, c, a.dn(j));
-      }
-      if (j + 1 <= J) {
-        const int i = j + 1;
-        const R di = a.idr / ((R(i) + R(0.5)) * dr);
-        R w = R(i) * di;
-        if (i == J) w += R(J + 1) * di;
-        ph += w * a.sr(SB_G, k, c, a.up(j));
-      }
-      o.ph = ph;
-      if (j == J) o.prev = (R(J + 1) * den * R(2) * dr * ih) * a.sr(SB_G, k, c, J);
+    C<R> ph = nf.at(PHI, 0, j);
+    if (j == J) ph += a.lnew_prev(k, f);
+    // d_i = 1 / ((i + 1/2) dr^2) = idr / r_(i+1/2)
+    const R irh = R(1) / ((R(j) + R(0.5)) * dr);
+    const R den = irh * a.idr;
+    R cc = -(R(2 * j + 1)) * den - (R(k * k) * irh * irh + a.ma2);
+    if (j == J) cc += R(J + 1) * den * (-R(2) * dr * ih);
+    ph += cc * S(SB_G, j);
+    if (j >= 1) ph += (R(j) * (a.idr / ((R(j) - R(0.5)) * dr))) * S(SB_G, jm);
+    if (j + 1 <= J) {
+      const int i = j + 1;
+      const R di = a.idr / ((R(i) + R(0.5)) * dr);
+      R w = R(i) * di;
+      if (i == J) w += R(J + 1) * di;
+      ph += w * S(SB_G, jp);
     }
+    o.ph = ph;
+    if (j == J) o.prev = (R(J + 1) * den * R(2) * dr * ih) * S(SB_G, J);
   }
-  {
-    // eX(f, jj) is the mean of E_x at rows jj and jj + 1 (jj on the last row)
-    // of the old and the new E_x: row j takes eX of rows j and j - 1
-    const C<R> e4 = R(0.25) * ((j == J ? R(2) : R(1)) * a.sr(SB_EXB, k, f, j) + a.sf(SB_EXB, k, f, j - 1));
-    C<R> ex, bx;
-    unshift_face(a, k, f, j, ex, bx);
-    const C<R> ext = a.lnew(EX, k, f, j) + ex + e4;
-    C<R> bxt = a.lnew(BX, k, f, j) + bx + R(0.5) * a.sr(SB_BXB, k, f, j);
-    C<R> bxJ = zero<R>();  // the last row's, for the box of row J - 1
-    if (j == J - 1) {
-      C<R> exJ, bxJs;
-      unshift_face(a, k, f, J, exJ, bxJs);
-      bxJ = a.lnew(BX, k, f, J) + bxJs + R(0.5) * a.sr(SB_BXB, k, f, J);
-      bxt -= kab * bxJ;  // the box reads B_x^(n+1/2)(J - 1)
-    }
-    o.ext = ext;
-    o.bxt = bxt;
-    // E_x^(n+1/2) = E_x^(n-1/2) + h Gamma_x; on the axis only m = 0 moves
-    o.ex = ((j > 0 || k == 0) ? ext : zero<R>()) + e4;
-    // B_x: interior rows carry it over; the box of the last row weighs
-    // B_x(J) by (a - b)/(a + b) and B_x(J - 1) by 1
-    C<R> ob = R(0.5) * a.sr(SB_BXB, k, f, j);
-    if (j < J) ob += bxt;
-    else ob += kab * bxt;
-    if (j == J - 1) ob += bxJ;
-    o.bx = ob;
+  // eX(f, jj) is the mean of E_x at rows jj and jj + 1 (jj on the last row)
+  // of the old and the new E_x: row j takes eX of rows j and j - 1
+  const C<R> exb_m = j >= 1 ? S(SB_EXB, jm) : zero<R>();
+  const C<R> e4 = R(0.25) * ((j == J ? R(2) : R(1)) * S(SB_EXB, j) + exb_m);
+  C<R> ex, bx;
+  unshift_face(a, nf, k, j, ex, bx);
+  const C<R> ext = nf.at(EX, 0, j) + ex + e4;
+  C<R> bxt = nf.at(BX, 0, j) + bx + R(0.5) * S(SB_BXB, j);
+  C<R> bxJ = zero<R>();  // the last row's, for the box of row J - 1
+  if (j == J - 1) {
+    C<R> exJ, bxJs;
+    unshift_face(a, nf, k, J, exJ, bxJs);
+    bxJ = nf.at(BX, 0, J) + bxJs + R(0.5) * S(SB_BXB, J);
+    bxt -= kab * bxJ;  // the box reads B_x^(n+1/2)(J - 1)
   }
+  o.ext = ext;
+  o.bxt = bxt;
+  // E_x^(n+1/2) = E_x^(n-1/2) + h Gamma_x; on the axis only m = 0 moves
+  o.ex = ((j > 0 || k == 0) ? ext : zero<R>()) + e4;
+  // B_x: interior rows carry it over; the box of the last row weighs
+  // B_x(J) by (a - b)/(a + b) and B_x(J - 1) by 1
+  C<R> ob = R(0.5) * S(SB_BXB, j);
+  if (j < J) ob += bxt;
+  else ob += kab * bxt;
+  if (j == J - 1) ob += bxJ;
+  o.bx = ob;
   return o;
 }
 
@@ -487,90 +574,98 @@ QDS_HD CellOut<R> cell_vals(const Adj<R, M> &a, int k, int c, int j) {
   CellOut<R> o;
   const int J = a.J;
   const R h = a.h, dr = a.dr, idr = a.idr, ih = a.ih;
-  const R kab = a.c_kab, ikab = a.c_ikab, irJ = a.c_irJ;
+  const R kab = a.c_kab, ikab = a.c_ikab, irJ = a.c_irJ, kf = R(-0.5) * kab;
+  const int jm = j > 0 ? j - 1 : 0, jp = j < J ? j + 1 : J;
+  const NewCols<R, M> nc(a, k, c);  // cells c - 1, c, c + 1
+  const ScrFaces<R, M> sf(a, k, c);  // faces c - 1, c
   // reciprocal radii of the rows this cell's faces reach (0 where unused)
   const R ir_j = j >= 1 ? R(1) / (R(j) * dr) : R(0);                // 1/r_j
   const R ir_j1 = R(1) / (R(j + 1) * dr);                           // 1/r_(j+1)
   const R ir_hm = j >= 1 ? R(1) / ((R(j) - R(0.5)) * dr) : R(0);    // 1/r_(j-1/2)
   const R ir_h = R(1) / ((R(j) + R(0.5)) * dr);                     // 1/r_(j+1/2)
-  {
-    C<R> trp = zero<R>(), trm = zero<R>(), ttp = zero<R>(), ttm = zero<R>();
-    // the transverse fields map to T^+- as E_r, B_th -> T_r and E_th, B_r -> T_th
-    auto Er = [&](C<R> v) { trp += R(0.5) * v; trm += R(0.5) * v; };
-    auto Bt = [&](C<R> v) { trp += R(0.5) * v; trm -= R(0.5) * v; };
-    auto Et = [&](C<R> v) { ttp += R(0.5) * v; ttm += R(0.5) * v; };
-    auto Br = [&](C<R> v) { ttp += R(0.5) * v; ttm -= R(0.5) * v; };
-    // ---- the shifted copies (-x for T_r^+, T_th^-, +x for T_r^-, T_th^+) ----
-    if (j < J) {
-      trp += a.trp_e(k, c + 1, j);
-      trm += a.trm_e(k, c - 1, j);
-    } else {  // last half row: E_r^(n+1)(c') takes (T_r^+(c'-1) + T_r^-(c'+1))/2
-      if (a.in_cell(c + 1)) trp += R(0.5) * (a.tn(0, k, c + 1, J) + a.tn(1, k, c + 1, J));
-      if (a.in_cell(c - 1)) trm += R(0.5) * (a.tn(0, k, c - 1, J) + a.tn(1, k, c - 1, J));
+  auto boxbt = [&](int dc) { return nc.at(TRP, dc, J) - nc.at(TRM, dc, J); };
+  C<R> trp = zero<R>(), trm = zero<R>(), ttp = zero<R>(), ttm = zero<R>();
+  // the transverse fields map to T^+- as E_r, B_th -> T_r and E_th, B_r -> T_th
+  auto Er = [&](C<R> v) { trp += R(0.5) * v; trm += R(0.5) * v; };
+  auto Bt = [&](C<R> v) { trp += R(0.5) * v; trm -= R(0.5) * v; };
+  auto Et = [&](C<R> v) { ttp += R(0.5) * v; ttm += R(0.5) * v; };
+  auto Br = [&](C<R> v) { ttp += R(0.5) * v; ttm -= R(0.5) * v; };
+  // ---- the shifted copies (-x for T_r^+, T_th^-, +x for T_r^-, T_th^+) ----
+  if (j < J) {
+    trp += nc.at(TRP, 1, j);
+    trm += nc.at(TRM, -1, j);
+    if (j == J - 1) {  // the fold of the outer box into half row J - 1
+      trp += kf * boxbt(1);
+      trm -= kf * boxbt(-1);
     }
-    ttp += a.tt_e(2, k, c - 1, j);
-    ttm += a.tt_e(3, k, c + 1, j);
-    // ---- the outer T_r boxes of cells c - 1, c, c + 1 (Eq. em_r_open_bt) ----
-    if (j >= J - 1) {
-      // B_th^(n+1) = (R - (a-b) B_th^(n+1)(J-1) + (a-b) B_th(J) + (a+b) B_th(J-1)) / (a+b),
-      // R = -(1/4) ih (E_r(c+1) - E_r(c-1)) - (1/(2 rJ)) (B_th + i m B_r) + ...
-      const C<R> Bb = a.box_bt(k, c);
-      const C<R> Rb = ikab * Bb;
-      const C<R> er_m = (R(-0.125) * ih) * (ikab * a.box_bt(k, c - 1));  // from cell c - 1
-      const C<R> er_p = (R(-0.125) * ih) * (ikab * a.box_bt(k, c + 1));  // from cell c + 1
-      if (j == J) {
-        Bt(kab * Bb + (R(-0.25) * irJ) * Rb);
-        Br(imul(R(k) * R(0.5) * irJ, Rb));
-      } else {
-        Bt(Bb + (R(-0.25) * irJ) * Rb);
-      }
-      Er(er_m - er_p);
-    }
-    // ---- faces c - 1 and c ----
-    for (int df = 0; df < 2; df++) {
-      const int f = c - 1 + df;
-      if (!a.in_face(f)) continue;
-      // the source means: rp, rm on row j; qp, qm on rows j, j + 1 (j, j on the last)
-      trp += R(0.5) * a.sr(SB_RPB, k, f, j);
-      trm += R(0.5) * a.sr(SB_RMB, k, f, j);
-      const R tw = (j == J) ? R(2) : R(1);
-      ttp += R(0.25) * (tw * a.sr(SB_QPB, k, f, j) + a.sf(SB_QPB, k, f, j - 1));
-      ttm += R(0.25) * (tw * a.sr(SB_QMB, k, f, j) + a.sf(SB_QMB, k, f, j - 1));
-      // E_x leapfrog (Eq. Ex_update; axis_Ex for m = 0)
-      if (j == 0 && k == 0) Bt((h * R(2) * idr) * a.sr(SB_EXT, k, f, 0));
-      if (j >= 1) {
-        const C<R> eb = a.sr(SB_EXT, k, f, j);
-        Bt((R(0.5) * h * (R(j) + R(0.5)) * ir_j) * eb);
-        Br(imul(R(-0.5) * h * R(k) * ir_j, eb));
-      }
-      if (j + 1 <= J) {
-        Bt((R(-0.5) * h * (R(j) + R(0.5)) * ir_j1) * a.sr(SB_EXT, k, f, a.up(j)));
-      }
-      // B_x leapfrog (Eq. Phix_explicit) on rows j - 1, j; the box of row J
-      if (j >= 1) {
-        Et((R(-0.5) * h * R(j) * ir_hm) * a.sr(SB_BXT, k, f, a.dn(j)));
-      }
-      if (j < J) {
-        const C<R> bb = a.sr(SB_BXT, k, f, j);
-        Et((R(0.5) * h * R(j) * ir_h) * bb);
-        Er(imul(R(0.5) * h * R(k) * ir_h, bb));
-      }
-      if (j >= J - 1) {
-        // B_x(J) = (R - (a-b) B_x^(n+1/2)(J-1) + (a-b) B_x(J) + (a+b) B_x(J-1)) / (a+b),
-        // R = (1/2) ih (B_r(f+1, J) - B_r(f, J)) - (1/(2 rJ)) (E_th + i m E_r) - ...
-        const C<R> Rb = ikab * a.sr(SB_BXT, k, f, J);
-        if (j == J) {
-          Br((df == 0 ? R(0.5) : R(-0.5)) * ih * Rb);  // face c - 1 reads B_r(c) with +, face c with -
-          Et((R(-0.25) * irJ) * Rb);
-        }
-        Er(imul(R(k) * R(0.125) * irJ, Rb));
-      }
-    }
-    o.t[0] = trp;
-    o.t[1] = trm;
-    o.t[2] = ttp;
-    o.t[3] = ttm;
+  } else {  // last half row: E_r^(n+1)(c') takes (T_r^+(c'-1) + T_r^-(c'+1))/2
+    trp += R(0.5) * (nc.at(TRP, 1, J) + nc.at(TRM, 1, J));
+    trm += R(0.5) * (nc.at(TRP, -1, J) + nc.at(TRM, -1, J));
   }
+  if (j > 0 || k == 1) {  // T_th on the axis only for m = 1
+    ttp += nc.at(TTP, -1, j);
+    ttm += nc.at(TTM, 1, j);
+  }
+  // ---- the outer T_r boxes of cells c - 1, c, c + 1 (Eq. em_r_open_bt) ----
+  if (j >= J - 1) {
+    // B_th^(n+1) = (R - (a-b) B_th^(n+1)(J-1) + (a-b) B_th(J) + (a+b) B_th(J-1)) / (a+b),
+    // R = -(1/4) ih (E_r(c+1) - E_r(c-1)) - (1/(2 rJ)) (B_th + i m B_r) + ...
+    const C<R> Bb = boxbt(0);
+    const C<R> Rb = ikab * Bb;
+    const C<R> er_m = (R(-0.125) * ih) * (ikab * boxbt(-1));  // from cell c - 1
+    const C<R> er_p = (R(-0.125) * ih) * (ikab * boxbt(1));   // from cell c + 1
+    if (j == J) {
+      Bt(kab * Bb + (R(-0.25) * irJ) * Rb);
+      Br(imul(R(k) * R(0.5) * irJ, Rb));
+    } else {
+      Bt(Bb + (R(-0.25) * irJ) * Rb);
+    }
+    Er(er_m - er_p);
+  }
+  // ---- faces c - 1 and c (a face off the box reads as zero) ----
+  const R tw = (j == J) ? R(2) : R(1);
+#pragma unroll
+  for (int df = 0; df < 2; df++) {
+    // the source means: rp, rm on row j; qp, qm on rows j, j + 1 (j, j on the last)
+    trp += R(0.5) * sf.at(SB_RPB, df, j);
+    trm += R(0.5) * sf.at(SB_RMB, df, j);
+    C<R> qpm = tw * sf.at(SB_QPB, df, j), qmm = tw * sf.at(SB_QMB, df, j);
+    if (j >= 1) {
+      qpm += sf.at(SB_QPB, df, jm);
+      qmm += sf.at(SB_QMB, df, jm);
+    }
+    ttp += R(0.25) * qpm;
+    ttm += R(0.25) * qmm;
+    // E_x leapfrog (Eq. Ex_update; axis_Ex for m = 0)
+    if (j == 0 && k == 0) Bt((h * R(2) * idr) * sf.at(SB_EXT, df, 0));
+    if (j >= 1) {
+      const C<R> eb = sf.at(SB_EXT, df, j);
+      Bt((R(0.5) * h * (R(j) + R(0.5)) * ir_j) * eb);
+      Br(imul(R(-0.5) * h * R(k) * ir_j, eb));
+    }
+    if (j + 1 <= J) Bt((R(-0.5) * h * (R(j) + R(0.5)) * ir_j1) * sf.at(SB_EXT, df, jp));
+    // B_x leapfrog (Eq. Phix_explicit) on rows j - 1, j; the box of row J
+    if (j >= 1) Et((R(-0.5) * h * R(j) * ir_hm) * sf.at(SB_BXT, df, jm));
+    if (j < J) {
+      const C<R> bb = sf.at(SB_BXT, df, j);
+      Et((R(0.5) * h * R(j) * ir_h) * bb);
+      Er(imul(R(0.5) * h * R(k) * ir_h, bb));
+    }
+    if (j >= J - 1) {
+      // B_x(J) = (R - (a-b) B_x^(n+1/2)(J-1) + (a-b) B_x(J) + (a+b) B_x(J-1)) / (a+b),
+      // R = (1/2) ih (B_r(f+1, J) - B_r(f, J)) - (1/(2 rJ)) (E_th + i m E_r) - ...
+      const C<R> Rb = ikab * sf.at(SB_BXT, df, J);
+      if (j == J) {
+        Br((df == 0 ? R(0.5) : R(-0.5)) * ih * Rb);  // face c - 1 reads B_r(c) with +, face c with -
+        Et((R(-0.25) * irJ) * Rb);
+      }
+      Er(imul(R(k) * R(0.125) * irJ, Rb));
+    }
+  }
+  o.t[0] = trp;
+  o.t[1] = trm;
+  o.t[2] = ttp;
+  o.t[3] = ttm;
   return o;
 }
 
