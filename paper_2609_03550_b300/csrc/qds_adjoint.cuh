@@ -405,11 +405,18 @@ QDS_HD void adj_src(const Adj<R, M> &a, int f, int j, double &dg_acc) {
   const R h = a.h;
   const AdjFwd<R, M> t(a.f, a.fnext, a.mw, f);
   C<R> Gb[M], Sb[M];
+  const bool last_face = f + 1 > a.nx - 2;  // phi of cell f + 1 is off the faces
   #pragma unroll
   for (int k = 0; k < M; k++) {
     // T_a^+(c + 1) = T_a^+(c) + h Gamma_a(c + 1/2), T_a^-(c) = T_a^-(c + 1) + h
-    // Gamma_a(c + 1/2): face f gives the old T_a^+ of cell f and T_a^- of f + 1
-    const C<R> tp = a.tap_n(k, f + 1, j), tm = a.tam_n(k, f, j);
+    // Gamma_a(c + 1/2): face f gives the old T_a^+ of cell f and T_a^- of f + 1;
+    // the new T_a adjoints carry the phi update's share of the faces on
+    // either side of their cell
+    const NewCols<R, M> nc(a, k, f);
+    const C<R> ph0 = nc.at(PHI, 0, j);
+    const C<R> ph1 = last_face ? zero<R>() : nc.at(PHI, 1, j);
+    const C<R> tp = nc.at(TAP, 1, j) + (R(0.25) * h) * (ph0 + ph1);
+    const C<R> tm = nc.at(TAM, 0, j) + (R(0.25) * h) * (nc.at(PHI, -1, j) + ph0);
     a.old(TAP, k, f, j) = tp;
     a.old(TAM, k, f + 1, j) = tm;
     Gb[k] = h * (tp + tm);
