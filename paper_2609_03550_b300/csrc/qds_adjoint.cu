@@ -57,7 +57,7 @@ struct AdjLayout {
 // AD_SRC: one thread per (x, r) point with all modes; AD_LEAP, AD_CELL: one
 // thread per (mode, x, r), r fastest.
 template <class R, int M, int ST>
-__global__ void __launch_bounds__(kThr, sizeof(R) == 8 ? 1 : (ST == AD_SRC ? (M <= 3 ? 3 : 2) : ST == AD_LEAP ? 6 : 5)) adjoint_kernel(Adj<R, M> a) {
+__global__ void __launch_bounds__(kThr, sizeof(R) == 8 ? 1 : (ST == AD_SRC ? (M <= 3 ? 3 : 2) : 6)) adjoint_kernel(Adj<R, M> a) {
   const int n = a.nx * a.nr;
   const int total = ST == AD_SRC ? n : M * n;
   double acc = 0;
