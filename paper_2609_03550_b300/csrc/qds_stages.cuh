@@ -272,8 +272,9 @@ QDS_NOINL C<R> ex_update(const TT &t, int grp, int k, int w, int j, C<R> jx) {
   C<R> bhi = R(0.5) * (t.Bt(grp, k, w, j) + t.Bt(grp, k, w + 1, j));
   C<R> blo = R(0.5) * (t.Bt(grp, k, w, j - 1) + t.Bt(grp, k, w + 1, j - 1));
   C<R> br = R(0.5) * (t.Br(grp, k, w, j) + t.Br(grp, k, w + 1, j));
-  C<R> curl = ((R(j) + R(0.5)) * bhi - (R(j) - R(0.5)) * blo) * (R(1) / (R(j) * t.dr));
-  C<R> gx = curl + imul(R(k) / rj, br) - jx;
+  const R irj = R(1) / rj;  // mode-independent: the divisions stay out of the mode loops
+  C<R> curl = ((R(j) + R(0.5)) * bhi - (R(j) - R(0.5)) * blo) * irj;
+  C<R> gx = curl + imul(R(k) * irj, br) - jx;
   return e0 + t.h * gx;
 }
 
@@ -284,8 +285,9 @@ QDS_NOINL C<R> bx_interior(const TT &t, int grp, int k, int w, int j) {
   C<R> elo = R(0.5) * (t.Et(grp, k, w, j) + t.Et(grp, k, w + 1, j));
   C<R> ehi = (j + 1 < t.nr) ? R(0.5) * (t.Et(grp, k, w, j + 1) + t.Et(grp, k, w + 1, j + 1)) : zero<R>();
   C<R> er = R(0.5) * (t.Er(grp, k, w, j) + t.Er(grp, k, w + 1, j));
-  C<R> curl = (R(j + 1) * ehi - R(j) * elo) * (R(1) / ((R(j) + R(0.5)) * t.dr));
-  return b0 - t.h * (curl + imul(R(k) / rh, er));
+  const R irh = R(1) / rh;
+  C<R> curl = (R(j + 1) * ehi - R(j) * elo) * irh;
+  return b0 - t.h * (curl + imul(R(k) * irh, er));
 }
 
 // Outer half row J+1/2, Eq. em_r_open_bx by the box scheme over
@@ -325,9 +327,9 @@ QDS_NOINL void leap_point(const TT &t, int grp, int k, int w, int j, C<R> jx, C<
     const C<R> rpl = t.cell(grp + TRP, k, w, j - 1) + t.cell(grp + TRP, k, w + 1, j - 1);
     const C<R> rml = t.cell(grp + TRM, k, w, j - 1) + t.cell(grp + TRM, k, w + 1, j - 1);
     const C<R> blo = R(0.25) * (rpl - rml);
-    const R rj = R(j) * t.dr;
-    const C<R> curl = ((R(j) + R(0.5)) * bth - (R(j) - R(0.5)) * blo) * (R(1) / rj);
-    ex = e0 + t.h * (curl + imul(R(k) / rj, brr) - jx);
+    const R irj = R(1) / (R(j) * t.dr);
+    const C<R> curl = ((R(j) + R(0.5)) * bth - (R(j) - R(0.5)) * blo) * irj;
+    ex = e0 + t.h * (curl + imul(R(k) * irj, brr) - jx);
   }
   if (j == t.J && !t.closed) {
     bx = bx_outer(t, grp, k, w, jt_face, bx_interior(t, grp, k, w, j - 1));
@@ -339,9 +341,9 @@ QDS_NOINL void leap_point(const TT &t, int grp, int k, int w, int j, C<R> jx, C<
     const C<R> qm1 = t.cell(grp + TTM, k, w, j + 1) + t.cell(grp + TTM, k, w + 1, j + 1);
     ehi = R(0.25) * (qp1 + qm1);
   }
-  const R rh = (R(j) + R(0.5)) * t.dr;
-  const C<R> curl = (R(j + 1) * ehi - R(j) * eth) * (R(1) / rh);
-  bx = t.face(grp + BX, k, w, j) - t.h * (curl + imul(R(k) / rh, er));
+  const R irh = R(1) / ((R(j) + R(0.5)) * t.dr);
+  const C<R> curl = (R(j + 1) * ehi - R(j) * eth) * irh;
+  bx = t.face(grp + BX, k, w, j) - t.h * (curl + imul(R(k) * irh, er));
 }
 
 // ---------------------------------------------------------------------------
@@ -392,16 +394,16 @@ struct Faces1 {
 template <class TT, class FS, class R = typename TT::Real>
 QDS_NOINL void tr_interior(const TT &t, const FS &fs, int grp, int k, int lx, int lr, C<R> &tp, C<R> &tm) {
   const int c = t.x0 + lx, j = t.r0 + lr;
-  R rh = (R(j) + R(0.5)) * t.dr;
+  const R irh = R(1) / ((R(j) + R(0.5)) * t.dr);
   C<R> sp = zero<R>(), sm = zero<R>();
   if (t.face_ok(c - 1)) {
     C<R> ehi = (j + 1 < t.nr) ? fs.ex(k, lx - 1, lr + 1) : zero<R>();
-    C<R> gr = -imul(R(k) / rh, fs.bx(k, lx - 1, lr)) - fs.jr(k, lx - 1, lr);
+    C<R> gr = -imul(R(k) * irh, fs.bx(k, lx - 1, lr)) - fs.jr(k, lx - 1, lr);
     sp = gr + t.idr * (ehi - fs.ex(k, lx - 1, lr));
   }
   if (t.face_ok(c)) {
     C<R> ehi = (j + 1 < t.nr) ? fs.ex(k, lx, lr + 1) : zero<R>();
-    C<R> gr = -imul(R(k) / rh, fs.bx(k, lx, lr)) - fs.jr(k, lx, lr);
+    C<R> gr = -imul(R(k) * irh, fs.bx(k, lx, lr)) - fs.jr(k, lx, lr);
     sm = gr - t.idr * (ehi - fs.ex(k, lx, lr));
   }
   tp = t.cell(grp + TRP, k, c - 1, j) + t.h * sp;
@@ -415,10 +417,10 @@ template <class TT, class FS, class R = typename TT::Real>
 QDS_NOINL void tr_outer(const TT &t, const FS &fs, int grp, int k, int lx, C<R> bt_in_new, int lr_J, C<R> &tp,
                         C<R> &tm) {
   const int c = t.x0 + lx, J = t.J;
-  R rh = (R(J) + R(0.5)) * t.dr, rJ = R(J) * t.dr;
+  const R irh = R(1) / ((R(J) + R(0.5)) * t.dr), rJ = R(J) * t.dr;
   C<R> gl = zero<R>(), gr = zero<R>();
-  if (t.face_ok(c - 1)) gl = -imul(R(k) / rh, fs.bx(k, lx - 1, lr_J)) - fs.jr(k, lx - 1, lr_J);
-  if (t.face_ok(c)) gr = -imul(R(k) / rh, fs.bx(k, lx, lr_J)) - fs.jr(k, lx, lr_J);
+  if (t.face_ok(c - 1)) gl = -imul(R(k) * irh, fs.bx(k, lx - 1, lr_J)) - fs.jr(k, lx - 1, lr_J);
+  if (t.face_ok(c)) gr = -imul(R(k) * irh, fs.bx(k, lx, lr_J)) - fs.jr(k, lx, lr_J);
   C<R> er_new = R(0.5) * (t.cell(grp + TRP, k, c - 1, J) + t.cell(grp + TRM, k, c + 1, J) + t.h * (gl + gr));
   C<R> erl = R(0.5) * (t.Er(grp, k, c - 1, J - 1) + t.Er(grp, k, c - 1, J));
   C<R> err = R(0.5) * (t.Er(grp, k, c + 1, J - 1) + t.Er(grp, k, c + 1, J));
@@ -448,7 +450,7 @@ QDS_NOINL void tt_update(const TT &t, const FS &fs, int grp, int k, int lx, int 
       p = imul(t.idr, fs.ex(k, lf, lr + 1) - fs.ex(k, lf, lr));
     } else {
       g = -t.idr * (fs.bx(k, lf, lr) - fs.bx(k, lf, lr - 1)) - fs.jt(k, lf, lr);
-      p = imul(R(k) / (R(j) * t.dr), fs.ex(k, lf, lr));
+      p = imul(R(k) * (R(1) / (R(j) * t.dr)), fs.ex(k, lf, lr));
     }
     if (side == 0) sp = g + p; else sm = g - p;
   }
@@ -518,6 +520,7 @@ QDS_NOINL void source_point(const TT &t, int lx, int lr, const NV &nv, int m_onl
   }
   const R idr2 = t.idr * t.idr;
   const R rh = (R(j) + R(0.5)) * t.dr;
+  const R irh2 = R(1) / (rh * rh);
 #pragma unroll
   for (int m = 0; m < M; m++) {
     if (m_only >= 0 && m != m_only) continue;
@@ -530,7 +533,7 @@ QDS_NOINL void source_point(const TT &t, int lx, int lr, const NV &nv, int m_onl
     else if (t.closed) pp = pc;
     else pp = t.face(PHI, m, w, j - 1) - (R(2) * t.dr * t.ih) * (pc - t.prev(m, w));
     C<R> lap = (R(j + 1) * (pp - pc) - R(j) * (pc - pm)) * (idr2 / (R(j) + R(0.5)));
-    C<R> ga = lap - (R(m * m) / (rh * rh) + t.ma2) * pc + t.gs * S;
+    C<R> ga = lap - (R(m * m) * irh2 + t.ma2) * pc + t.gs * S;
     t.sG(m, lx, lr) = ga;
   }
 }
@@ -609,7 +612,7 @@ QDS_NOINL void current_point(const TT &t, int lx, int lr, C<R> (&jax)[M], C<R> (
       a2[k] = R(0.5) * (er_lo + er_hi);
       C<R> ph = t.face(PHI, k, w, j);
       C<R> pl = (j > 0) ? t.face(PHI, k, w, j - 1) : par * ph;
-      if (j > 0) b2[k] = imul(-R(k) * R(0.5) / (R(j) * t.dr), pl + ph);
+      if (j > 0) b2[k] = imul(-R(k) * R(0.5) * (R(1) / (R(j) * t.dr)), pl + ph);
       else b2[k] = (k == 1) ? imul(-t.idr, ph - pl) : zero<R>();
       a3[k] = R(0.5) * (t.Et(0, k, w, j) + t.Et(0, k, w + 1, j));
       b3[k] = t.idr * (ph - pl);
@@ -671,7 +674,7 @@ QDS_NOINL void current_point(const TT &t, int lx, int lr, C<R> (&jax)[M], C<R> (
       if (j1 >= 0) ex_hi = t.sA(0, k, lx, lr + 1);
       else ex_hi = t.closed ? zero<R>() : ex_lo;
       a3[k] = R(0.5) * (ex_lo + ex_hi);
-      b3[k] = imul(-R(k) * R(0.5) / ((R(j) + R(0.5)) * t.dr), po + pn);
+      b3[k] = imul(-R(k) * R(0.5) * (R(1) / ((R(j) + R(0.5)) * t.dr)), po + pn);
     }
 #pragma unroll
     for (int m = 0; m < M; m++)
