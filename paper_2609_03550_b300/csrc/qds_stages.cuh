@@ -215,6 +215,37 @@ struct Tile {
     return scr[(size_t)plane * P + ((size_t)k * nx + slot(w)) * ld + j];
   }
   // lx, lr are offsets from the point (x0, r0)
+  // Reads of the new state and of the scratch planes.  Each pass reads only
+  // what earlier passes (earlier kernels) wrote, never what it writes
+  // itself, so these reads take the non-coherent path and the compiler may
+  // move them past the pass's own stores.
+  QDS_HD C<R> rnew(int field, int k, int w, int j) const {
+    if (FAST) {
+#if defined(QDS_EMU)
+      QDS_CHECK(cell_ok(w) && j >= 0 && j < nr, "unchecked new-state read");
+#endif
+      return ldg(n + eidx(field, k, slot(w), j));
+    }
+    if (!cell_ok(w) || j < 0 || j >= nr) return zero<R>();
+#if defined(QDS_EMU)
+    QDS_CHECK(gidx(field, k, w, j) < state_len, "pass-mode new-state read");
+#endif
+    return ldg(n + gidx(field, k, w, j));
+  }
+  QDS_HD C<R> rscr(int plane, int k, int w, int j) const {
+    if (!FAST && (!cell_ok(w) || j < 0 || j >= nr)) return zero<R>();
+    return ldg(scr + ((size_t)plane * P + ((size_t)k * nx + slot(w)) * ld + j));
+  }
+  QDS_HD C<R> rA(int pl, int k, int lx, int lr) const { return rnew(pl ? BX : EX, k, x0 + lx, r0 + lr); }
+  QDS_HD C<R> rG(int k, int lx, int lr) const { return rscr(0, k, x0 + lx, r0 + lr); }
+  QDS_HD C<R> rT(int pl, int k, int lx, int lr) const {
+    return rnew(pl < 4 ? TRP + pl : TAP + (pl - 4), k, x0 + lx, r0 + lr);
+  }
+  QDS_HD C<R> rP(int k, int lx, int lr) const { return rnew(PHI, k, x0 + lx, r0 + lr); }
+  QDS_HD C<R> rJ(int pl, int k, int lx, int lr) const {
+    if (pl < 2) return rnew(pl ? BX1 : EX1, k, x0 + lx, r0 + lr);
+    return rscr(pl - 1, k, x0 + lx, r0 + lr);
+  }
   QDS_HD C<R> &sA(int pl, int k, int lx, int lr) const { return gnew(pl ? BX : EX, k, x0 + lx, r0 + lr); }  // 0: Ex0n, 1: Bx0n
   QDS_HD C<R> &sG(int k, int lx, int lr) const { return gscr(0, k, x0 + lx, r0 + lr); }
   QDS_HD C<R> &sT(int pl, int k, int lx, int lr) const {  // 0..3 T0 new, 4 Tap new, 5 Tam new
@@ -355,8 +386,8 @@ template <class TT>
 struct Faces0 {
   using R = typename TT::Real;
   const TT &t;
-  QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sA(0, k, lx, lr); }
-  QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sA(1, k, lx, lr); }
+  QDS_HD C<R> ex(int k, int lx, int lr) const { return t.rA(0, k, lx, lr); }
+  QDS_HD C<R> bx(int k, int lx, int lr) const { return t.rA(1, k, lx, lr); }
   QDS_HD C<R> jr(int k, int lx, int lr) const {
     int w = t.x0 + lx, j = t.r0 + lr;
     if (!t.jr || !t.face_ok(w)) return zero<R>();
@@ -378,11 +409,11 @@ template <class TT>
 struct Faces1 {
   using R = typename TT::Real;
   const TT &t;
-  QDS_HD C<R> ex(int k, int lx, int lr) const { return t.sJ(0, k, lx, lr); }
-  QDS_HD C<R> bx(int k, int lx, int lr) const { return t.sJ(1, k, lx, lr); }
-  QDS_HD C<R> jx(int k, int lx, int lr) const { return t.sJ(2, k, lx, lr); }
-  QDS_HD C<R> jr(int k, int lx, int lr) const { return t.sJ(3, k, lx, lr); }
-  QDS_HD C<R> jt(int k, int lx, int lr) const { return t.sJ(4, k, lx, lr); }
+  QDS_HD C<R> ex(int k, int lx, int lr) const { return t.rJ(0, k, lx, lr); }
+  QDS_HD C<R> bx(int k, int lx, int lr) const { return t.rJ(1, k, lx, lr); }
+  QDS_HD C<R> jx(int k, int lx, int lr) const { return t.rJ(2, k, lx, lr); }
+  QDS_HD C<R> jr(int k, int lx, int lr) const { return t.rJ(3, k, lx, lr); }
+  QDS_HD C<R> jt(int k, int lx, int lr) const { return t.rJ(4, k, lx, lr); }
 };
 
 // ---------------------------------------------------------------------------
@@ -475,8 +506,8 @@ struct TileLeapVals {
   using R = typename TT::Real;
   const TT &t;
   int lx, lr;
-  QDS_HD C<R> exn(int k, int dj) const { return t.sA(0, k, lx, lr + dj); }
-  QDS_HD C<R> bxn(int k) const { return t.sA(1, k, lx, lr); }
+  QDS_HD C<R> exn(int k, int dj) const { return t.rA(0, k, lx, lr + dj); }
+  QDS_HD C<R> bxn(int k) const { return t.rA(1, k, lx, lr); }
 };
 
 // m_only >= 0: only the output mode m_only (the inputs of all modes are
@@ -563,9 +594,9 @@ struct TileNewVals {
   int lx;
   QDS_HD C<R> ns(int pl, int k, int jj) const {
     const int l = jj - t.r0;
-    return t.sT(pl, k, lx, l) + t.sT(pl, k, lx + 1, l);
+    return t.rT(pl, k, lx, l) + t.rT(pl, k, lx + 1, l);
   }
-  QDS_HD C<R> pn(int k, int jj) const { return t.sP(k, lx, jj - t.r0); }
+  QDS_HD C<R> pn(int k, int jj) const { return t.rP(k, lx, jj - t.r0); }
 };
 
 // comp selects the components computed (bit 0: j_a,x, 1: j_a,r, 2:
@@ -594,8 +625,8 @@ QDS_NOINL void current_point(const TT &t, int lx, int lr, C<R> (&jax)[M], C<R> (
 #pragma unroll
     for (int k = 0; k < M; k++) {
       const R par = (k & 1) ? R(-1) : R(1);
-      C<R> bx_hi = R(0.5) * (t.face(BX, k, w, j) + t.sA(1, k, lx, lr));
-      C<R> bx_lo = (j > 0) ? R(0.5) * (t.face(BX, k, w, j - 1) + t.sA(1, k, lx, lr - 1)) : par * bx_hi;
+      C<R> bx_hi = R(0.5) * (t.face(BX, k, w, j) + t.rA(1, k, lx, lr));
+      C<R> bx_lo = (j > 0) ? R(0.5) * (t.face(BX, k, w, j - 1) + t.rA(1, k, lx, lr - 1)) : par * bx_hi;
       a1[k] = R(0.5) * (bx_lo + bx_hi);
       C<R> dt_hi = R(0.125) * (t.cell(TAP, k, w, j) + t.cell(TAM, k, w, j) + t.cell(TAP, k, w + 1, j) + t.cell(TAM, k, w + 1, j) +
                                nv.ns(4, k, j) + nv.ns(5, k, j));
@@ -670,8 +701,8 @@ QDS_NOINL void current_point(const TT &t, int lx, int lr, C<R> (&jax)[M], C<R> (
       b1[k] = TAX(4, k, j);
       b2[k] = TAX(5, k, j);
       C<R> po = t.face(PHI, k, w, j), pn = nv.pn(k, j);
-      C<R> ex_lo = t.sA(0, k, lx, lr), ex_hi;
-      if (j1 >= 0) ex_hi = t.sA(0, k, lx, lr + 1);
+      C<R> ex_lo = t.rA(0, k, lx, lr), ex_hi;
+      if (j1 >= 0) ex_hi = t.rA(0, k, lx, lr + 1);
       else ex_hi = t.closed ? zero<R>() : ex_lo;
       a3[k] = R(0.5) * (ex_lo + ex_hi);
       b3[k] = imul(-R(k) * R(0.5) * (R(1) / ((R(j) + R(0.5)) * t.dr)), po + pn);
@@ -708,7 +739,7 @@ QDS_NOINL void current_point(const TT &t, int lx, int lr, C<R> (&jax)[M], C<R> (
       C<R> am_lo = (j > 0) ? TAX(5, k, j - 1) : par * am_hi;
       b1[k] = R(0.5) * (am_lo + am_hi);   // Ta- paired with Tr+
       b2[k] = R(0.5) * (ap_lo + ap_hi);   // Ta+ paired with Tr-
-      a3[k] = t.sA(0, k, lx, lr);
+      a3[k] = t.rA(0, k, lx, lr);
       C<R> pbh = R(0.5) * (t.face(PHI, k, w, j) + nv.pn(k, j));
       C<R> pbl = (j > 0) ? R(0.5) * (t.face(PHI, k, w, j - 1) + nv.pn(k, j - 1)) : par * pbh;
       b3[k] = t.idr * (pbh - pbl);
@@ -794,8 +825,8 @@ QDS_HD void run_stage(Tile<R, M, FAST> t, int st) {
         }
         tt_update(t, fs, 0, k, lx, lr, up, um);
         if (ax) {
-          ap = t.cell(TAP, k, c - 1, j) + t.h * t.sG(k, lx - 1, lr);
-          am = t.cell(TAM, k, c + 1, j) + t.h * t.sG(k, lx, lr);
+          ap = t.cell(TAP, k, c - 1, j) + t.h * t.rG(k, lx - 1, lr);
+          am = t.cell(TAM, k, c + 1, j) + t.h * t.rG(k, lx, lr);
         }
       }
       t.store(TRP, k, c, j, tp); t.store(TRM, k, c, j, tm);
@@ -807,8 +838,8 @@ QDS_HD void run_stage(Tile<R, M, FAST> t, int st) {
         const bool flive = t.face_ok(c) && j >= 0 && j < t.nr;
         C<R> v = zero<R>(), po = zero<R>();
         if (flive) {
-          const C<R> ap1 = t.cell(TAP, k, c, j) + t.h * t.sG(k, lx, lr);
-          const C<R> am1 = t.cell(TAM, k, c + 2, j) + t.h * t.sG(k, lx + 1, lr);
+          const C<R> ap1 = t.cell(TAP, k, c, j) + t.h * t.rG(k, lx, lr);
+          const C<R> am1 = t.cell(TAM, k, c + 2, j) + t.h * t.rG(k, lx + 1, lr);
           po = t.face(PHI, k, c, j);
           v = po + (R(0.25) * t.h) * (am1 + am + ap1 + ap);
         }
